@@ -1,0 +1,211 @@
+/*
+ * mace.h -- C ABI of the GB300 library for partial-update MACE CT
+ * reconstruction (Sridhar, Wang, Buzzard, Bouman, arXiv 1911.09278).
+ *
+ * The problem (Sec. II-A, Eqs. "MAP est", "global_obj", "local_obj"):
+ *   x* = argmin_x  sum_k 1/2 ||y_k - A_k x||^2_{Lambda_k} + beta h(x),
+ * split over N view subsets J_i (interleaved by default: J_i = {m : m mod N
+ * = i}, 0-based) into agents f_i = sum_{k in J_i} ... + (beta/N) h(x).
+ * Each agent's proximal map F_i (Eq. "prox_F") is replaced by its partial
+ * update F~_i(v; X_i) (Algorithm 2: ICD passes from the state X_i), and the
+ * Mann iteration of T = (2F - I)(2G - I) (Eqs. "w*_fixed_pt", "Mann") is run
+ * as Algorithm 1:  v = (2G - I) w;  X = F~(v; X);  w <- rho (2X - v) +
+ * (1 - rho) w;  solution x* = mean_i w_i.
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 on success, a negative MACE_E* code on failure; the
+ *     message of the last failure on the calling thread is mace_last_error().
+ *   - Handles are opaque and owned by the library; free them with the
+ *     matching mace_free_* call.  A state borrows its system matrix, which
+ *     must outlive every state built on it.
+ *   - All device work is ordered on the CUDA stream given at creation (NULL
+ *     = the legacy default stream).  Entry points that return host values
+ *     synchronise that stream.
+ *   - Image arrays are [nz][ny][nx] row-major (row 0 at the top); sinogram
+ *     arrays are [nz][n_views][n_channels]; stacked agent images are
+ *     [n_agents][nz*ny*nx].  All are float32.
+ *   - ptr_is_device != 0 means the pointer is CUDA device memory read or
+ *     written on the state's stream; otherwise it is host memory and the call
+ *     copies synchronously.  Input pointers are only read during the call.
+ *
+ * The GPU never faults on bad input: arguments are checked on the host and
+ * device-side waits are bounded (MACE_ETIMEOUT).
+ */
+#ifndef MACE_H
+#define MACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MACE_OK               0
+#define MACE_EINVAL          -1   /* bad argument, shape or parameter       */
+#define MACE_ENOMEM          -2   /* device or host allocation failed       */
+#define MACE_ECUDA           -3   /* a CUDA runtime call failed             */
+#define MACE_ENOTCONVERGED   -4   /* max_iter reached before tol            */
+#define MACE_ETIMEOUT        -5   /* a bounded device-side wait expired     */
+#define MACE_ENUMERIC        -6   /* non-finite residual (divergence)       */
+
+typedef struct mace_sysmatrix mace_sysmatrix;
+typedef struct mace_state mace_state;
+
+/* Scanner geometry (Sec. II-A; the paper fixes parallel-beam views over
+ * 180 degrees, Sec. IV, but not the projector).  Parallel beam; square
+ * pixels of pitch pixel_pitch with pixel (row i, col j) centred at
+ * ((j - (nx-1)/2) dx, ((ny-1)/2 - i) dx); channel c covers detector
+ * coordinate t in [(c - n_channels/2) dd + off, (c + 1 - n_channels/2) dd +
+ * off).  A[c, s] for view angle theta is the strip integral of pixel s over
+ * channel c divided by dd (t = x cos theta + y sin theta).
+ * view_angles: host array of n_views radians, or NULL for m pi / n_views.
+ * nz > 1 is a stack of slices sharing the 2D matrix. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t n_views, n_channels;
+    double pixel_pitch, channel_pitch, channel_offset;
+    const double *view_angles;
+} mace_geometry;
+
+/* View partition J_1..J_N (Sec. II-A, footnote: any partition).
+ * view_agent: host array of n_views agent indices in [0, n_agents), or NULL
+ * for interleaved subsets m mod n_agents.  Every agent needs >= 1 view. */
+typedef struct {
+    int32_t n_agents;
+    const int32_t *view_agent;
+} mace_partition;
+
+typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
+
+/* Prior, agent and solver parameters.
+ *   prior 0: quadratic, rho(D) = D^2 / (2 sigma_x^2) (the x^T B x prior of
+ *            Theorem 2, with h = 1/2 x^T B x);
+ *   prior 1: Q-GGMRF, rho(D) = (D^2/(2 sigma_x^2)) / (1 + |D/(T sigma_x)|^(p-q)),
+ *            p must be 2 (the paper cites the prior without defining it).
+ *   h(x) = sum over neighbour pairs of b_sr rho(x_s - x_r), b_sr ~ 1/distance
+ *   over the 8-neighbourhood, normalised to sum 1; neighbourhood must be 8.
+ *   sigma: the proximal parameter of Eq. "prox_F"; sigma_mode 0 takes it in
+ *   image units, 1 scales it by 1/sqrt(mean_{i,s} sum_{k in J_i} A^2 Lambda).
+ *   rho in (0, 1): Mann parameter (Eq. "Mann").
+ *   sweeps_per_iter >= 1 ICD passes per Mann iteration; symmetric != 0 runs
+ *   every second pass in reverse voxel order.
+ *   recompute_every > 0: e_i = y_i - A_i X_i is recomputed from scratch every
+ *   that many iterations (removes float drift); 0 never.
+ *   max_iter, tol: mace_reconstruct stops when the relative Mann residual
+ *   ||w^(k+1) - w^(k)|| / ||w^(k+1)|| (FP64) falls below tol.
+ *   concurrency: super-voxels of one agent updated at the same time (0 =
+ *   every warp the GPU holds; 1 = one at a time, the serial ICD order). */
+typedef struct {
+    int32_t prior;
+    int32_t neighbourhood;
+    double beta, sigma_x, p, q, T;
+    double sigma;
+    int32_t sigma_mode;
+    double rho;
+    int32_t sweeps_per_iter;
+    int32_t symmetric;
+    int32_t recompute_every;
+    int32_t max_iter;
+    double tol;
+    int32_t concurrency;
+} mace_params;
+
+/* Sizes of a built system matrix (for memory accounting, Table 3). */
+typedef struct {
+    int64_t n_voxels;        /* nx*ny (one slice)                          */
+    int32_t n_agents, sv_size, n_sv;   /* super-voxels per agent             */
+    int32_t max_views;       /* largest |J_i|                              */
+    int64_t nnz;             /* stored non-zeros over all agents           */
+    int64_t bytes_columns;   /* headers + values + padding                 */
+    int64_t bytes_meta;      /* offsets and band descriptors               */
+    int64_t agent_bytes[64]; /* column bytes of agents 0..63               */
+} mace_sysmatrix_info;
+
+/* Build the stored system matrix (the paper precomputes and stores A,
+ * Sec. I and Table 3) for every agent: voxel-column-major per super-voxel
+ * (sv_size x sv_size pixel tiles), per view a run (first channel, length
+ * 0..3, values).  dtype selects the stored value type.  Runs on the GPU on
+ * cuda_stream (a cudaStream_t or NULL).  *out receives the handle.
+ * Errors: MACE_EINVAL (sizes, angles, partition, sv_size not in [2, 32],
+ * more than 4096 views), MACE_ENOMEM, MACE_ECUDA. */
+int mace_build_sysmatrix(const mace_geometry *geom, const mace_partition *part,
+                         mace_dtype dtype, int32_t sv_size, void *cuda_stream,
+                         mace_sysmatrix **out);
+
+int mace_sysmatrix_get_info(const mace_sysmatrix *sm, mace_sysmatrix_info *info);
+
+/* Decode the stored column of pixel (row i, col j) for agent g: for each of
+ * the agent's views (increasing m) the first channel, run length and values
+ * (widened to float).  c0, len: [|J_g|]; vals: [3 |J_g|], zero-padded.
+ * Host arrays; copies a few hundred bytes from the device. */
+int mace_sysmatrix_column(const mace_sysmatrix *sm, int32_t g, int32_t i, int32_t j,
+                          int32_t *c0, int32_t *len, float *vals);
+
+/* The pixel visiting order of a forward ICD pass (raster indices i*nx + j,
+ * nx*ny entries): super-voxels in the library's order, raster inside each.
+ * With params.concurrency = 1 every agent's pass is exactly Algorithm 2 in
+ * this order; a backward pass visits it from the end. */
+int mace_sysmatrix_visit_order(const mace_sysmatrix *sm, int64_t *order);
+
+/* Create a reconstruction state: copies y and weights (Lambda, the inverse
+ * noise variances) into agent-major device layout, sets w^(0) = w0 (NULL =
+ * 0; [n_agents][n] float32), X^(0) = G(w^(0)) (Algorithm 1 initialisation)
+ * and e_i = y_i - A_i X_i.  Work is ordered on cuda_stream.
+ * Errors: MACE_EINVAL (parameters out of range, non-finite or negative
+ * weights), MACE_ENOMEM, MACE_ECUDA. */
+int mace_init(const mace_sysmatrix *sm, const float *y, const float *weights,
+              int32_t ptr_is_device, const mace_params *params, const float *w0,
+              void *cuda_stream, mace_state **out);
+
+/* Run n_iters Mann iterations of Algorithm 1.  residual_out (may be NULL)
+ * receives the relative Mann residual of the last iteration (FP64);
+ * converged_out (may be NULL) is set to 1 once it is below params.tol.
+ * Errors: MACE_ENUMERIC when the residual is not finite, MACE_ETIMEOUT,
+ * MACE_ECUDA. */
+int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out,
+                 int32_t *converged_out);
+
+/* Iterate until the residual is below params.tol or params.max_iter
+ * iterations have run (checking every 10 iterations), then write the
+ * consensus image x* = mean_i w_i (Algorithm 1 output) to x_out ([nz][ny][nx]).
+ * Returns MACE_ENOTCONVERGED (x_out still written) if max_iter was hit. */
+int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device,
+                     int32_t *iters_out, double *residual_out);
+
+/* Consensus image mean_i w_i of the current state, without iterating. */
+int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device);
+
+/* Checkpoint / resume: the complete algorithm state is (w, X) (Eq.
+ * "PUCEupdate"); e_i is recomputed from X on mace_set_state.  w, X:
+ * [n_agents][n] float32 (either may be NULL in get_state). */
+int mace_get_state(mace_state *st, float *w, float *X, int32_t ptr_is_device);
+int mace_set_state(mace_state *st, const float *w, const float *X, int32_t ptr_is_device);
+
+/* One partial-update pass X_i <- F~_i(v_i; X_i) (Algorithm 2) for every
+ * agent with the given v ([n_agents][n] float32), without touching w.
+ * backward != 0 visits voxels in reverse order.  For testing the agent
+ * update in isolation. */
+int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_device, int32_t backward);
+
+/* Error sinograms e_i in agent-local layout: agent g's block is
+ * [nz][|J_g|][n_channels], agents concatenated in order. */
+int mace_get_error(mace_state *st, float *e, int32_t ptr_is_device);
+int64_t mace_error_size(const mace_state *st);
+
+/* Recompute e_i = y_i - A_i X_i from scratch. */
+int mace_recompute_error(mace_state *st);
+
+/* Iterations run so far, the proximal sigma in image units, the last
+ * residual and the super-voxels of one agent in flight per pass. */
+int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
+                   double *last_residual, int32_t *concurrency);
+
+void mace_free_state(mace_state *st);
+void mace_free_sysmatrix(mace_sysmatrix *sm);
+const char *mace_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACE_H */

@@ -1,0 +1,1615 @@
+// GB300 (sm_103a) implementation of partial-update MACE CT reconstruction
+// (Sridhar, Wang, Buzzard, Bouman, arXiv 1911.09278).  C ABI in include/mace.h.
+//
+// Per Mann iteration (Algorithm 1):
+//   consensus_kernel   wbar = (1/N) sum_i w_i in FP64 (the operator G, Eq.
+//                      "G_operators"), plus the final fixed-order reduction of
+//                      the previous iteration's residual partials;
+//   icd_sweep_kernel   K passes of Algorithm 2 per agent: X_i <- F~_i(v_i; X_i)
+//                      with v_i = 2 wbar - w_i formed on the fly;
+//   mann_kernel        w_i <- rho (2 X_i - v_i) + (1 - rho) w_i, FP64 partials of
+//                      ||w^(k+1) - w^(k)||^2 and ||w^(k+1)||^2.
+//
+// The stored system matrix is voxel-column-major per super-voxel (an SxS tile
+// of pixels): for every agent, super-voxel and pixel, a column holding, per
+// view of the agent, a run (first channel relative to the super-voxel's
+// sinogram band, length 0..3) and its values.  One warp owns one super-voxel
+// at a time: it stages the super-voxel's band of the agent's error sinogram
+// e_i and weights Lambda_i in shared memory, streams the columns in with TMA
+// bulk copies into a per-warp ring, visits the pixels in order (lane = view),
+// and flushes its change of e back to global memory at the end.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/mace.h"
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                          \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess)                                                  \
+            return fail(MACE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+extern "C" const char *mace_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------
+static constexpr int kMaxViews = 4096;     // per geometry
+static constexpr int kRing = 8;            // column ring stages per warp
+static constexpr uint32_t kSpinLimit = 1u << 26;  // bounded device waits
+static constexpr int kStatusTimeout = 1;
+
+// ---------------------------------------------------------------------------
+// geometry: strip-integral footprint of a square pixel (FP64, IEEE ops only)
+// ---------------------------------------------------------------------------
+struct GeoParams {
+    int nx, ny, D;
+    double dx, dd, off;
+};
+
+__device__ __forceinline__ double trap_cdf_dev(double u, double w1, double w2)
+{
+    double u1 = __dmul_rn(0.5, __dsub_rn(w2, w1));
+    double u2 = __dmul_rn(0.5, __dadd_rn(w2, w1));
+    double h = __ddiv_rn(1.0, w2);
+    if (u <= -u2) return 0.0;
+    if (u < -u1) {
+        double d = __dadd_rn(u, u2);
+        return __ddiv_rn(__dmul_rn(__dmul_rn(h, d), d), __dmul_rn(2.0, w1));
+    }
+    if (u <= u1) return __dmul_rn(h, __dadd_rn(__dmul_rn(0.5, w1), __dadd_rn(u, u1)));
+    if (u < u2) {
+        double d = __dsub_rn(u2, u);
+        return __dsub_rn(1.0, __ddiv_rn(__dmul_rn(__dmul_rn(h, d), d), __dmul_rn(2.0, w1)));
+    }
+    return 1.0;
+}
+
+// Run of pixel (row i, col j) at view (ct, st): first channel and length
+// (0..3, clipped to the detector); values in vals when non-null.
+__device__ __forceinline__ int footprint_dev(const GeoParams &G, double ct, double st, int i, int j,
+                                             int &c0, double *vals)
+{
+    double xc = __dmul_rn(__dsub_rn((double)j, __dmul_rn(0.5, (double)(G.nx - 1))), G.dx);
+    double yc = __dmul_rn(__dsub_rn(__dmul_rn(0.5, (double)(G.ny - 1)), (double)i), G.dx);
+    double t0 = __dadd_rn(__dmul_rn(xc, ct), __dmul_rn(yc, st));
+    double qc = __dadd_rn(__ddiv_rn(__dsub_rn(t0, G.off), G.dd), __dmul_rn(0.5, (double)G.D));
+    double a = __ddiv_rn(__dmul_rn(G.dx, fabs(ct)), G.dd);
+    double b = __ddiv_rn(__dmul_rn(G.dx, fabs(st)), G.dd);
+    double w1 = a < b ? a : b;
+    double w2 = a < b ? b : a;
+    double half = __dmul_rn(0.5, __dadd_rn(a, b));
+    double lo = __dsub_rn(qc, half), hi = __dadd_rn(qc, half);
+    int cf = (int)floor(lo);
+    int cl = (int)ceil(hi) - 1;
+    if (cf < 0) cf = 0;
+    if (cl > G.D - 1) cl = G.D - 1;
+    int L = cl - cf + 1;
+    if (L < 0) L = 0;
+    if (L > 3) L = 3;  // excluded by the host check on the pitches
+    c0 = cf;
+    if (vals) {
+        double scale = __ddiv_rn(__dmul_rn(G.dx, G.dx), G.dd);
+        for (int k = 0; k < L; ++k) {
+            double c = (double)(cf + k);
+            double hiu = __dsub_rn(__dadd_rn(c, 1.0), qc);
+            double lou = __dsub_rn(c, qc);
+            vals[k] = __dmul_rn(scale, __dsub_rn(trap_cdf_dev(hiu, w1, w2), trap_cdf_dev(lou, w1, w2)));
+        }
+    }
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// system matrix
+// ---------------------------------------------------------------------------
+struct mace_sysmatrix {
+    GeoParams geo;
+    int nz;
+    int V, N, S, nsvx, nsvy, nsv, S2;
+    int max_views, max_band, max_col_bytes;
+    mace_dtype dtype;
+    int vbytes;                       // bytes per stored value
+    cudaStream_t stream;
+    std::vector<int> view_agent;      // [V]
+    std::vector<int> agent_views;     // views grouped by agent (increasing m)
+    std::vector<int> view_off;        // [N+1]
+    std::vector<double> cosv, sinv;
+    // device
+    double2 *d_cs = nullptr;          // (cos, sin) per view in agent order
+    int *d_view_off = nullptr;        // [N+1]
+    uint32_t *d_band = nullptr;       // [nsv * V]: agent g block at nsv*view_off[g], (lo | len << 16)
+    uint32_t *d_band_tot = nullptr;   // [N * nsv]
+    int64_t *d_sv_base = nullptr;     // [N * nsv] byte offset of the super-voxel block
+    uint32_t *d_col_off = nullptr;    // [N * nsv * (S2 + 1)] byte offsets inside the block
+    uint8_t *d_cols = nullptr;
+    int64_t bytes_cols = 0, nnz = 0;
+    std::vector<int64_t> agent_bytes;
+    std::vector<int32_t> sv_order;    // visiting order of super-voxels
+    int32_t *d_sv_order = nullptr;
+};
+
+__global__ void band_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
+                            int N, int S, int nsvx, int nsv, uint32_t *__restrict__ band)
+{
+    // one thread per (view in agent order, super-voxel); the view's agent block
+    // of band[] starts at nsv * view_off[g]
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int V = view_off[N];
+    if (tid >= (int64_t)V * nsv) return;
+    int vg = (int)(tid / nsv);        // global index in agent order
+    int sv = (int)(tid % nsv);
+    int g = 0;
+    while (view_off[g + 1] <= vg) ++g;
+    int v = vg - view_off[g];
+    int Vg = view_off[g + 1] - view_off[g];
+    int si = sv / nsvx, sj = sv % nsvx;
+    int lo = 1 << 30, hi = -1;
+    for (int t = 0; t < S * S; ++t) {
+        int i = si * S + t / S, j = sj * S + t % S;
+        if (i >= G.ny || j >= G.nx) continue;
+        int c0;
+        int L = footprint_dev(G, cs[vg].x, cs[vg].y, i, j, c0, nullptr);
+        if (L > 0) {
+            lo = min(lo, c0);
+            hi = max(hi, c0 + L - 1);
+        }
+    }
+    uint32_t d = 0;
+    if (hi >= lo) d = (uint32_t)lo | ((uint32_t)(hi - lo + 1) << 16);
+    band[(int64_t)nsv * view_off[g] + (int64_t)sv * Vg + v] = d;
+}
+
+// bytes of one column: headers padded to 4, then per round of 32 views the
+// slot-0 values of every view, slot-1 values of views with L >= 2, slot-2
+// values of views with L == 3; padded to 16.
+__global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
+                               int N, int S, int nsvx, int nsv, int vbytes,
+                               uint32_t *__restrict__ col_bytes, uint32_t *__restrict__ col_nnz)
+{
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int S2 = S * S;
+    if (tid >= (int64_t)N * nsv * S2) return;
+    int g = (int)(tid / ((int64_t)nsv * S2));
+    int rem = (int)(tid % ((int64_t)nsv * S2));
+    int sv = rem / S2, t = rem % S2;
+    int si = sv / nsvx, sj = sv % nsvx;
+    int i = si * S + t / S, j = sj * S + t % S;
+    if (i >= G.ny || j >= G.nx) { col_bytes[tid] = 0; col_nnz[tid] = 0; return; }
+    int v0 = view_off[g], Vg = view_off[g + 1] - v0;
+    int nvals = 0, nz = 0;
+    for (int v = 0; v < Vg; ++v) {
+        int c0;
+        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr);
+        nvals += L > 0 ? L : 1;   // slot 0 always present
+        nz += L;
+    }
+    uint32_t bytes = (uint32_t)((Vg + 3) & ~3) + (uint32_t)nvals * vbytes;
+    col_bytes[tid] = (bytes + 15u) & ~15u;
+    col_nnz[tid] = nz;
+}
+
+template <typename T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ float from_double<float>(double x) { return __double2float_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+template <> __device__ __forceinline__ __half from_double<__half>(double x) { return __double2half(x); }
+
+template <typename T>
+__global__ void fill_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
+                            int N, int S, int nsvx, int nsv, const uint32_t *__restrict__ band,
+                            const int64_t *__restrict__ sv_base, const uint32_t *__restrict__ col_off,
+                            uint8_t *__restrict__ cols)
+{
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int S2 = S * S;
+    if (tid >= (int64_t)N * nsv * S2) return;
+    int g = (int)(tid / ((int64_t)nsv * S2));
+    int rem = (int)(tid % ((int64_t)nsv * S2));
+    int sv = rem / S2, t = rem % S2;
+    int si = sv / nsvx, sj = sv % nsvx;
+    int i = si * S + t / S, j = sj * S + t % S;
+    if (i >= G.ny || j >= G.nx) return;
+    int v0 = view_off[g], Vg = view_off[g + 1] - v0;
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    int64_t gsv = (int64_t)g * nsv + sv;
+    uint8_t *col = cols + sv_base[gsv] + col_off[gsv * (S2 + 1) + t];
+    T *vals = (T *)(col + ((Vg + 3) & ~3));
+    int base = 0;
+    for (int r = 0; r * 32 < Vg; ++r) {
+        int Vr = min(32, Vg - r * 32);
+        int Ls[32];
+        double a[32][3];
+        int n1 = 0, n2 = 0;
+        for (int l = 0; l < Vr; ++l) {
+            int v = r * 32 + l, c0;
+            int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a[l]);
+            int lo = (int)(bd[v] & 0xFFFFu);
+            int crel = L > 0 ? c0 - lo : 0;
+            col[v] = (uint8_t)((crel << 2) | L);
+            Ls[l] = L;
+            if (L == 0) a[l][0] = 0.0;
+            n1 += L >= 2;
+            n2 += L == 3;
+        }
+        int k1 = 0, k2 = 0;
+        for (int l = 0; l < Vr; ++l) {
+            vals[base + l] = from_double<T>(a[l][0]);
+            if (Ls[l] >= 2) vals[base + Vr + (k1++)] = from_double<T>(a[l][1]);
+            if (Ls[l] == 3) vals[base + Vr + n1 + (k2++)] = from_double<T>(a[l][2]);
+        }
+        base += Vr + n1 + n2;
+    }
+}
+
+static int check_geometry(const mace_geometry *g)
+{
+    if (!g) return fail(MACE_EINVAL, "geometry is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->n_views < 1 || g->n_channels < 1)
+        return fail(MACE_EINVAL, "geometry sizes must be positive");
+    if (g->n_views > kMaxViews) return fail(MACE_EINVAL, "more than 4096 views");
+    if (g->n_channels > 65535) return fail(MACE_EINVAL, "more than 65535 channels");
+    if (!(g->pixel_pitch > 0) || !(g->channel_pitch > 0) || !std::isfinite(g->channel_offset))
+        return fail(MACE_EINVAL, "pitches must be positive and finite");
+    // runs of at most 3 channels: footprint width dx(|cos|+|sin|)/dd <= sqrt(2) dx/dd <= 2
+    if (g->pixel_pitch * std::sqrt(2.0) > 2.0 * g->channel_pitch)
+        return fail(MACE_EINVAL, "channel_pitch must be >= pixel_pitch / sqrt(2)");
+    if (g->nz != 1) return fail(MACE_EINVAL, "only nz == 1 (2D) is supported");
+    return MACE_OK;
+}
+
+extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partition *part,
+                                    mace_dtype dtype, int32_t sv_size, void *cuda_stream,
+                                    mace_sysmatrix **out)
+{
+    if (!out) return fail(MACE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_geometry(geom);
+    if (rc) return rc;
+    if (!part || part->n_agents < 1 || part->n_agents > geom->n_views)
+        return fail(MACE_EINVAL, "n_agents must be in [1, n_views]");
+    if (sv_size < 2 || sv_size > 32) return fail(MACE_EINVAL, "sv_size must be in [2, 32]");
+    if (dtype != MACE_F32 && dtype != MACE_BF16 && dtype != MACE_F16)
+        return fail(MACE_EINVAL, "unknown dtype");
+
+    mace_sysmatrix *M = new mace_sysmatrix();
+    M->geo = GeoParams{geom->nx, geom->ny, geom->n_channels, geom->pixel_pitch, geom->channel_pitch,
+                       geom->channel_offset};
+    M->nz = geom->nz;
+    M->V = geom->n_views;
+    M->N = part->n_agents;
+    M->S = sv_size;
+    M->S2 = sv_size * sv_size;
+    M->nsvx = (geom->nx + sv_size - 1) / sv_size;
+    M->nsvy = (geom->ny + sv_size - 1) / sv_size;
+    M->nsv = M->nsvx * M->nsvy;
+    M->dtype = dtype;
+    M->vbytes = dtype == MACE_F32 ? 4 : 2;
+    M->stream = (cudaStream_t)cuda_stream;
+    M->view_agent.resize(M->V);
+    for (int m = 0; m < M->V; ++m) {
+        int g = part->view_agent ? part->view_agent[m] : m % M->N;
+        if (g < 0 || g >= M->N) { delete M; return fail(MACE_EINVAL, "view_agent out of range"); }
+        M->view_agent[m] = g;
+    }
+    M->view_off.assign(M->N + 1, 0);
+    for (int m = 0; m < M->V; ++m) M->view_off[M->view_agent[m] + 1]++;
+    for (int g = 0; g < M->N; ++g) {
+        if (M->view_off[g + 1] == 0) { delete M; return fail(MACE_EINVAL, "an agent has no views"); }
+        M->view_off[g + 1] += M->view_off[g];
+    }
+    M->agent_views.resize(M->V);
+    {
+        std::vector<int> fillp(M->view_off.begin(), M->view_off.end() - 1);
+        for (int m = 0; m < M->V; ++m) M->agent_views[fillp[M->view_agent[m]]++] = m;
+    }
+    M->max_views = 0;
+    for (int g = 0; g < M->N; ++g) M->max_views = std::max(M->max_views, M->view_off[g + 1] - M->view_off[g]);
+    // view angles on the host (libm), in agent order
+    M->cosv.resize(M->V);
+    M->sinv.resize(M->V);
+    std::vector<double2> cs(M->V);
+    for (int m = 0; m < M->V; ++m) {
+        double th = geom->view_angles ? geom->view_angles[m] : (double)m * M_PI / (double)M->V;
+        if (!std::isfinite(th)) { delete M; return fail(MACE_EINVAL, "non-finite view angle"); }
+        M->cosv[m] = cos(th);
+        M->sinv[m] = sin(th);
+    }
+    for (int k = 0; k < M->V; ++k) cs[k] = make_double2(M->cosv[M->agent_views[k]], M->sinv[M->agent_views[k]]);
+
+    auto cleanup = [&](int code, const std::string &msg) {
+        mace_free_sysmatrix(M);
+        return fail(code, msg);
+    };
+    cudaStream_t s = M->stream;
+    const int64_t nband = (int64_t)M->nsv * M->V;
+    const int64_t ncol = (int64_t)M->N * M->nsv * M->S2;
+    if (cudaMalloc(&M->d_cs, sizeof(double2) * M->V) != cudaSuccess ||
+        cudaMalloc(&M->d_view_off, sizeof(int) * (M->N + 1)) != cudaSuccess ||
+        cudaMalloc(&M->d_band, sizeof(uint32_t) * nband) != cudaSuccess ||
+        cudaMalloc(&M->d_band_tot, sizeof(uint32_t) * M->N * M->nsv) != cudaSuccess ||
+        cudaMalloc(&M->d_sv_base, sizeof(int64_t) * M->N * M->nsv) != cudaSuccess ||
+        cudaMalloc(&M->d_col_off, sizeof(uint32_t) * M->N * M->nsv * (M->S2 + 1)) != cudaSuccess ||
+        cudaMalloc(&M->d_sv_order, sizeof(int32_t) * M->nsv) != cudaSuccess)
+        return cleanup(MACE_ENOMEM, "cudaMalloc failed for system-matrix metadata");
+    if (cudaMemcpyAsync(M->d_cs, cs.data(), sizeof(double2) * M->V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(M->d_view_off, M->view_off.data(), sizeof(int) * (M->N + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return cleanup(MACE_ECUDA, "copy of view tables failed");
+
+    band_kernel<<<(unsigned)((nband + 255) / 256), 256, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S,
+                                                               M->nsvx, M->nsv, M->d_band);
+    uint32_t *d_bytes = nullptr, *d_nnz = nullptr;
+    if (cudaMalloc(&d_bytes, sizeof(uint32_t) * ncol) != cudaSuccess ||
+        cudaMalloc(&d_nnz, sizeof(uint32_t) * ncol) != cudaSuccess) {
+        cudaFree(d_bytes);
+        return cleanup(MACE_ENOMEM, "cudaMalloc failed for column sizes");
+    }
+    colsize_kernel<<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S,
+                                                                  M->nsvx, M->nsv, M->vbytes, d_bytes, d_nnz);
+    std::vector<uint32_t> h_bytes(ncol), h_nnz(ncol), h_band(nband);
+    cudaError_t ce = cudaMemcpyAsync(h_bytes.data(), d_bytes, sizeof(uint32_t) * ncol, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_nnz.data(), d_nnz, sizeof(uint32_t) * ncol, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_band.data(), M->d_band, sizeof(uint32_t) * nband, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(d_bytes);
+    cudaFree(d_nnz);
+    if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix size pass: ") + cudaGetErrorString(ce));
+
+    // offsets (host prefix sums; a one-off cost per geometry)
+    std::vector<int64_t> sv_base(M->N * M->nsv);
+    std::vector<uint32_t> col_off((int64_t)M->N * M->nsv * (M->S2 + 1));
+    std::vector<uint32_t> band_tot(M->N * M->nsv);
+    int64_t total = 0;
+    M->max_band = 0;
+    M->max_col_bytes = 16;
+    M->agent_bytes.assign(M->N, 0);
+    for (int g = 0; g < M->N; ++g) {
+        int Vg = M->view_off[g + 1] - M->view_off[g];
+        for (int sv = 0; sv < M->nsv; ++sv) {
+            int64_t gsv = (int64_t)g * M->nsv + sv;
+            sv_base[gsv] = total;
+            uint32_t off = 0;
+            for (int t = 0; t < M->S2; ++t) {
+                col_off[gsv * (M->S2 + 1) + t] = off;
+                uint32_t b = h_bytes[gsv * M->S2 + t];
+                off += b;
+                M->max_col_bytes = std::max<int>(M->max_col_bytes, (int)b);
+                M->nnz += h_nnz[gsv * M->S2 + t];
+            }
+            col_off[gsv * (M->S2 + 1) + M->S2] = off;
+            total += off;
+            M->agent_bytes[g] += off;
+            uint32_t bt = 0;
+            const uint32_t *bd = h_band.data() + (int64_t)M->nsv * M->view_off[g] + (int64_t)sv * Vg;
+            for (int v = 0; v < Vg; ++v) {
+                uint32_t len = bd[v] >> 16;
+                if (len > 64) return cleanup(MACE_EINVAL, "super-voxel band wider than 64 channels; use a smaller sv_size");
+                bt += len;
+            }
+            band_tot[gsv] = bt;
+            M->max_band = std::max<int>(M->max_band, (int)bt);
+        }
+    }
+    M->bytes_cols = total;
+    if (cudaMalloc(&M->d_cols, total > 0 ? total : 16) != cudaSuccess)
+        return cleanup(MACE_ENOMEM, "cudaMalloc failed for the system matrix (" + std::to_string(total) + " bytes)");
+    // super-voxel visiting order: a stride permutation that spreads consecutive
+    // super-voxels over the image (they run concurrently)
+    M->sv_order.resize(M->nsv);
+    {
+        int64_t p = std::max<int64_t>(1, (int64_t)llround(0.6180339887 * M->nsv));
+        while (std::gcd<int64_t>(p, M->nsv) != 1) ++p;
+        for (int k = 0; k < M->nsv; ++k) M->sv_order[k] = (int32_t)(((int64_t)k * p) % M->nsv);
+    }
+    ce = cudaMemcpyAsync(M->d_sv_base, sv_base.data(), sizeof(int64_t) * sv_base.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_col_off, col_off.data(), sizeof(uint32_t) * col_off.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_band_tot, band_tot.data(), sizeof(uint32_t) * band_tot.size(), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_sv_order, M->sv_order.data(), sizeof(int32_t) * M->nsv, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(M->d_cols, 0, total > 0 ? total : 16, s);
+    if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix upload: ") + cudaGetErrorString(ce));
+    if (M->dtype == MACE_F32)
+        fill_kernel<float><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
+                                                                          M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+    else if (M->dtype == MACE_BF16)
+        fill_kernel<__nv_bfloat16><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
+                                                                                  M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+    else
+        fill_kernel<__half><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
+                                                                           M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+    ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix build: ") + cudaGetErrorString(ce));
+    *out = M;
+    return MACE_OK;
+}
+
+extern "C" int mace_sysmatrix_get_info(const mace_sysmatrix *M, mace_sysmatrix_info *info)
+{
+    if (!M || !info) return fail(MACE_EINVAL, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n_voxels = (int64_t)M->geo.nx * M->geo.ny;
+    info->n_agents = M->N;
+    info->sv_size = M->S;
+    info->n_sv = M->nsv;
+    info->max_views = M->max_views;
+    info->nnz = M->nnz;
+    info->bytes_columns = M->bytes_cols;
+    info->bytes_meta = (int64_t)M->nsv * M->V * 4 + (int64_t)M->N * M->nsv * (8 + 4 + 4 * (M->S2 + 1));
+    for (int g = 0; g < M->N && g < 64; ++g) info->agent_bytes[g] = M->agent_bytes[g];
+    return MACE_OK;
+}
+
+static float value_to_float(const uint8_t *p, mace_dtype dt)
+{
+    if (dt == MACE_F32) { float f; memcpy(&f, p, 4); return f; }
+    uint16_t u; memcpy(&u, p, 2);
+    if (dt == MACE_BF16) { uint32_t b = (uint32_t)u << 16; float f; memcpy(&f, &b, 4); return f; }
+    // IEEE half -> float
+    uint32_t sgn = (u >> 15) & 1, ex = (u >> 10) & 0x1F, man = u & 0x3FF;
+    float f;
+    if (ex == 0) f = std::ldexp((float)man, -24);
+    else if (ex == 31) f = man ? NAN : INFINITY;
+    else f = std::ldexp((float)(man | 0x400), (int)ex - 25);
+    return sgn ? -f : f;
+}
+
+extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t i, int32_t j,
+                                     int32_t *c0, int32_t *len, float *vals)
+{
+    if (!M || !c0 || !len || !vals) return fail(MACE_EINVAL, "NULL argument");
+    if (g < 0 || g >= M->N || i < 0 || i >= M->geo.ny || j < 0 || j >= M->geo.nx)
+        return fail(MACE_EINVAL, "column index out of range");
+    int sv = (i / M->S) * M->nsvx + (j / M->S);
+    int t = (i % M->S) * M->S + (j % M->S);
+    int64_t gsv = (int64_t)g * M->nsv + sv;
+    int Vg = M->view_off[g + 1] - M->view_off[g];
+    int64_t base;
+    uint32_t off[2];
+    std::vector<uint32_t> bd(Vg);
+    CUDA_TRY(cudaMemcpy(&base, M->d_sv_base + gsv, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(off, M->d_col_off + gsv * (M->S2 + 1) + t, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(bd.data(), M->d_band + (int64_t)M->nsv * M->view_off[g] + (int64_t)sv * Vg,
+                        sizeof(uint32_t) * Vg, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> col(off[1] - off[0]);
+    if (!col.empty())
+        CUDA_TRY(cudaMemcpy(col.data(), M->d_cols + base + off[0], col.size(), cudaMemcpyDeviceToHost));
+    const uint8_t *vals_p = col.data() + ((Vg + 3) & ~3);
+    int base_v = 0;
+    for (int r = 0; r * 32 < Vg; ++r) {
+        int Vr = std::min(32, Vg - r * 32);
+        int n1 = 0, n2 = 0;
+        for (int l = 0; l < Vr; ++l) { int L = col[r * 32 + l] & 3; n1 += L >= 2; n2 += L == 3; }
+        int k1 = 0, k2 = 0;
+        for (int l = 0; l < Vr; ++l) {
+            int v = r * 32 + l;
+            int L = col[v] & 3, crel = col[v] >> 2;
+            len[v] = L;
+            c0[v] = L > 0 ? (int)(bd[v] & 0xFFFFu) + crel : 0;
+            vals[3 * v] = vals[3 * v + 1] = vals[3 * v + 2] = 0.f;
+            if (L >= 1) vals[3 * v] = value_to_float(vals_p + (size_t)(base_v + l) * M->vbytes, M->dtype);
+            if (L >= 2) vals[3 * v + 1] = value_to_float(vals_p + (size_t)(base_v + Vr + k1++) * M->vbytes, M->dtype);
+            if (L == 3) vals[3 * v + 2] = value_to_float(vals_p + (size_t)(base_v + Vr + n1 + k2++) * M->vbytes, M->dtype);
+        }
+        base_v += Vr + n1 + n2;
+    }
+    return MACE_OK;
+}
+
+extern "C" int mace_sysmatrix_visit_order(const mace_sysmatrix *M, int64_t *order)
+{
+    if (!M || !order) return fail(MACE_EINVAL, "NULL argument");
+    int64_t k = 0;
+    for (int q = 0; q < M->nsv; ++q) {
+        int sv = M->sv_order[q], si = sv / M->nsvx, sj = sv % M->nsvx;
+        for (int t = 0; t < M->S2; ++t) {
+            int i = si * M->S + t / M->S, j = sj * M->S + t % M->S;
+            if (i < M->geo.ny && j < M->geo.nx) order[k++] = (int64_t)i * M->geo.nx + j;
+        }
+    }
+    return MACE_OK;
+}
+
+extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
+{
+    if (!M) return;
+    cudaFree(M->d_cs);
+    cudaFree(M->d_view_off);
+    cudaFree(M->d_band);
+    cudaFree(M->d_band_tot);
+    cudaFree(M->d_sv_base);
+    cudaFree(M->d_col_off);
+    cudaFree(M->d_cols);
+    cudaFree(M->d_sv_order);
+    delete M;
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction state
+// ---------------------------------------------------------------------------
+struct mace_state {
+    const mace_sysmatrix *M;
+    mace_params P;
+    cudaStream_t stream;
+    int64_t n;                 // voxels
+    int64_t ne;                // total error-sinogram entries over agents
+    double sigma_abs;
+    float2 *d_eL = nullptr;    // (e, Lambda) per agent [V_g][D], agents concatenated
+    float *d_y = nullptr;      // y per agent, same layout
+    float *d_w = nullptr;      // [N][n]
+    float *d_X = nullptr;      // [N][n]
+    float *d_vexp = nullptr;   // [N][n] explicit v (prox-pass entry point)
+    double *d_wbar = nullptr;  // [n]
+    double *d_part = nullptr;  // [nblk_mann][2] residual partials
+    double *d_resid = nullptr; // [4]: dw2, ww2, r, flag
+    int *d_counter = nullptr;  // work counters [8]
+    int *d_status = nullptr;   // device status word
+    int nblk_mann = 0;
+    int iters = 0;
+    double last_resid = INFINITY;
+    int sweep_warps = 0, sweep_wpb = 0, concurrency = 0;
+    size_t sweep_smem = 0, warp_smem = 0;
+};
+
+struct SweepArgs {
+    const uint8_t *cols;
+    const int64_t *sv_base;
+    const uint32_t *col_off;
+    const uint32_t *band;
+    const int *view_off;
+    const int32_t *sv_order;
+    float2 *eL;
+    float *X;
+    const float *w;
+    const double *wbar;
+    const float *vexp;
+    int *counter;
+    int *status;
+    int N, nsv, nsvx, S, nx, ny, D;
+    int backward;
+    int max_band, col_stride, max_views;   // per-warp shared-memory layout
+    float inv_s2, pscale;
+    int prior;                  // 0 quadratic, 1 Q-GGMRF
+    float inv_sx2, inv_Tsx, qexp, qq;   // prior constants
+    float b_edge, b_diag;
+};
+
+// --- PTX helpers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1D TMA bulk copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
+{
+    if (A.prior == 0) return A.inv_sx2;
+    float a = __powf(fabsf(d * A.inv_Tsx), A.qexp);
+    float opa = 1.f + a;
+    return (2.f + A.qq * a) * 0.5f * A.inv_sx2 / (opa * opa);
+}
+
+template <typename T> __device__ __forceinline__ float ld_val(const uint8_t *p, int idx);
+template <> __device__ __forceinline__ float ld_val<float>(const uint8_t *p, int idx) { return ((const float *)p)[idx]; }
+template <> __device__ __forceinline__ float ld_val<__nv_bfloat16>(const uint8_t *p, int idx)
+{
+    return __bfloat162float(((const __nv_bfloat16 *)p)[idx]);
+}
+template <> __device__ __forceinline__ float ld_val<__half>(const uint8_t *p, int idx)
+{
+    return __half2float(((const __half *)p)[idx]);
+}
+
+// Per-warp shared-memory layout (bytes, each part 16-aligned):
+//   ring:   kRing * col_stride            column staging (TMA destination)
+//   bars:   kRing * 8                     mbarriers
+//   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
+//   bsnap:  max_band * 4                  e of the band when the super-voxel began
+//   bdesc:  max_views * 4                 band descriptor of each view (lo | len << 16)
+//   boff:   max_views * 2                 band offset of each view (u16)
+//   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
+//   vt:     S^2 * 4                       v tile
+struct WarpSmem {
+    size_t ring, bars, beL, bsnap, bdesc, boff, xt, vt, total;
+};
+
+__host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views)
+{
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    WarpSmem L;
+    size_t o = 0;
+    L.ring = o;  o += r16((size_t)kRing * col_stride);
+    L.bars = o;  o += r16(kRing * 8);
+    L.beL = o;   o += r16((size_t)max_band * 8);
+    L.bsnap = o; o += r16((size_t)max_band * 4);
+    L.bdesc = o; o += r16((size_t)max_views * 4);
+    L.boff = o;  o += r16((size_t)max_views * 2);
+    L.xt = o;    o += r16((size_t)(S + 2) * (S + 2) * 4);
+    L.vt = o;    o += r16((size_t)S * S * 4);
+    L.total = o;
+    return L;
+}
+
+static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views)
+{
+    return warp_smem_layout(max_band, col_stride, S, max_views).total;
+}
+
+// One warp per super-voxel at a time; lane = view (views lane, lane+32, ...).
+// MAXR > 0: the agent has at most 32*MAXR views and each lane keeps its runs
+// in registers between the reduction and the update; MAXR == 0: any number of
+// views, runs re-read from shared memory.
+template <typename T, int MAXR>
+__global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, A.S, A.max_views);
+    uint8_t *base = smem + wib * Ly.total;
+    uint8_t *ring = base + Ly.ring;
+    uint64_t *bars = (uint64_t *)(base + Ly.bars);
+    float2 *beL = (float2 *)(base + Ly.beL);
+    float *bsnap = (float *)(base + Ly.bsnap);
+    uint32_t *bdesc = (uint32_t *)(base + Ly.bdesc);
+    uint16_t *boff = (uint16_t *)(base + Ly.boff);
+    float *xt = (float *)(base + Ly.xt);
+    float *vt = (float *)(base + Ly.vt);
+
+    if (lane == 0)
+        for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+
+    const int S = A.S, S2 = S * S, T2 = S + 2;
+    uint32_t issued = 0, consumed = 0;   // ring sequence numbers (per warp)
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = (int64_t)A.nx * A.ny;
+
+    // warp w serves agent w mod N; the agent's super-voxels are handed out in
+    // visiting order through the agent's counter, so at most
+    // (warps / N) super-voxels of one agent are in flight at a time
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int g = gw % A.N;
+    const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
+    const int hdr_bytes = (Vg + 3) & ~3;
+    float2 *eLg = A.eL + (int64_t)v0 * A.D;    // agent block [Vg][D]
+    float *Xg = A.X + (int64_t)g * n;
+
+    while (true) {
+        int slot = 0;
+        if (lane == 0) {
+            slot = atomicAdd(&A.counter[g], 1);
+            if (slot < A.nsv && *((volatile int *)A.status) != 0) slot = A.nsv;
+        }
+        slot = __shfl_sync(FULL, slot, 0);
+        if (slot >= A.nsv) break;
+        if (A.backward) slot = A.nsv - 1 - slot;
+        const int sv = A.sv_order[slot];
+        const int si = sv / A.nsvx, sj = sv % A.nsvx;
+        const int64_t gsv = (int64_t)g * A.nsv + sv;
+        const uint8_t *svcols = A.cols + A.sv_base[gsv];
+        const uint32_t *coff = A.col_off + gsv * (S2 + 1);
+
+        // --- prefetch the first columns (processing order) ---------------
+        int next_issue = 0;
+        auto issue = [&](int k) {
+            int t = A.backward ? S2 - 1 - k : k;
+            uint32_t o0 = coff[t], o1 = coff[t + 1];
+            uint32_t bytes = o1 - o0;
+            if (bytes) {
+                int stg = issued % kRing;
+                if (lane == 0) {
+                    fence_proxy_async();
+                    mbar_expect_tx(&bars[stg], bytes);
+                    tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + o0, bytes, &bars[stg]);
+                }
+                ++issued;
+            }
+        };
+        while (next_issue < S2 && (int)(issued - consumed) < kRing) issue(next_issue++);
+
+        // --- band descriptors and offsets ----------------------------------
+        const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
+        int run = 0;
+        for (int r = 0; r * 32 < Vg; ++r) {
+            int v = r * 32 + lane;
+            uint32_t d = v < Vg ? bd[v] : 0u;
+            int len = (int)(d >> 16);
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (v < Vg) {
+                boff[v] = (uint16_t)(run + incl - len);
+                bdesc[v] = d;
+            }
+            run += __shfl_sync(FULL, incl, 31);
+        }
+        __syncwarp();
+        // --- band snapshot: one coalesced row per view -----------------------
+#pragma unroll 4
+        for (int v = 0; v < Vg; ++v) {
+            const uint32_t d = bdesc[v];
+            const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
+            const float2 *src = eLg + (int64_t)v * A.D + lo;
+            const int b0 = boff[v];
+            for (int k = lane; k < len; k += 32) {
+                float2 el = src[k];
+                beL[b0 + k] = el;
+                bsnap[b0 + k] = el.x;
+            }
+        }
+        // --- X tile with halo, v tile ---------------------------------------
+        for (int k = lane; k < T2 * T2; k += 32) {
+            int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
+            xt[k] = (i >= 0 && i < A.ny && j >= 0 && j < A.nx) ? Xg[(int64_t)i * A.nx + j] : 0.f;
+        }
+        for (int k = lane; k < S2; k += 32) {
+            int i = si * S + k / S, j = sj * S + k % S;
+            float vv = 0.f;
+            if (i < A.ny && j < A.nx) {
+                int64_t s = (int64_t)i * A.nx + j;
+                vv = A.vexp ? A.vexp[(int64_t)g * n + s]
+                            : (float)(2.0 * A.wbar[s] - (double)A.w[(int64_t)g * n + s]);
+            }
+            vt[k] = vv;
+        }
+        __syncwarp();
+
+        // --- visit the pixels ------------------------------------------------
+        for (int k = 0; k < S2; ++k) {
+            const int t = A.backward ? S2 - 1 - k : k;
+            const uint32_t bytes = coff[t + 1] - coff[t];
+            if (bytes == 0) continue;   // pixel outside the image
+            const int ti = t / S, tj = t % S;
+            const int i = si * S + ti, j = sj * S + tj;
+            // wait for the column
+            const int stg = consumed % kRing;
+            const uint32_t parity = (consumed / kRing) & 1u;
+            uint32_t spins = 0;
+            while (!mbar_try_wait(&bars[stg], parity)) {
+                if (++spins > kSpinLimit) {
+                    // give up: flag the host, then wait (bounded) for this
+                    // warp's copies still in flight before leaving
+                    if (lane == 0) atomicExch(A.status, kStatusTimeout);
+                    for (uint32_t q = consumed + 1; q < issued; ++q) {
+                        uint32_t sp2 = 0;
+                        while (!mbar_try_wait(&bars[q % kRing], (q / kRing) & 1u) && ++sp2 < kSpinLimit) {}
+                    }
+                    return;
+                }
+            }
+            const uint8_t *col = ring + (size_t)stg * A.col_stride;
+            const uint8_t *vals = col + hdr_bytes;
+
+            // data term: p1 = -sum A Lambda e, p2 = sum A^2 Lambda
+            float p1 = 0.f, p2 = 0.f;
+            constexpr int RC = MAXR > 0 ? MAXR : 1;
+            float ca0[RC], ca1[RC], ca2[RC];
+            int cb[RC], cL[RC];
+            int vbase = 0;
+            const int R = (Vg + 31) >> 5;
+#pragma unroll
+            for (int r = 0; r < (MAXR > 0 ? MAXR : 1 << 20); ++r) {
+                if (r >= R) break;
+                const int v = r * 32 + lane;
+                const int Vr = min(32, Vg - r * 32);
+                const uint32_t h = lane < Vr ? col[v] : 0u;
+                const int L = h & 3;
+                const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
+                const int n1 = __popc(m1);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+                int b = 0;
+                if (L > 0) {
+                    b = boff[v] + (int)(h >> 2);
+                    a0 = ld_val<T>(vals, vbase + lane);
+                    float2 el = beL[b];
+                    p1 = fmaf(-a0 * el.y, el.x, p1);
+                    p2 = fmaf(a0 * a0, el.y, p2);
+                    if (L >= 2) {
+                        a1 = ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask));
+                        el = beL[b + 1];
+                        p1 = fmaf(-a1 * el.y, el.x, p1);
+                        p2 = fmaf(a1 * a1, el.y, p2);
+                    }
+                    if (L == 3) {
+                        a2 = ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask));
+                        el = beL[b + 2];
+                        p1 = fmaf(-a2 * el.y, el.x, p1);
+                        p2 = fmaf(a2 * a2, el.y, p2);
+                    }
+                }
+                if (MAXR > 0) {
+                    ca0[r < RC ? r : 0] = a0; ca1[r < RC ? r : 0] = a1; ca2[r < RC ? r : 0] = a2;
+                    cb[r < RC ? r : 0] = b;   cL[r < RC ? r : 0] = L;
+                }
+                vbase += Vr + n1 + __popc(m2);
+            }
+            // prior through the surrogate weights (lanes 0..7: the 8 neighbours)
+            const int tc = (ti + 1) * T2 + (tj + 1);
+            const float xs = xt[tc];
+            if (lane < 8) {
+                const int kk = lane < 4 ? lane : lane + 1;   // skip the centre of the 3x3
+                const int di = kk / 3 - 1, dj = kk % 3 - 1;
+                const int ii = i + di, jj = j + dj;
+                if (ii >= 0 && ii < A.ny && jj >= 0 && jj < A.nx) {
+                    const float d = xs - xt[tc + di * T2 + dj];
+                    const float wgt = A.pscale * ((di != 0 && dj != 0) ? A.b_diag : A.b_edge) * prior_weight(A, d);
+                    p1 = fmaf(wgt, d, p1);
+                    p2 += wgt;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                p1 += __shfl_xor_sync(FULL, p1, o);
+                p2 += __shfl_xor_sync(FULL, p2, o);
+            }
+            // the step's sign and zero set come from num alone, so a fast
+            // division leaves the fixed point unchanged
+            const float num = p1 + (xs - vt[t]) * A.inv_s2;
+            const float den = p2 + A.inv_s2;
+            const float alpha = -__fdividef(num, den);
+            // update e: each lane owns its views' band rows
+            if (MAXR > 0) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    if (r >= R) break;
+                    const int L = cL[r], b = cb[r];
+                    if (L > 0) {
+                        beL[b].x = fmaf(-ca0[r], alpha, beL[b].x);
+                        if (L >= 2) beL[b + 1].x = fmaf(-ca1[r], alpha, beL[b + 1].x);
+                        if (L == 3) beL[b + 2].x = fmaf(-ca2[r], alpha, beL[b + 2].x);
+                    }
+                }
+            } else {
+                vbase = 0;
+                for (int r = 0; r < R; ++r) {
+                    const int v = r * 32 + lane;
+                    const int Vr = min(32, Vg - r * 32);
+                    const uint32_t h = lane < Vr ? col[v] : 0u;
+                    const int L = h & 3;
+                    const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
+                    const int n1 = __popc(m1);
+                    if (L > 0) {
+                        const int b = boff[v] + (int)(h >> 2);
+                        beL[b].x = fmaf(-ld_val<T>(vals, vbase + lane), alpha, beL[b].x);
+                        if (L >= 2)
+                            beL[b + 1].x = fmaf(-ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask)), alpha, beL[b + 1].x);
+                        if (L == 3)
+                            beL[b + 2].x = fmaf(-ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask)), alpha, beL[b + 2].x);
+                    }
+                    vbase += Vr + n1 + __popc(m2);
+                }
+            }
+            if (lane == 0) xt[tc] = xs + alpha;
+            ++consumed;
+            __syncwarp();
+            // refill the ring slot just freed
+            while (next_issue < S2 && (int)(issued - consumed) < kRing) issue(next_issue++);
+        }
+
+        // --- write back: X tile and the change of e (one row per view) ------
+        for (int k = lane; k < S2; k += 32) {
+            int i = si * S + k / S, j = sj * S + k % S;
+            if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(k / S + 1) * T2 + (k % S + 1)];
+        }
+#pragma unroll 4
+        for (int v = 0; v < Vg; ++v) {
+            const uint32_t d = bdesc[v];
+            const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
+            float2 *dst = eLg + (int64_t)v * A.D + lo;
+            const int b0 = boff[v];
+            for (int k = lane; k < len; k += 32) {
+                const float de = beL[b0 + k].x - bsnap[b0 + k];
+                if (de != 0.f) atomicAdd(&dst[k].x, de);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// --- consensus (G), Mann, residual ------------------------------------------
+__global__ void consensus_kernel(const float *__restrict__ w, int N, int64_t n, double *__restrict__ wbar,
+                                 float *__restrict__ xout)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double acc = 0.0;
+    for (int g = 0; g < N; ++g) acc += (double)w[(int64_t)g * n + s];
+    double m = acc / (double)N;
+    if (wbar) wbar[s] = m;
+    if (xout) xout[s] = (float)m;
+}
+
+__global__ void __launch_bounds__(256) mann_kernel(float *__restrict__ w, const float *__restrict__ X,
+                                                   const double *__restrict__ wbar, int N, int64_t n, float rho,
+                                                   double *__restrict__ part)
+{
+    __shared__ double sh[2][8];
+    double d2 = 0.0, w2 = 0.0;
+    const int64_t total = (int64_t)N * n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = k % n;
+        float wo = w[k];
+        float v = (float)(2.0 * wbar[s] - (double)wo);
+        float wn = rho * (2.f * X[k] - v) + (1.f - rho) * wo;
+        w[k] = wn;
+        double d = (double)wn - (double)wo;
+        d2 += d * d;
+        w2 += (double)wn * (double)wn;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        w2 += __shfl_down_sync(0xffffffffu, w2, o);
+    }
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][wid] = d2; sh[1][wid] = w2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sh[0][k]; b += sh[1][k]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void residual_kernel(const double *__restrict__ part, int nblk, double *__restrict__ out)
+{
+    // one thread: fixed-order sum of the block partials
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblk; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }
+    out[0] = a;
+    out[1] = b;
+    out[2] = b > 0.0 ? sqrt(a / b) : sqrt(a);
+}
+
+// --- error sinogram: e = y - A X ---------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
+                                                      const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
+                                                      const int *__restrict__ view_off, float2 *__restrict__ eL,
+                                                      const float *__restrict__ X, int N, int nsv, int nsvx, int S, int nx,
+                                                      int ny, int D)
+{
+    // one warp per (agent, super-voxel); lane = view; e must hold y on entry
+    const int lane = threadIdx.x & 31;
+    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (item >= (int64_t)N * nsv) return;
+    const int g = (int)(item / nsv), sv = (int)(item % nsv);
+    const int si = sv / nsvx, sj = sv % nsvx, S2 = S * S;
+    const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
+    const int64_t gsv = (int64_t)g * nsv + sv;
+    const uint8_t *svcols = cols + sv_base[gsv];
+    const uint32_t *coff = col_off + gsv * (S2 + 1);
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    const int hdr_bytes = (Vg + 3) & ~3;
+    float2 *eLg = eL + (int64_t)v0 * D;
+    const float *Xg = X + (int64_t)g * nx * ny;
+    const unsigned FULL = 0xffffffffu, lt_mask = (1u << lane) - 1u;
+    for (int t = 0; t < S2; ++t) {
+        if (coff[t + 1] == coff[t]) continue;
+        const int i = si * S + t / S, j = sj * S + t % S;
+        const float xs = Xg[(int64_t)i * nx + j];
+        const uint8_t *col = svcols + coff[t];
+        const uint8_t *vals = col + hdr_bytes;
+        int vbase = 0;
+        for (int r = 0; r * 32 < Vg; ++r) {
+            const int v = r * 32 + lane;
+            const int Vr = min(32, Vg - r * 32);
+            const uint32_t h = lane < Vr ? col[v] : 0u;
+            const int L = h & 3, c = h >> 2;
+            const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
+            const int n1 = __popc(m1);
+            if (L > 0 && xs != 0.f) {
+                float2 *row = eLg + (int64_t)v * D + (int)(bd[v] & 0xFFFFu) + c;
+                atomicAdd(&row[0].x, -ld_val<T>(vals, vbase + lane) * xs);
+                if (L >= 2) atomicAdd(&row[1].x, -ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask)) * xs);
+                if (L == 3) atomicAdd(&row[2].x, -ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask)) * xs);
+            }
+            vbase += Vr + n1 + __popc(m2);
+        }
+    }
+}
+
+__global__ void pack_kernel(const float *__restrict__ y, const float *__restrict__ lam, const int *__restrict__ agent_view,
+                            int V, int D, float2 *__restrict__ eL, float *__restrict__ yg)
+{
+    // agent-ordered row k holds view agent_view[k]
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)V * D) return;
+    int k = (int)(tid / D), c = (int)(tid % D);
+    int m = agent_view[k];
+    float yy = y[(int64_t)m * D + c];
+    eL[tid] = make_float2(yy, lam[(int64_t)m * D + c]);
+    yg[tid] = yy;
+}
+
+__global__ void reset_error_kernel(const float *__restrict__ yg, float2 *__restrict__ eL, int64_t ne)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ne) eL[k].x = yg[k];
+}
+
+__global__ void broadcast_kernel(const double *__restrict__ wbar, float *__restrict__ X, int N, int64_t n)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < (int64_t)N * n) X[k] = (float)wbar[k % n];
+}
+
+__global__ void check_weights_kernel(const float *__restrict__ y, const float *__restrict__ lam, int64_t m, int *bad)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    float a = y[k], b = lam[k];
+    if (!isfinite(a) || !isfinite(b) || b < 0.f) atomicOr(bad, 1);
+}
+
+__device__ __forceinline__ float ld_any(const uint8_t *p, int idx, int dtype)
+{
+    if (dtype == MACE_F32) return ld_val<float>(p, idx);
+    if (dtype == MACE_BF16) return ld_val<__nv_bfloat16>(p, idx);
+    return ld_val<__half>(p, idx);
+}
+
+__global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
+                                  const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
+                                  const int *__restrict__ view_off, const float2 *__restrict__ eL, int N, int nsv,
+                                  int S, int D, int dtype, double *__restrict__ out)
+{
+    // sum over all agents and voxels of sum_{k in J_i} A^2 Lambda (FP64), for
+    // the normalised sigma; one warp per (agent, super-voxel)
+    const int lane = threadIdx.x & 31;
+    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (item >= (int64_t)N * nsv) return;
+    const int g = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
+    const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
+    const int64_t gsv = (int64_t)g * nsv + sv;
+    const uint32_t *coff = col_off + gsv * (S2 + 1);
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    const unsigned FULL = 0xffffffffu, lt_mask = (1u << lane) - 1u;
+    double acc = 0.0;
+    for (int t = 0; t < S2; ++t) {
+        if (coff[t + 1] == coff[t]) continue;
+        const uint8_t *col = cols + sv_base[gsv] + coff[t];
+        const uint8_t *vals = col + ((Vg + 3) & ~3);
+        int vbase = 0;
+        for (int r = 0; r * 32 < Vg; ++r) {
+            const int v = r * 32 + lane;
+            const int Vr = min(32, Vg - r * 32);
+            const uint32_t h = lane < Vr ? col[v] : 0u;
+            const int L = h & 3, c = h >> 2;
+            const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
+            const int n1 = __popc(m1);
+            if (L > 0) {
+                const float2 *row = eL + (int64_t)(v0 + v) * D + (int)(bd[v] & 0xFFFFu) + c;
+                const int i0 = vbase + lane, i1 = vbase + Vr + __popc(m1 & lt_mask),
+                          i2 = vbase + Vr + n1 + __popc(m2 & lt_mask);
+                float a0 = ld_any(vals, i0, dtype);
+                float a1 = L >= 2 ? ld_any(vals, i1, dtype) : 0.f;
+                float a2 = L == 3 ? ld_any(vals, i2, dtype) : 0.f;
+                acc += (double)a0 * a0 * row[0].y;
+                if (L >= 2) acc += (double)a1 * a1 * row[1].y;
+                if (L == 3) acc += (double)a2 * a2 * row[2].y;
+            }
+            vbase += Vr + n1 + __popc(m2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+    if (lane == 0) atomicAdd(out, acc);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int launch_forward(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    int64_t items = (int64_t)M->N * M->nsv;
+    unsigned blocks = (unsigned)((items * 32 + 255) / 256);
+    reset_error_kernel<<<(unsigned)((st->ne + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, st->ne);
+    switch (M->dtype) {
+    case MACE_F32:
+        forward_kernel<float><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
+                                                              st->d_eL, st->d_X, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                              M->geo.ny, M->geo.D);
+        break;
+    case MACE_BF16:
+        forward_kernel<__nv_bfloat16><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band,
+                                                                      M->d_view_off, st->d_eL, st->d_X, M->N, M->nsv, M->nsvx,
+                                                                      M->S, M->geo.nx, M->geo.ny, M->geo.D);
+        break;
+    default:
+        forward_kernel<__half><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
+                                                               st->d_eL, st->d_X, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                               M->geo.ny, M->geo.D);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MACE_OK;
+}
+
+typedef void (*sweep_fn)(SweepArgs);
+
+static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M)
+{
+    const bool small = M->max_views <= 64;
+    switch (M->dtype) {
+    case MACE_F32: return small ? icd_sweep_kernel<float, 2> : icd_sweep_kernel<float, 0>;
+    case MACE_BF16: return small ? icd_sweep_kernel<__nv_bfloat16, 2> : icd_sweep_kernel<__nv_bfloat16, 0>;
+    default: return small ? icd_sweep_kernel<__half, 2> : icd_sweep_kernel<__half, 0>;
+    }
+}
+
+static int launch_sweep(mace_state *st, int backward, const float *vexp)
+{
+    const mace_sysmatrix *M = st->M;
+    SweepArgs A;
+    A.cols = M->d_cols;
+    A.sv_base = M->d_sv_base;
+    A.col_off = M->d_col_off;
+    A.band = M->d_band;
+    A.view_off = M->d_view_off;
+    A.sv_order = M->d_sv_order;
+    A.eL = st->d_eL;
+    A.X = st->d_X;
+    A.w = st->d_w;
+    A.wbar = st->d_wbar;
+    A.vexp = vexp;
+    A.counter = st->d_counter;
+    A.status = st->d_status;
+    A.N = M->N;
+    A.nsv = M->nsv;
+    A.nsvx = M->nsvx;
+    A.S = M->S;
+    A.nx = M->geo.nx;
+    A.ny = M->geo.ny;
+    A.D = M->geo.D;
+    A.backward = backward;
+    A.max_band = M->max_band;
+    A.col_stride = (M->max_col_bytes + 15) & ~15;
+    A.max_views = M->max_views;
+    A.inv_s2 = (float)(1.0 / (st->sigma_abs * st->sigma_abs));
+    A.pscale = (float)(st->P.beta / (double)M->N);
+    A.prior = st->P.prior;
+    A.inv_sx2 = (float)(1.0 / (st->P.sigma_x * st->P.sigma_x));
+    A.inv_Tsx = (float)(1.0 / (st->P.T * st->P.sigma_x));
+    A.qexp = (float)(st->P.p - st->P.q);
+    A.qq = (float)st->P.q;
+    double bsum = 4.0 + 4.0 / std::sqrt(2.0);
+    A.b_edge = (float)(1.0 / bsum);
+    A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
+    CUDA_TRY(cudaMemsetAsync(st->d_counter, 0, sizeof(int) * M->N, st->stream));
+    dim3 grid(st->sweep_warps / st->sweep_wpb), block(32 * st->sweep_wpb);
+    sweep_kernel_ptr(M)<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    CUDA_TRY(cudaGetLastError());
+    return MACE_OK;
+}
+
+static int configure_sweep(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    int nsm = 0, max_smem = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int col_stride = (M->max_col_bytes + 15) & ~15;
+    st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views);
+    int wpb = (int)std::min<size_t>(8, (size_t)max_smem / st->warp_smem);
+    if (wpb < 1) return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
+    st->sweep_wpb = wpb;
+    st->sweep_smem = st->warp_smem * wpb;
+    sweep_fn fn = sweep_kernel_ptr(M);
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->sweep_smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, st->sweep_smem));
+    if (per_sm < 1) per_sm = 1;
+    // concurrency C super-voxels per agent: N * C warps, all resident
+    int64_t capacity = (int64_t)per_sm * nsm * wpb;
+    int64_t C = capacity / M->N;
+    if (C < 1) C = 1;
+    if (st->P.concurrency > 0) C = std::min<int64_t>(C, st->P.concurrency);
+    C = std::min<int64_t>(C, M->nsv);
+    int64_t warps = C * M->N;
+    if (warps > capacity) return fail(MACE_EINVAL, "more agents than resident warps; lower n_agents");
+    // whole blocks of wpb warps; the last block may be smaller, so pick the
+    // largest wpb <= configured that divides the warp count
+    int w = std::min<int64_t>(wpb, warps);
+    while (warps % w) --w;
+    st->sweep_wpb = w;
+    st->sweep_smem = st->warp_smem * w;
+    st->sweep_warps = (int)warps;
+    st->concurrency = (int)C;
+    return MACE_OK;
+}
+
+static int check_params(const mace_params *P)
+{
+    if (!P) return fail(MACE_EINVAL, "params is NULL");
+    if (P->prior != 0 && P->prior != 1) return fail(MACE_EINVAL, "prior must be 0 (quadratic) or 1 (Q-GGMRF)");
+    if (P->neighbourhood != 8) return fail(MACE_EINVAL, "neighbourhood must be 8 for 2D");
+    if (!(P->beta >= 0) || !(P->sigma_x > 0) || !std::isfinite(P->beta) || !std::isfinite(P->sigma_x))
+        return fail(MACE_EINVAL, "beta must be >= 0 and sigma_x > 0");
+    if (P->prior == 1 && (P->p != 2.0 || !(P->q >= 1.0 && P->q <= 2.0) || !(P->T > 0)))
+        return fail(MACE_EINVAL, "Q-GGMRF needs p == 2, 1 <= q <= 2, T > 0");
+    if (!(P->sigma > 0) || !std::isfinite(P->sigma)) return fail(MACE_EINVAL, "sigma must be positive");
+    if (P->sigma_mode != 0 && P->sigma_mode != 1) return fail(MACE_EINVAL, "sigma_mode must be 0 or 1");
+    if (!(P->rho > 0 && P->rho < 1)) return fail(MACE_EINVAL, "rho must be in (0, 1)");
+    if (P->sweeps_per_iter < 1 || P->sweeps_per_iter > 64) return fail(MACE_EINVAL, "sweeps_per_iter must be in [1, 64]");
+    if (P->recompute_every < 0) return fail(MACE_EINVAL, "recompute_every must be >= 0");
+    if (P->max_iter < 0) return fail(MACE_EINVAL, "max_iter must be >= 0");
+    if (!(P->tol >= 0)) return fail(MACE_EINVAL, "tol must be >= 0");
+    if (P->concurrency < 0) return fail(MACE_EINVAL, "concurrency must be >= 0");
+    return MACE_OK;
+}
+
+extern "C" void mace_free_state(mace_state *st)
+{
+    if (!st) return;
+    cudaFree(st->d_eL);
+    cudaFree(st->d_y);
+    cudaFree(st->d_w);
+    cudaFree(st->d_X);
+    cudaFree(st->d_vexp);
+    cudaFree(st->d_wbar);
+    cudaFree(st->d_part);
+    cudaFree(st->d_resid);
+    cudaFree(st->d_counter);
+    cudaFree(st->d_status);
+    delete st;
+}
+
+static int copy_in(void *dst, const void *src, size_t bytes, int is_dev, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (!is_dev) CUDA_TRY(cudaStreamSynchronize(s));
+    return MACE_OK;
+}
+
+static int copy_out(void *dst, const void *src, size_t bytes, int is_dev, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!is_dev) CUDA_TRY(cudaStreamSynchronize(s));
+    return MACE_OK;
+}
+
+static int set_X_from_w(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, st->d_wbar, nullptr);
+    broadcast_kernel<<<(unsigned)((M->N * st->n + 255) / 256), 256, 0, st->stream>>>(st->d_wbar, st->d_X, M->N, st->n);
+    CUDA_TRY(cudaGetLastError());
+    return MACE_OK;
+}
+
+extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *weights, int32_t ptr_is_device,
+                         const mace_params *params, const float *w0, void *cuda_stream, mace_state **out)
+{
+    if (!out) return fail(MACE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!M || !y || !weights) return fail(MACE_EINVAL, "NULL sysmatrix, y or weights");
+    int rc = check_params(params);
+    if (rc) return rc;
+    mace_state *st = new mace_state();
+    st->M = M;
+    st->P = *params;
+    st->stream = (cudaStream_t)cuda_stream;
+    st->n = (int64_t)M->geo.nx * M->geo.ny;
+    st->ne = (int64_t)M->V * M->geo.D;
+    const int64_t NN = (int64_t)M->N * st->n;
+    auto bail = [&](int code, const std::string &msg) {
+        mace_free_state(st);
+        return fail(code, msg);
+    };
+    if (cudaMalloc(&st->d_eL, sizeof(float2) * st->ne) != cudaSuccess ||
+        cudaMalloc(&st->d_y, sizeof(float) * st->ne) != cudaSuccess ||
+        cudaMalloc(&st->d_w, sizeof(float) * NN) != cudaSuccess ||
+        cudaMalloc(&st->d_X, sizeof(float) * NN) != cudaSuccess ||
+        cudaMalloc(&st->d_wbar, sizeof(double) * st->n) != cudaSuccess ||
+        cudaMalloc(&st->d_resid, sizeof(double) * 4) != cudaSuccess ||
+        cudaMalloc(&st->d_counter, sizeof(int) * M->N) != cudaSuccess ||
+        cudaMalloc(&st->d_status, sizeof(int)) != cudaSuccess)
+        return bail(MACE_ENOMEM, "cudaMalloc failed for the reconstruction state");
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    st->nblk_mann = std::max(1, std::min<int>(nsm * 4, (int)((NN + 255) / 256)));
+    if (cudaMalloc(&st->d_part, sizeof(double) * 2 * st->nblk_mann) != cudaSuccess)
+        return bail(MACE_ENOMEM, "cudaMalloc failed for residual partials");
+    cudaStream_t s = st->stream;
+    // inputs: stage on the device, validate, pack agent-major
+    float *d_yin = nullptr, *d_lin = nullptr;
+    const int64_t m = st->ne;
+    if (ptr_is_device) {
+        d_yin = (float *)y;
+        d_lin = (float *)weights;
+    } else {
+        if (cudaMalloc(&d_yin, sizeof(float) * m) != cudaSuccess || cudaMalloc(&d_lin, sizeof(float) * m) != cudaSuccess) {
+            cudaFree(d_yin);
+            return bail(MACE_ENOMEM, "cudaMalloc failed for input staging");
+        }
+        if (cudaMemcpyAsync(d_yin, y, sizeof(float) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_lin, weights, sizeof(float) * m, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaFree(d_yin);
+            cudaFree(d_lin);
+            return bail(MACE_ECUDA, "copy of y / weights failed");
+        }
+    }
+    int *d_av = nullptr;
+    int bad = 0;
+    cudaError_t ce = cudaMalloc(&d_av, sizeof(int) * M->V);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_av, M->agent_views.data(), sizeof(int) * M->V, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
+    if (ce == cudaSuccess) {
+        check_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, m, st->d_status);
+        pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, d_av, M->V, M->geo.D, st->d_eL, st->d_y);
+        ce = cudaMemcpyAsync(&bad, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(d_av);
+    if (!ptr_is_device) { cudaFree(d_yin); cudaFree(d_lin); }
+    if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("input packing: ") + cudaGetErrorString(ce));
+    if (bad) return bail(MACE_EINVAL, "y and weights must be finite and weights >= 0");
+    CUDA_TRY(cudaMemsetAsync(st->d_status, 0, sizeof(int), s));
+    // w^(0), X^(0) = G(w^(0)), e = y - A X
+    if (w0) {
+        rc = copy_in(st->d_w, w0, sizeof(float) * NN, ptr_is_device, s);
+        if (rc) { mace_free_state(st); return rc; }
+    } else if (cudaMemsetAsync(st->d_w, 0, sizeof(float) * NN, s) != cudaSuccess) {
+        return bail(MACE_ECUDA, "memset w");
+    }
+    rc = set_X_from_w(st);
+    if (rc == MACE_OK) rc = launch_forward(st);
+    if (rc) { mace_free_state(st); return rc; }
+    // sigma in image units
+    if (params->sigma_mode == 1) {
+        double *d_t2 = nullptr;
+        double h_t2 = 0.0;
+        ce = cudaMalloc(&d_t2, sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(d_t2, 0, sizeof(double), s);
+        if (ce == cudaSuccess) {
+            int64_t items = (int64_t)M->N * M->nsv;
+            theta2_sum_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
+                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, M->N, M->nsv, M->S,
+                M->geo.D, (int)M->dtype, d_t2);
+            ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
+        }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        cudaFree(d_t2);
+        if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("theta2: ") + cudaGetErrorString(ce));
+        double mean_t2 = h_t2 / ((double)M->N * (double)st->n);
+        if (!(mean_t2 > 0)) return bail(MACE_EINVAL, "all weights are zero");
+        st->sigma_abs = params->sigma / std::sqrt(mean_t2);
+    } else {
+        st->sigma_abs = params->sigma;
+    }
+    rc = configure_sweep(st);
+    if (rc) { mace_free_state(st); return rc; }
+    ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("init: ") + cudaGetErrorString(ce));
+    *out = st;
+    return MACE_OK;
+}
+
+static int run_iteration(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, st->d_wbar, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
+        int rc = launch_sweep(st, st->P.symmetric ? (k & 1) : 0, nullptr);
+        if (rc) return rc;
+    }
+    mann_kernel<<<st->nblk_mann, 256, 0, st->stream>>>(st->d_w, st->d_X, st->d_wbar, M->N, st->n, (float)st->P.rho,
+                                                       st->d_part);
+    residual_kernel<<<1, 32, 0, st->stream>>>(st->d_part, st->nblk_mann, st->d_resid);
+    CUDA_TRY(cudaGetLastError());
+    st->iters++;
+    if (st->P.recompute_every > 0 && st->iters % st->P.recompute_every == 0) return launch_forward(st);
+    return MACE_OK;
+}
+
+static int read_status(mace_state *st, double *r)
+{
+    double h[4];
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(h, st->d_resid, sizeof(double) * 3, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+    *r = h[2];
+    st->last_resid = h[2];
+    if (!std::isfinite(h[2])) return fail(MACE_ENUMERIC, "non-finite Mann residual (divergence)");
+    return MACE_OK;
+}
+
+extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out, int32_t *converged_out)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    if (n_iters < 0) return fail(MACE_EINVAL, "n_iters must be >= 0");
+    for (int k = 0; k < n_iters; ++k) {
+        int rc = run_iteration(st);
+        if (rc) return rc;
+    }
+    double r = st->last_resid;
+    if (n_iters > 0) {
+        int rc = read_status(st, &r);
+        if (rc) return rc;
+    }
+    if (residual_out) *residual_out = r;
+    if (converged_out) *converged_out = r < st->P.tol ? 1 : 0;
+    return MACE_OK;
+}
+
+extern "C" int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device)
+{
+    if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
+    const mace_sysmatrix *M = st->M;
+    float *d_x = ptr_is_device ? x_out : nullptr;
+    if (!d_x && cudaMalloc(&d_x, sizeof(float) * st->n) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc x");
+    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, nullptr, d_x);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess && !ptr_is_device) {
+        ce = cudaMemcpyAsync(x_out, d_x, sizeof(float) * st->n, cudaMemcpyDeviceToHost, st->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st->stream);
+    }
+    if (!ptr_is_device) cudaFree(d_x);
+    if (ce != cudaSuccess) return fail(MACE_ECUDA, std::string("consensus: ") + cudaGetErrorString(ce));
+    return MACE_OK;
+}
+
+extern "C" int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device, int32_t *iters_out,
+                                double *residual_out)
+{
+    if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
+    const int check = 10;
+    double r = st->last_resid;
+    int run = 0;
+    bool conv = false;
+    while (run < st->P.max_iter) {
+        int chunk = std::min(check, st->P.max_iter - run);
+        int32_t c = 0;
+        int rc = mace_iterate(st, chunk, &r, &c);
+        if (rc) return rc;
+        run += chunk;
+        if (c) { conv = true; break; }
+    }
+    int rc = mace_consensus(st, x_out, ptr_is_device);
+    if (rc) return rc;
+    if (iters_out) *iters_out = run;
+    if (residual_out) *residual_out = r;
+    if (!conv) return fail(MACE_ENOTCONVERGED, "max_iter reached before tol");
+    return MACE_OK;
+}
+
+extern "C" int mace_get_state(mace_state *st, float *w, float *X, int32_t ptr_is_device)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    size_t bytes = sizeof(float) * st->M->N * st->n;
+    if (w) { int rc = copy_out(w, st->d_w, bytes, ptr_is_device, st->stream); if (rc) return rc; }
+    if (X) { int rc = copy_out(X, st->d_X, bytes, ptr_is_device, st->stream); if (rc) return rc; }
+    return MACE_OK;
+}
+
+extern "C" int mace_set_state(mace_state *st, const float *w, const float *X, int32_t ptr_is_device)
+{
+    if (!st || !w || !X) return fail(MACE_EINVAL, "NULL argument");
+    size_t bytes = sizeof(float) * st->M->N * st->n;
+    int rc = copy_in(st->d_w, w, bytes, ptr_is_device, st->stream);
+    if (!rc) rc = copy_in(st->d_X, X, bytes, ptr_is_device, st->stream);
+    if (!rc) rc = launch_forward(st);
+    if (!rc) {
+        st->last_resid = INFINITY;
+        CUDA_TRY(cudaStreamSynchronize(st->stream));
+    }
+    return rc;
+}
+
+extern "C" int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_device, int32_t backward)
+{
+    if (!st || !v) return fail(MACE_EINVAL, "NULL argument");
+    size_t bytes = sizeof(float) * st->M->N * st->n;
+    if (!st->d_vexp && cudaMalloc(&st->d_vexp, bytes) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc v");
+    int rc = copy_in(st->d_vexp, v, bytes, ptr_is_device, st->stream);
+    if (!rc) rc = launch_sweep(st, backward ? 1 : 0, st->d_vexp);
+    if (!rc) {
+        int status = 0;
+        CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+        CUDA_TRY(cudaStreamSynchronize(st->stream));
+        if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+    }
+    return rc;
+}
+
+extern "C" int64_t mace_error_size(const mace_state *st) { return st ? st->ne : -1; }
+
+extern "C" int mace_get_error(mace_state *st, float *e, int32_t ptr_is_device)
+{
+    if (!st || !e) return fail(MACE_EINVAL, "NULL argument");
+    // strided copy of the .x components
+    CUDA_TRY(cudaMemcpy2DAsync(e, sizeof(float), st->d_eL, sizeof(float2), sizeof(float), st->ne,
+                               ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return MACE_OK;
+}
+
+extern "C" int mace_recompute_error(mace_state *st)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    int rc = launch_forward(st);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return MACE_OK;
+}
+
+extern "C" int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs, double *last_residual,
+                              int32_t *concurrency)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    if (concurrency) *concurrency = st->concurrency;
+    if (iters) *iters = st->iters;
+    if (sigma_abs) *sigma_abs = st->sigma_abs;
+    if (last_residual) *last_residual = st->last_resid;
+    return MACE_OK;
+}
