@@ -1,0 +1,355 @@
+"""Benchmark: MACE reconstructions per second on the 512^2 / 720-view /
+725-channel / 16-agent Q-GGMRF workload, on one or more GB300s.
+
+A step is one complete partial-update MACE reconstruction (Algorithm 1, the
+ICD sweeps of Algorithm 2, the FP64 consensus and the Mann update, iterated
+to the Mann-residual tolerance) of a batch of B synthetic scans that share
+the stored system matrix.  `value` counts reconstructions per second with the
+inputs already in HBM; `e2e` repeats the measurement through the same C-ABI
+call with host buffers (pinned-host -> device copies of y and Lambda before,
+device -> host copy of the images after, inside the timed region).
+
+--impl reference times the FP64 CPU oracle instead (bounded sample, host
+cores).  Under torchrun every rank runs its own independent batch (replicas;
+no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
+                     "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
+                n=512, n_views=720, n_channels=725, n_agents=16)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(batch, rank):
+    import synth
+    ys, ls = [], []
+    for b in range(batch):
+        c = synth.make_case(n=WORKLOAD["n"], n_views=WORKLOAD["n_views"], n_channels=WORKLOAD["n_channels"],
+                            I0=2e4, mu_max=0.02 * 64 / WORKLOAD["n"], seed=2 + 1000 * rank + 7 * b,
+                            noise_seed=102 + 1000 * rank + 7 * b)
+        ys.append(c["y"][0])
+        ls.append(c["lam"][0])
+    y = np.stack(ys).astype(np.float32)
+    lam = np.stack(ls).astype(np.float32)
+    return y, lam
+
+
+def solver_params(mace, sigma_x, args):
+    return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=0.8,
+                            sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
+                            tol=args.tol, concurrency=args.concurrency, sv_order=0)
+
+
+def run_mace(args, rank, world):
+    import torch
+    import synth
+    import paper_1911_09278_gb300 as mace
+    from paper_1911_09278_gb300 import build as gbuild
+
+    gbuild.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B = args.batch
+    y, lam = make_inputs(B, rank)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    stream = torch.cuda.Stream()
+    sm = mace.mace_build_sysmatrix(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"],
+                                   WORKLOAD["n_agents"], sv_size=args.sv, dtype=args.dtype, stream=stream)
+    info = sm.info()
+    prm = solver_params(mace, sx, args)
+    d_y = torch.from_numpy(y).cuda()
+    d_l = torch.from_numpy(lam).cuda()
+    d_x = torch.empty((B, WORKLOAD["n"], WORKLOAD["n"]), device="cuda", dtype=torch.float32)
+    h_y = torch.from_numpy(y).pin_memory()
+    h_l = torch.from_numpy(lam).pin_memory()
+    h_x = torch.empty((B, WORKLOAD["n"], WORKLOAD["n"]), dtype=torch.float32).pin_memory()
+
+    iters_seen = []
+    timing = {"ms": 0.0, "launches": 0}
+
+    def step(device_inputs, record):
+        if device_inputs:
+            st = mace.mace_init(sm, d_y, d_l, prm, stream=stream, batch=B)
+        else:
+            dy = torch.empty_like(d_y)
+            dl = torch.empty_like(d_l)
+            with torch.cuda.stream(stream):
+                dy.copy_(h_y, non_blocking=True)
+                dl.copy_(h_l, non_blocking=True)
+            st = mace.mace_init(sm, dy, dl, prm, stream=stream, batch=B)
+        if record:
+            st.set_timing(True, max_launches=2 * args.max_iter + 8)
+        x, it, r, conv = st.reconstruct(out=d_x)
+        if not device_inputs:
+            with torch.cuda.stream(stream):
+                h_x.copy_(d_x, non_blocking=True)
+        if record:
+            ms, n = st.get_timing()
+            timing["ms"] += ms
+            timing["launches"] += n
+        iters_seen.append((it, r, conv))
+        st.close()
+
+    def timed(device_inputs, record):
+        for _ in range(args.warmup):
+            step(device_inputs, False)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(device_inputs, record)
+        ev1.record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        dev_s = ev0.elapsed_time(ev1) / 1000.0
+        el = max(dev_s, wall)
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        return el, ck
+
+    el, clocks = timed(True, True)
+    iters_main = [it for it, _, _ in iters_seen[-args.steps:]]
+    conv_main = all(c for _, _, c in iters_seen[-args.steps:])
+    el_e2e, _ = timed(False, False)
+    recons = B * args.steps * world
+    value = recons / el
+    e2e = recons / el_e2e
+    hbm, peak_kind = peaks()
+    # roofline of the ICD sweep kernel: algorithmic bytes per launch = the
+    # stored matrix once + per reconstruction the state it reads and writes
+    n = WORKLOAD["n"] ** 2
+    N = WORKLOAD["n_agents"]
+    per_recon = N * n * (4 + 4 + 4) + n * 8 + 2 * WORKLOAD["n_views"] * WORKLOAD["n_channels"] * 8
+    alg_bytes = info["bytes_columns"] + B * per_recon
+    avg_launch_s = (timing["ms"] / 1000.0) / max(1, timing["launches"])
+    achieved = alg_bytes / avg_launch_s / 1e9 if timing["launches"] else None
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(tf):
+        try:
+            with open(tf) as f:
+                tt = json.load(f)
+            if tt.get("batch") == B and tt.get("sv") == args.sv and tt.get("dtype") == args.dtype:
+                traffic = tt.get("bytes_per_launch")
+        except Exception:
+            pass
+    out = {
+        "metric": "recons/sec at oracle-matched RMSE",
+        "value": value,
+        "unit": "recons/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * el / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.dtype == "f32" else args.dtype + "-A/f32",
+        "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Poisson counts)",
+        "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv,
+                   "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma,
+                   "tol": args.tol, "iterations": iters_main, "converged": conv_main,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (stored matrix %.2f GB)" % (info["bytes_columns"] / 1e9)},
+        "e2e": {"value": e2e, "unit": "recons/s",
+                "h2d_bytes_per_step": int(2 * y.nbytes), "d2h_bytes_per_step": int(B * n * 4)},
+        "gpu_launches": None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "icd_sweep_kernel",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0},
+        "clocks": clocks,
+    }
+    # kernel launches inside one timed step: init (check, pack, consensus,
+    # broadcast, reset, forward, theta2) + per iteration (consensus, 2 sweeps,
+    # mann, residual) + recompute every 10 iterations (reset, forward) + output
+    its = sum(iters_main)
+    out["gpu_launches"] = int(args.steps * 7 + its * 5 + 2 * (its // 10) + args.steps)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, seconds=args.cpu_seconds)
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(args, y, lam, sx, seconds=20.0):
+    """The FP64 oracle (Algorithm 1 with the same solver settings, serial ICD
+    order, one OpenMP thread per agent) on the host cores: time a bounded
+    number of Mann iterations, scale to the iterations the oracle needs."""
+    import oracle
+    threads = os.cpu_count() or 1
+    P = oracle.Problem(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"], y, lam,
+                       n_agents=WORKLOAD["n_agents"], prior="qggmrf", sigma_x=sx)
+    t2 = oracle.mean_theta2(P)
+    sigma = args.sigma / math.sqrt(t2)
+    t0 = time.perf_counter()
+    P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=1, tol=0.0, n_threads=threads)
+    one = time.perf_counter() - t0
+    k = max(1, min(20, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=k, tol=0.0, n_threads=threads)
+    per_iter = (time.perf_counter() - t0) / k
+    iters = args.oracle_iters
+    return {"value": 1.0 / (per_iter * iters), "unit": "recons/s", "cores": threads, "kind": "oracle",
+            "sample": "%d Mann iterations (2 ICD passes each) of one 512^2 reconstruction, "
+                      "%.2f s/iteration, scaled to %d iterations to tolerance" % (k, per_iter, iters)}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    same workload (a few Mann iterations), reported in reconstructions/s."""
+    if rank != 0:
+        return None
+    import synth
+    import oracle
+    y, lam = make_inputs(1, 0)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    threads = os.cpu_count() or 1
+    P = oracle.Problem(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"], y[0], lam[0],
+                       n_agents=WORKLOAD["n_agents"], prior="qggmrf", sigma_x=sx)
+    t2 = oracle.mean_theta2(P)
+    sigma = args.sigma / math.sqrt(t2)
+    per_step_iters = 2
+    for _ in range(args.warmup):
+        P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=1, tol=0.0, n_threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=per_step_iters, tol=0.0, n_threads=threads)
+    el = time.perf_counter() - t0
+    per_iter = el / (args.steps * per_step_iters)
+    value = 1.0 / (per_iter * args.oracle_iters)
+    sample = ("%d Mann iterations per step of one 512^2 reconstruction (%.2f s/iteration), "
+              "scaled to %d iterations to tolerance" % (per_step_iters, per_iter, args.oracle_iters))
+    return {"impl": "reference", "metric": "recons/sec at oracle-matched RMSE", "value": value,
+            "unit": "recons/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "batch_per_gpu": 1},
+            "cpu_baseline": {"value": value, "unit": "recons/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "recons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mace", choices=["mace", "reference"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--concurrency", type=int, default=4)
+    ap.add_argument("--sigma", type=float, default=0.5)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--max-iter", dest="max_iter", type=int, default=2000)
+    ap.add_argument("--sv", type=int, default=8)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=300)
+    ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_mace(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

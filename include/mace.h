@@ -94,7 +94,11 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   max_iter, tol: mace_reconstruct stops when the relative Mann residual
  *   ||w^(k+1) - w^(k)|| / ||w^(k+1)|| (FP64) falls below tol.
  *   concurrency: super-voxels of one agent updated at the same time (0 =
- *   every warp the GPU holds; 1 = one at a time, the serial ICD order). */
+ *   every warp the GPU holds; 1 = one at a time, the serial ICD order).
+ *   sv_order: 0 visits super-voxels in raster order cut into `concurrency`
+ *   bands that run side by side (plain raster when concurrency is 1);
+ *   1 a stride permutation spreading consecutive super-voxels apart.
+ *   Pixels inside a super-voxel are visited in raster order. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -108,6 +112,7 @@ typedef struct {
     int32_t max_iter;
     double tol;
     int32_t concurrency;
+    int32_t sv_order;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */
@@ -126,7 +131,7 @@ typedef struct {
  * (sv_size x sv_size pixel tiles), per view a run (first channel, length
  * 0..3, values).  dtype selects the stored value type.  Runs on the GPU on
  * cuda_stream (a cudaStream_t or NULL).  *out receives the handle.
- * Errors: MACE_EINVAL (sizes, angles, partition, sv_size not in [2, 32],
+ * Errors: MACE_EINVAL (sizes, angles, partition, sv_size not 4, 8 or 16,
  * more than 4096 views), MACE_ENOMEM, MACE_ECUDA. */
 int mace_build_sysmatrix(const mace_geometry *geom, const mace_partition *part,
                          mace_dtype dtype, int32_t sv_size, void *cuda_stream,
@@ -141,33 +146,40 @@ int mace_sysmatrix_get_info(const mace_sysmatrix *sm, mace_sysmatrix_info *info)
 int mace_sysmatrix_column(const mace_sysmatrix *sm, int32_t g, int32_t i, int32_t j,
                           int32_t *c0, int32_t *len, float *vals);
 
-/* The pixel visiting order of a forward ICD pass (raster indices i*nx + j,
- * nx*ny entries): super-voxels in the library's order, raster inside each.
- * With params.concurrency = 1 every agent's pass is exactly Algorithm 2 in
- * this order; a backward pass visits it from the end. */
-int mace_sysmatrix_visit_order(const mace_sysmatrix *sm, int64_t *order);
-
-/* Create a reconstruction state: copies y and weights (Lambda, the inverse
- * noise variances) into agent-major device layout, sets w^(0) = w0 (NULL =
- * 0; [n_agents][n] float32), X^(0) = G(w^(0)) (Algorithm 1 initialisation)
- * and e_i = y_i - A_i X_i.  Work is ordered on cuda_stream.
- * Errors: MACE_EINVAL (parameters out of range, non-finite or negative
- * weights), MACE_ENOMEM, MACE_ECUDA. */
-int mace_init(const mace_sysmatrix *sm, const float *y, const float *weights,
+/* Create a reconstruction state for a batch of `batch` independent
+ * reconstructions that share the system matrix (same geometry and
+ * partition, different data).  Copies y and weights (Lambda, the inverse
+ * noise variances), [batch][nz][n_views][n_channels], into agent-major device
+ * layout, sets w^(0) = w0 (NULL = 0; [batch][n_agents][n] float32), X^(0) =
+ * G(w^(0)) (Algorithm 1 initialisation) and e_i = y_i - A_i X_i.  Work is
+ * ordered on cuda_stream.  All arrays of a state below carry the leading
+ * batch dimension.
+ * Errors: MACE_EINVAL (batch not in [1, 4096], parameters out of range,
+ * non-finite or negative weights), MACE_ENOMEM, MACE_ECUDA. */
+int mace_init(const mace_sysmatrix *sm, int32_t batch, const float *y, const float *weights,
               int32_t ptr_is_device, const mace_params *params, const float *w0,
               void *cuda_stream, mace_state **out);
 
-/* Run n_iters Mann iterations of Algorithm 1.  residual_out (may be NULL)
- * receives the relative Mann residual of the last iteration (FP64);
- * converged_out (may be NULL) is set to 1 once it is below params.tol.
+/* Run n_iters Mann iterations of Algorithm 1 on every reconstruction of the
+ * batch.  residual_out (may be NULL) receives the largest relative Mann
+ * residual over the batch at the last iteration (FP64); converged_out (may
+ * be NULL) is set to 1 once it is below params.tol.
  * Errors: MACE_ENUMERIC when the residual is not finite, MACE_ETIMEOUT,
  * MACE_ECUDA. */
 int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out,
                  int32_t *converged_out);
 
+/* Asynchronous form of mace_iterate: mace_launch enqueues n_iters
+ * iterations on the state's stream and returns without waiting; mace_poll
+ * waits for the stream and reports the last residual (as mace_iterate).
+ * States on different streams then run on the GPU at the same time. */
+int mace_launch(mace_state *st, int32_t n_iters);
+int mace_poll(mace_state *st, double *residual_out, int32_t *converged_out);
+
 /* Iterate until the residual is below params.tol or params.max_iter
  * iterations have run (checking every 10 iterations), then write the
- * consensus image x* = mean_i w_i (Algorithm 1 output) to x_out ([nz][ny][nx]).
+ * consensus images x* = mean_i w_i (Algorithm 1 output) to x_out
+ * ([batch][nz][ny][nx]).
  * Returns MACE_ENOTCONVERGED (x_out still written) if max_iter was hit. */
 int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device,
                      int32_t *iters_out, double *residual_out);
@@ -177,18 +189,25 @@ int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device);
 
 /* Checkpoint / resume: the complete algorithm state is (w, X) (Eq.
  * "PUCEupdate"); e_i is recomputed from X on mace_set_state.  w, X:
- * [n_agents][n] float32 (either may be NULL in get_state). */
+ * [batch][n_agents][n] float32 (either may be NULL in get_state). */
 int mace_get_state(mace_state *st, float *w, float *X, int32_t ptr_is_device);
 int mace_set_state(mace_state *st, const float *w, const float *X, int32_t ptr_is_device);
 
 /* One partial-update pass X_i <- F~_i(v_i; X_i) (Algorithm 2) for every
- * agent with the given v ([n_agents][n] float32), without touching w.
+ * agent with the given v ([batch][n_agents][n] float32), without touching w.
  * backward != 0 visits voxels in reverse order.  For testing the agent
  * update in isolation. */
 int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_device, int32_t backward);
 
+/* The pixel visiting order of a forward ICD pass of this state (raster
+ * indices i*nx + j, nx*ny entries); a backward pass visits it from the end.
+ * With params.concurrency = 1 each agent's pass is exactly Algorithm 2 in
+ * this order. */
+int mace_get_visit_order(const mace_state *st, int64_t *order);
+
 /* Error sinograms e_i in agent-local layout: agent g's block is
- * [nz][|J_g|][n_channels], agents concatenated in order. */
+ * [nz][|J_g|][n_channels], agents concatenated in order, reconstructions
+ * concatenated; mace_error_size gives the total count. */
 int mace_get_error(mace_state *st, float *e, int32_t ptr_is_device);
 int64_t mace_error_size(const mace_state *st);
 
@@ -199,6 +218,13 @@ int mace_recompute_error(mace_state *st);
  * residual and the super-voxels of one agent in flight per pass. */
 int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
                    double *last_residual, int32_t *concurrency);
+
+/* CUDA-event timing of the ICD sweep launches on the state's stream:
+ * mace_set_timing(st, 1, max_launches) starts recording (up to max_launches
+ * launches); mace_get_timing returns the summed device time in ms and the
+ * number of launches recorded since, then restarts the count. */
+int mace_set_timing(mace_state *st, int32_t enable, int32_t max_launches);
+int mace_get_timing(mace_state *st, double *sweep_ms, int32_t *launches);
 
 void mace_free_state(mace_state *st);
 void mace_free_sysmatrix(mace_sysmatrix *sm);

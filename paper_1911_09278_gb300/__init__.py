@@ -30,8 +30,9 @@ DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 # every symbol include/mace.h declares
 EXPORTS = [
     "mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
-    "mace_sysmatrix_visit_order",
-    "mace_init", "mace_iterate", "mace_reconstruct", "mace_consensus",
+    "mace_get_visit_order",
+    "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
+    "mace_set_timing", "mace_get_timing",
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
@@ -63,7 +64,7 @@ class Params(ctypes.Structure):
                 ("rho", ctypes.c_double), ("sweeps_per_iter", ctypes.c_int32),
                 ("symmetric", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("concurrency", ctypes.c_int32)]
+                ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -90,9 +91,13 @@ def load(path=LIB_PATH):
     L.mace_build_sysmatrix.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Partition), i32, i32, vp, pp]
     L.mace_sysmatrix_get_info.argtypes = [vp, ctypes.POINTER(SysmatrixInfo)]
     L.mace_sysmatrix_column.argtypes = [vp, i32, i32, i32, vp, vp, vp]
-    L.mace_sysmatrix_visit_order.argtypes = [vp, vp]
-    L.mace_init.argtypes = [vp, vp, vp, i32, ctypes.POINTER(Params), vp, vp, pp]
+    L.mace_get_visit_order.argtypes = [vp, vp]
+    L.mace_init.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(Params), vp, vp, pp]
     L.mace_iterate.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.mace_launch.argtypes = [vp, i32]
+    L.mace_poll.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.mace_set_timing.argtypes = [vp, i32, i32]
+    L.mace_get_timing.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_reconstruct.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mace_consensus.argtypes = [vp, vp, i32]
     L.mace_get_state.argtypes = [vp, vp, vp, i32]
@@ -110,8 +115,9 @@ def load(path=LIB_PATH):
     L.mace_free_sysmatrix.restype = None
     L.mace_last_error.restype = ctypes.c_char_p
     for name in ("mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
-                 "mace_sysmatrix_visit_order",
-                 "mace_init", "mace_iterate", "mace_reconstruct", "mace_consensus",
+                 "mace_get_visit_order",
+                 "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
+    "mace_set_timing", "mace_get_timing",
                  "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
                  "mace_recompute_error", "mace_get_stats"):
         getattr(L, name).restype = ctypes.c_int
@@ -183,12 +189,6 @@ class Sysmatrix:
                                             vals.ctypes.data_as(ctypes.c_void_p)))
         return c0, ln, vals
 
-    def visit_order(self):
-        """Pixel visiting order of a forward ICD pass (raster indices)."""
-        o = np.empty(self.nx * self.ny, np.int64)
-        _check(load().mace_sysmatrix_visit_order(self.handle, o.ctypes.data_as(ctypes.c_void_p)))
-        return o
-
     def close(self):
         if self.handle:
             load().mace_free_sysmatrix(self.handle)
@@ -219,20 +219,25 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
-                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8):
+                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0):
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
-                  max_iter, tol, concurrency)
+                  max_iter, tol, concurrency, sv_order)
 
 
 class State:
-    """Handle of a reconstruction state (mace_init)."""
+    """Handle of a reconstruction state (mace_init) holding `batch`
+    reconstructions that share one system matrix."""
 
-    def __init__(self, handle, sm, params):
+    def __init__(self, handle, sm, params, batch):
         self.handle = handle
         self.sm = sm            # the state borrows the system matrix
         self.params = params
+        self.batch = batch
         self.n = sm.nx * sm.ny
+
+    def _img_shape(self):
+        return (self.sm.ny, self.sm.nx) if self.batch == 1 else (self.batch, self.sm.ny, self.sm.nx)
 
     def iterate(self, n_iters):
         r = ctypes.c_double()
@@ -240,10 +245,30 @@ class State:
         _check(load().mace_iterate(self.handle, n_iters, ctypes.byref(r), ctypes.byref(c)))
         return r.value, bool(c.value)
 
+    def launch(self, n_iters):
+        """Enqueue n_iters iterations on the state's stream (no wait)."""
+        _check(load().mace_launch(self.handle, n_iters))
+
+    def poll(self):
+        r = ctypes.c_double()
+        c = ctypes.c_int32()
+        _check(load().mace_poll(self.handle, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, bool(c.value)
+
+    def set_timing(self, enable=True, max_launches=4096):
+        _check(load().mace_set_timing(self.handle, int(bool(enable)), max_launches))
+
+    def get_timing(self):
+        """(summed sweep-kernel device ms, launches) since set_timing / last call."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int32()
+        _check(load().mace_get_timing(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     def reconstruct(self, out=None):
         """Iterate to tol / max_iter; returns (x, iters, residual, converged)."""
-        x = np.empty((self.sm.ny, self.sm.nx), np.float32) if out is None else out
-        ptr, dev, keep = _out_ptr(x, self.n)
+        x = np.empty(self._img_shape(), np.float32) if out is None else out
+        ptr, dev, keep = _out_ptr(x, self.batch * self.n)
         it = ctypes.c_int32()
         r = ctypes.c_double()
         rc = _check(load().mace_reconstruct(self.handle, ptr, dev, ctypes.byref(it), ctypes.byref(r)),
@@ -251,30 +276,37 @@ class State:
         return x, it.value, r.value, rc == MACE_OK
 
     def consensus(self, out=None):
-        x = np.empty((self.sm.ny, self.sm.nx), np.float32) if out is None else out
-        ptr, dev, keep = _out_ptr(x, self.n)
+        x = np.empty(self._img_shape(), np.float32) if out is None else out
+        ptr, dev, keep = _out_ptr(x, self.batch * self.n)
         _check(load().mace_consensus(self.handle, ptr, dev))
         return x
 
     def get_state(self):
         N = self.sm.n_agents
-        w = np.empty((N, self.n), np.float32)
-        X = np.empty((N, self.n), np.float32)
+        shape = (N, self.n) if self.batch == 1 else (self.batch, N, self.n)
+        w = np.empty(shape, np.float32)
+        X = np.empty(shape, np.float32)
         _check(load().mace_get_state(self.handle, w.ctypes.data_as(ctypes.c_void_p),
                                      X.ctypes.data_as(ctypes.c_void_p), 0))
         return w, X
 
     def set_state(self, w, X):
         N = self.sm.n_agents
-        pw, dw, kw = _in_ptr(w, N * self.n)
-        px, dx, kx = _in_ptr(X, N * self.n)
+        pw, dw, kw = _in_ptr(w, self.batch * N * self.n)
+        px, dx, kx = _in_ptr(X, self.batch * N * self.n)
         if dw != dx:
             raise ValueError("w and X must both be host or both be device arrays")
         _check(load().mace_set_state(self.handle, pw, px, dw))
 
     def prox_pass(self, v, backward=False):
-        pv, dv, kv = _in_ptr(v, self.sm.n_agents * self.n)
+        pv, dv, kv = _in_ptr(v, self.batch * self.sm.n_agents * self.n)
         _check(load().mace_prox_pass(self.handle, pv, dv, int(bool(backward))))
+
+    def visit_order(self):
+        """Pixel visiting order of a forward ICD pass (raster indices)."""
+        o = np.empty(self.n, np.int64)
+        _check(load().mace_get_visit_order(self.handle, o.ctypes.data_as(ctypes.c_void_p)))
+        return o
 
     def error(self):
         ne = load().mace_error_size(self.handle)
@@ -317,19 +349,24 @@ def _out_ptr(a, n):
     return a.ctypes.data_as(ctypes.c_void_p), 0, a
 
 
-def mace_init(sm, y, weights, params, w0=None, stream=None):
+def mace_init(sm, y, weights, params, w0=None, stream=None, batch=None):
+    """y, weights: [batch][n_views][n_channels] (or [n_views][n_channels] for
+    one reconstruction)."""
     m = sm.n_views * sm.n_channels
-    py, dy, ky = _in_ptr(y, m)
-    pl, dl, kl = _in_ptr(weights, m)
+    if batch is None:
+        size = y.numel() if _is_torch(y) else np.asarray(y).size
+        batch = max(1, size // m)
+    py, dy, ky = _in_ptr(y, batch * m)
+    pl, dl, kl = _in_ptr(weights, batch * m)
     if dy != dl:
         raise ValueError("y and weights must both be host or both be device arrays")
-    pw, dw, kw = _in_ptr(w0, sm.n_agents * sm.nx * sm.ny)
+    pw, dw, kw = _in_ptr(w0, batch * sm.n_agents * sm.nx * sm.ny)
     if w0 is not None and dw != dy:
         raise ValueError("w0 must live where y does")
     h = ctypes.c_void_p()
-    _check(load().mace_init(sm.handle, py, pl, dy, ctypes.byref(params), pw, _stream_handle(stream),
+    _check(load().mace_init(sm.handle, batch, py, pl, dy, ctypes.byref(params), pw, _stream_handle(stream),
                             ctypes.byref(h)))
-    return State(h, sm, params)
+    return State(h, sm, params, batch)
 
 
 def mace_iterate(state, n_iters):

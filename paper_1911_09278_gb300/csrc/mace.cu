@@ -148,8 +148,6 @@ struct mace_sysmatrix {
     uint8_t *d_cols = nullptr;
     int64_t bytes_cols = 0, nnz = 0;
     std::vector<int64_t> agent_bytes;
-    std::vector<int32_t> sv_order;    // visiting order of super-voxels
-    int32_t *d_sv_order = nullptr;
 };
 
 __global__ void band_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
@@ -290,7 +288,7 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
     if (rc) return rc;
     if (!part || part->n_agents < 1 || part->n_agents > geom->n_views)
         return fail(MACE_EINVAL, "n_agents must be in [1, n_views]");
-    if (sv_size < 2 || sv_size > 32) return fail(MACE_EINVAL, "sv_size must be in [2, 32]");
+    if (sv_size != 4 && sv_size != 8 && sv_size != 16) return fail(MACE_EINVAL, "sv_size must be 4, 8 or 16");
     if (dtype != MACE_F32 && dtype != MACE_BF16 && dtype != MACE_F16)
         return fail(MACE_EINVAL, "unknown dtype");
 
@@ -351,8 +349,7 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
         cudaMalloc(&M->d_band, sizeof(uint32_t) * nband) != cudaSuccess ||
         cudaMalloc(&M->d_band_tot, sizeof(uint32_t) * M->N * M->nsv) != cudaSuccess ||
         cudaMalloc(&M->d_sv_base, sizeof(int64_t) * M->N * M->nsv) != cudaSuccess ||
-        cudaMalloc(&M->d_col_off, sizeof(uint32_t) * M->N * M->nsv * (M->S2 + 1)) != cudaSuccess ||
-        cudaMalloc(&M->d_sv_order, sizeof(int32_t) * M->nsv) != cudaSuccess)
+        cudaMalloc(&M->d_col_off, sizeof(uint32_t) * M->N * M->nsv * (M->S2 + 1)) != cudaSuccess)
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for system-matrix metadata");
     if (cudaMemcpyAsync(M->d_cs, cs.data(), sizeof(double2) * M->V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(M->d_view_off, M->view_off.data(), sizeof(int) * (M->N + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -415,18 +412,9 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
     M->bytes_cols = total;
     if (cudaMalloc(&M->d_cols, total > 0 ? total : 16) != cudaSuccess)
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for the system matrix (" + std::to_string(total) + " bytes)");
-    // super-voxel visiting order: a stride permutation that spreads consecutive
-    // super-voxels over the image (they run concurrently)
-    M->sv_order.resize(M->nsv);
-    {
-        int64_t p = std::max<int64_t>(1, (int64_t)llround(0.6180339887 * M->nsv));
-        while (std::gcd<int64_t>(p, M->nsv) != 1) ++p;
-        for (int k = 0; k < M->nsv; ++k) M->sv_order[k] = (int32_t)(((int64_t)k * p) % M->nsv);
-    }
     ce = cudaMemcpyAsync(M->d_sv_base, sv_base.data(), sizeof(int64_t) * sv_base.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_col_off, col_off.data(), sizeof(uint32_t) * col_off.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_band_tot, band_tot.data(), sizeof(uint32_t) * band_tot.size(), cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_sv_order, M->sv_order.data(), sizeof(int32_t) * M->nsv, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(M->d_cols, 0, total > 0 ? total : 16, s);
     if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix upload: ") + cudaGetErrorString(ce));
     if (M->dtype == MACE_F32)
@@ -517,20 +505,6 @@ extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t
     return MACE_OK;
 }
 
-extern "C" int mace_sysmatrix_visit_order(const mace_sysmatrix *M, int64_t *order)
-{
-    if (!M || !order) return fail(MACE_EINVAL, "NULL argument");
-    int64_t k = 0;
-    for (int q = 0; q < M->nsv; ++q) {
-        int sv = M->sv_order[q], si = sv / M->nsvx, sj = sv % M->nsvx;
-        for (int t = 0; t < M->S2; ++t) {
-            int i = si * M->S + t / M->S, j = sj * M->S + t % M->S;
-            if (i < M->geo.ny && j < M->geo.nx) order[k++] = (int64_t)i * M->geo.nx + j;
-        }
-    }
-    return MACE_OK;
-}
-
 extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
 {
     if (!M) return;
@@ -541,7 +515,6 @@ extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
     cudaFree(M->d_sv_base);
     cudaFree(M->d_col_off);
     cudaFree(M->d_cols);
-    cudaFree(M->d_sv_order);
     delete M;
 }
 
@@ -552,19 +525,26 @@ struct mace_state {
     const mace_sysmatrix *M;
     mace_params P;
     cudaStream_t stream;
-    int64_t n;                 // voxels
-    int64_t ne;                // total error-sinogram entries over agents
+    int B;                     // reconstructions in the batch (same geometry)
+    int64_t n;                 // voxels of one image
+    int64_t ne;                // error-sinogram entries of one reconstruction
     double sigma_abs;
-    float2 *d_eL = nullptr;    // (e, Lambda) per agent [V_g][D], agents concatenated
-    float *d_y = nullptr;      // y per agent, same layout
-    float *d_w = nullptr;      // [N][n]
-    float *d_X = nullptr;      // [N][n]
-    float *d_vexp = nullptr;   // [N][n] explicit v (prox-pass entry point)
-    double *d_wbar = nullptr;  // [n]
-    double *d_part = nullptr;  // [nblk_mann][2] residual partials
-    double *d_resid = nullptr; // [4]: dw2, ww2, r, flag
-    int *d_counter = nullptr;  // work counters [8]
+    float2 *d_eL = nullptr;    // (e, Lambda) [B][agents: V_g][D]
+    float *d_y = nullptr;      // y, same layout
+    float *d_w = nullptr;      // [B][N][n]
+    float *d_X = nullptr;      // [B][N][n]
+    float *d_vexp = nullptr;   // [B][N][n] explicit v (prox-pass entry point)
+    double *d_wbar = nullptr;  // [B][n]
+    double *d_part = nullptr;  // [B][nblk_mann][2] residual partials
+    double *d_resid = nullptr; // [B][3]: dw2, ww2, r
+    int *d_counter = nullptr;  // work counters [B][N]
     int *d_status = nullptr;   // device status word
+    std::vector<int32_t> sv_order;   // super-voxel visiting order of a forward pass
+    int32_t *d_sv_order = nullptr;
+    // optional CUDA-event timing of the sweep launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;     // pairs (start, stop)
+    int ev_used = 0;
     int nblk_mann = 0;
     int iters = 0;
     double last_resid = INFINITY;
@@ -586,9 +566,10 @@ struct SweepArgs {
     const float *vexp;
     int *counter;
     int *status;
-    int N, nsv, nsvx, S, nx, ny, D;
+    int B, N, nsv, nsvx, S, nx, ny, D;
+    int64_t ne;
     int backward;
-    int max_band, col_stride, max_views;   // per-warp shared-memory layout
+    int max_band, col_stride, max_views;   // per-warp shared-memory layout (S is a template parameter)
     float inv_s2, pscale;
     int prior;                  // 0 quadratic, 1 Q-GGMRF
     float inv_sx2, inv_Tsx, qexp, qq;   // prior constants
@@ -663,11 +644,14 @@ template <> __device__ __forceinline__ float ld_val<__half>(const uint8_t *p, in
 //   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
 //   bsnap:  max_band * 4                  e of the band when the super-voxel began
 //   bdesc:  max_views * 4                 band descriptor of each view (lo | len << 16)
+//   bview:  max_band * 2                  view of each band entry (u16)
 //   boff:   max_views * 2                 band offset of each view (u16)
+//   coff:   (S^2 + 1) * 4                 column byte offsets of the super-voxel
+//   tl:     S^2 * 2                       non-empty pixels in visiting order
 //   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
 //   vt:     S^2 * 4                       v tile
 struct WarpSmem {
-    size_t ring, bars, beL, bsnap, bdesc, boff, xt, vt, total;
+    size_t ring, bars, beL, bsnap, bdesc, bview, boff, coff, tl, xt, vt, total;
 };
 
 __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views)
@@ -680,7 +664,10 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_strid
     L.beL = o;   o += r16((size_t)max_band * 8);
     L.bsnap = o; o += r16((size_t)max_band * 4);
     L.bdesc = o; o += r16((size_t)max_views * 4);
+    L.bview = o; o += r16((size_t)max_band * 2);
     L.boff = o;  o += r16((size_t)max_views * 2);
+    L.coff = o;  o += r16((size_t)(S * S + 1) * 4);
+    L.tl = o;    o += r16((size_t)S * S * 2);
     L.xt = o;    o += r16((size_t)(S + 2) * (S + 2) * 4);
     L.vt = o;    o += r16((size_t)S * S * 4);
     L.total = o;
@@ -695,21 +682,25 @@ static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views
 // One warp per super-voxel at a time; lane = view (views lane, lane+32, ...).
 // MAXR > 0: the agent has at most 32*MAXR views and each lane keeps its runs
 // in registers between the reduction and the update; MAXR == 0: any number of
-// views, runs re-read from shared memory.
-template <typename T, int MAXR>
-__global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
+// views, runs re-read from shared memory.  S: super-voxel side.
+template <typename T, int MAXR, int S>
+__global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int S2 = S * S, T2 = S + 2;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, A.S, A.max_views);
+    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views);
     uint8_t *base = smem + wib * Ly.total;
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
     float2 *beL = (float2 *)(base + Ly.beL);
     float *bsnap = (float *)(base + Ly.bsnap);
     uint32_t *bdesc = (uint32_t *)(base + Ly.bdesc);
+    uint16_t *bview = (uint16_t *)(base + Ly.bview);
     uint16_t *boff = (uint16_t *)(base + Ly.boff);
+    uint32_t *scoff = (uint32_t *)(base + Ly.coff);
+    uint16_t *tl = (uint16_t *)(base + Ly.tl);
     float *xt = (float *)(base + Ly.xt);
     float *vt = (float *)(base + Ly.vt);
 
@@ -718,59 +709,72 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncwarp();
 
-    const int S = A.S, S2 = S * S, T2 = S + 2;
-    uint32_t issued = 0, consumed = 0;   // ring sequence numbers (per warp)
+    uint32_t seq = 0;   // columns consumed by this warp so far (ring position)
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = (int64_t)A.nx * A.ny;
 
-    // warp w serves agent w mod N; the agent's super-voxels are handed out in
-    // visiting order through the agent's counter, so at most
-    // (warps / N) super-voxels of one agent are in flight at a time
+    // warp w serves agent g of reconstruction b, (b, g) = w mod (B N); the
+    // pair's super-voxels are handed out in visiting order through its
+    // counter, so at most warps / (B N) super-voxels of one agent of one
+    // reconstruction are in flight at a time
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    const int g = gw % A.N;
+    const int pair = gw % (A.B * A.N);
+    const int b = pair / A.N, g = pair - b * A.N;
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
     const int hdr_bytes = (Vg + 3) & ~3;
-    float2 *eLg = A.eL + (int64_t)v0 * A.D;    // agent block [Vg][D]
-    float *Xg = A.X + (int64_t)g * n;
+    const int R = (Vg + 31) >> 5;
+    float2 *eLg = A.eL + (int64_t)b * A.ne + (int64_t)v0 * A.D;    // agent block [Vg][D]
+    float *Xg = A.X + (int64_t)pair * n;
+    const float *wg = A.w + (int64_t)pair * n;
+    const double *wbg = A.wbar + (int64_t)b * n;
+    const float *vg = A.vexp ? A.vexp + (int64_t)pair * n : nullptr;
 
+    // the next super-voxel is claimed one super-voxel ahead, so the claim's
+    // round trip overlaps the current super-voxel's work
+    int next_slot = 0;
+    if (lane == 0) next_slot = atomicAdd(&A.counter[pair], 1);
     while (true) {
-        int slot = 0;
-        if (lane == 0) {
-            slot = atomicAdd(&A.counter[g], 1);
-            if (slot < A.nsv && *((volatile int *)A.status) != 0) slot = A.nsv;
-        }
+        int slot = __shfl_sync(FULL, next_slot, 0);
+        if (lane == 0 && slot < A.nsv && *((volatile int *)A.status) != 0) slot = A.nsv;
         slot = __shfl_sync(FULL, slot, 0);
         if (slot >= A.nsv) break;
+        if (lane == 0) next_slot = atomicAdd(&A.counter[pair], 1);
         if (A.backward) slot = A.nsv - 1 - slot;
         const int sv = A.sv_order[slot];
-        const int si = sv / A.nsvx, sj = sv % A.nsvx;
+        const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
         const int64_t gsv = (int64_t)g * A.nsv + sv;
         const uint8_t *svcols = A.cols + A.sv_base[gsv];
         const uint32_t *coff = A.col_off + gsv * (S2 + 1);
 
-        // --- prefetch the first columns (processing order) ---------------
-        int next_issue = 0;
-        auto issue = [&](int k) {
-            int t = A.backward ? S2 - 1 - k : k;
-            uint32_t o0 = coff[t], o1 = coff[t + 1];
-            uint32_t bytes = o1 - o0;
-            if (bytes) {
-                int stg = issued % kRing;
-                if (lane == 0) {
-                    fence_proxy_async();
-                    mbar_expect_tx(&bars[stg], bytes);
-                    tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + o0, bytes, &bars[stg]);
-                }
-                ++issued;
+        // --- column offsets and the list of pixels to visit -----------------
+        for (int k = lane; k <= S2; k += 32) scoff[k] = coff[k];
+        __syncwarp();
+        int count = 0;
+        for (int k0 = 0; k0 < S2; k0 += 32) {
+            const int k = k0 + lane;
+            const int t = A.backward ? S2 - 1 - k : k;
+            const bool ne = k < S2 && scoff[t + 1] != scoff[t];
+            const unsigned m = __ballot_sync(FULL, ne);
+            if (ne) tl[count + __popc(m & lt_mask)] = (uint16_t)t;
+            count += __popc(m);
+        }
+        __syncwarp();
+        // --- prefetch the first columns --------------------------------------
+        if (lane == 0) {
+            const int pre = min(count, kRing);
+            for (int q = 0; q < pre; ++q) {
+                const int t = tl[q];
+                const uint32_t stg = (seq + q) % kRing;
+                mbar_expect_tx(&bars[stg], scoff[t + 1] - scoff[t]);
+                tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + scoff[t], scoff[t + 1] - scoff[t], &bars[stg]);
             }
-        };
-        while (next_issue < S2 && (int)(issued - consumed) < kRing) issue(next_issue++);
+        }
 
         // --- band descriptors and offsets ----------------------------------
         const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
         int run = 0;
-        for (int r = 0; r * 32 < Vg; ++r) {
+        for (int r = 0; r < R; ++r) {
             int v = r * 32 + lane;
             uint32_t d = v < Vg ? bd[v] : 0u;
             int len = (int)(d >> 16);
@@ -781,61 +785,60 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
                 if (lane >= o) incl += y;
             }
             if (v < Vg) {
-                boff[v] = (uint16_t)(run + incl - len);
+                const int b0 = run + incl - len;
+                boff[v] = (uint16_t)b0;
                 bdesc[v] = d;
+                for (int k = 0; k < len; ++k) bview[b0 + k] = (uint16_t)v;
             }
             run += __shfl_sync(FULL, incl, 31);
         }
+        const int band_tot = run;
         __syncwarp();
-        // --- band snapshot: one coalesced row per view -----------------------
-#pragma unroll 4
-        for (int v = 0; v < Vg; ++v) {
-            const uint32_t d = bdesc[v];
-            const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
-            const float2 *src = eLg + (int64_t)v * A.D + lo;
-            const int b0 = boff[v];
-            for (int k = lane; k < len; k += 32) {
-                float2 el = src[k];
-                beL[b0 + k] = el;
-                bsnap[b0 + k] = el.x;
-            }
+        // --- band snapshot: all entries loaded at once -----------------------
+        for (int f = lane; f < band_tot; f += 32) {
+            const int v = bview[f];
+            const float2 el = eLg[(int64_t)v * A.D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v])];
+            beL[f] = el;
+            bsnap[f] = el.x;
         }
         // --- X tile with halo, v tile ---------------------------------------
         for (int k = lane; k < T2 * T2; k += 32) {
-            int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
+            const int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
             xt[k] = (i >= 0 && i < A.ny && j >= 0 && j < A.nx) ? Xg[(int64_t)i * A.nx + j] : 0.f;
         }
         for (int k = lane; k < S2; k += 32) {
-            int i = si * S + k / S, j = sj * S + k % S;
+            const int i = si * S + k / S, j = sj * S + k % S;
             float vv = 0.f;
             if (i < A.ny && j < A.nx) {
-                int64_t s = (int64_t)i * A.nx + j;
-                vv = A.vexp ? A.vexp[(int64_t)g * n + s]
-                            : (float)(2.0 * A.wbar[s] - (double)A.w[(int64_t)g * n + s]);
+                const int64_t s = (int64_t)i * A.nx + j;
+                vv = vg ? vg[s] : (float)(2.0 * wbg[s] - (double)wg[s]);
             }
             vt[k] = vv;
         }
+        // prior constants of this lane's neighbour (lanes 0..7)
+        const int kk = lane < 4 ? lane : lane + 1;
+        const int pdi = kk / 3 - 1, pdj = kk % 3 - 1;
+        const float pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
         __syncwarp();
 
         // --- visit the pixels ------------------------------------------------
-        for (int k = 0; k < S2; ++k) {
-            const int t = A.backward ? S2 - 1 - k : k;
-            const uint32_t bytes = coff[t + 1] - coff[t];
-            if (bytes == 0) continue;   // pixel outside the image
+        for (int q = 0; q < count; ++q) {
+            const int t = tl[q];
             const int ti = t / S, tj = t % S;
             const int i = si * S + ti, j = sj * S + tj;
-            // wait for the column
-            const int stg = consumed % kRing;
-            const uint32_t parity = (consumed / kRing) & 1u;
+            const uint32_t stg = (seq + q) % kRing;
+            const uint32_t parity = ((seq + q) / kRing) & 1u;
             uint32_t spins = 0;
             while (!mbar_try_wait(&bars[stg], parity)) {
                 if (++spins > kSpinLimit) {
                     // give up: flag the host, then wait (bounded) for this
                     // warp's copies still in flight before leaving
                     if (lane == 0) atomicExch(A.status, kStatusTimeout);
-                    for (uint32_t q = consumed + 1; q < issued; ++q) {
+                    const int last = min(count, q + kRing);
+                    for (int q2 = q + 1; q2 < last; ++q2) {
                         uint32_t sp2 = 0;
-                        while (!mbar_try_wait(&bars[q % kRing], (q / kRing) & 1u) && ++sp2 < kSpinLimit) {}
+                        while (!mbar_try_wait(&bars[(seq + q2) % kRing], ((seq + q2) / kRing) & 1u) &&
+                               ++sp2 < kSpinLimit) {}
                     }
                     return;
                 }
@@ -849,7 +852,6 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
             float ca0[RC], ca1[RC], ca2[RC];
             int cb[RC], cL[RC];
             int vbase = 0;
-            const int R = (Vg + 31) >> 5;
 #pragma unroll
             for (int r = 0; r < (MAXR > 0 ? MAXR : 1 << 20); ++r) {
                 if (r >= R) break;
@@ -890,12 +892,10 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
             const int tc = (ti + 1) * T2 + (tj + 1);
             const float xs = xt[tc];
             if (lane < 8) {
-                const int kk = lane < 4 ? lane : lane + 1;   // skip the centre of the 3x3
-                const int di = kk / 3 - 1, dj = kk % 3 - 1;
-                const int ii = i + di, jj = j + dj;
+                const int ii = i + pdi, jj = j + pdj;
                 if (ii >= 0 && ii < A.ny && jj >= 0 && jj < A.nx) {
-                    const float d = xs - xt[tc + di * T2 + dj];
-                    const float wgt = A.pscale * ((di != 0 && dj != 0) ? A.b_diag : A.b_edge) * prior_weight(A, d);
+                    const float d = xs - xt[tc + pdi * T2 + pdj];
+                    const float wgt = pb * prior_weight(A, d);
                     p1 = fmaf(wgt, d, p1);
                     p2 += wgt;
                 }
@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
             }
             // the step's sign and zero set come from num alone, so a fast
             // division leaves the fixed point unchanged
-            const float num = p1 + (xs - vt[t]) * A.inv_s2;
+            const float num = fmaf(xs - vt[t], A.inv_s2, p1);
             const float den = p2 + A.inv_s2;
             const float alpha = -__fdividef(num, den);
             // update e: each lane owns its views' band rows
@@ -943,26 +943,28 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
                 }
             }
             if (lane == 0) xt[tc] = xs + alpha;
-            ++consumed;
             __syncwarp();
-            // refill the ring slot just freed
-            while (next_issue < S2 && (int)(issued - consumed) < kRing) issue(next_issue++);
+            // refill the ring slot just freed.  Every read of the slot has
+            // completed: its values fed the reduction all lanes joined before
+            // the __syncwarp above, so the TMA write cannot overtake them.
+            if (lane == 0 && q + kRing < count) {
+                const int t2 = tl[q + kRing];
+                mbar_expect_tx(&bars[stg], scoff[t2 + 1] - scoff[t2]);
+                tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + scoff[t2], scoff[t2 + 1] - scoff[t2], &bars[stg]);
+            }
         }
+        seq += count;
 
         // --- write back: X tile and the change of e (one row per view) ------
         for (int k = lane; k < S2; k += 32) {
-            int i = si * S + k / S, j = sj * S + k % S;
+            const int i = si * S + k / S, j = sj * S + k % S;
             if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(k / S + 1) * T2 + (k % S + 1)];
         }
-#pragma unroll 4
-        for (int v = 0; v < Vg; ++v) {
-            const uint32_t d = bdesc[v];
-            const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
-            float2 *dst = eLg + (int64_t)v * A.D + lo;
-            const int b0 = boff[v];
-            for (int k = lane; k < len; k += 32) {
-                const float de = beL[b0 + k].x - bsnap[b0 + k];
-                if (de != 0.f) atomicAdd(&dst[k].x, de);
+        for (int f = lane; f < band_tot; f += 32) {
+            const float de = beL[f].x - bsnap[f];
+            if (de != 0.f) {
+                const int v = bview[f];
+                atomicAdd(&eLg[(int64_t)v * A.D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v])].x, de);
             }
         }
         __syncwarp();
@@ -970,31 +972,39 @@ __global__ void __launch_bounds__(256) icd_sweep_kernel(SweepArgs A)
 }
 
 // --- consensus (G), Mann, residual ------------------------------------------
-__global__ void consensus_kernel(const float *__restrict__ w, int N, int64_t n, double *__restrict__ wbar,
+__global__ void consensus_kernel(const float *__restrict__ w, int B, int N, int64_t n, double *__restrict__ wbar,
                                  float *__restrict__ xout)
 {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    // wbar[b][s] = (1/N) sum_g w[b][g][s], FP64, fixed agent order
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)B * n) return;
+    int64_t b = k / n, s = k - b * n;
+    const float *wb = w + b * N * n;
     double acc = 0.0;
-    for (int g = 0; g < N; ++g) acc += (double)w[(int64_t)g * n + s];
+    for (int g = 0; g < N; ++g) acc += (double)wb[(int64_t)g * n + s];
     double m = acc / (double)N;
-    if (wbar) wbar[s] = m;
-    if (xout) xout[s] = (float)m;
+    if (wbar) wbar[k] = m;
+    if (xout) xout[k] = (float)m;
 }
 
 __global__ void __launch_bounds__(256) mann_kernel(float *__restrict__ w, const float *__restrict__ X,
                                                    const double *__restrict__ wbar, int N, int64_t n, float rho,
                                                    double *__restrict__ part)
 {
+    // blockIdx.y = reconstruction b
     __shared__ double sh[2][8];
+    const int64_t b = blockIdx.y;
+    float *wb = w + b * N * n;
+    const float *Xb = X + b * N * n;
+    const double *wbarb = wbar + b * n;
     double d2 = 0.0, w2 = 0.0;
     const int64_t total = (int64_t)N * n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
         int64_t s = k % n;
-        float wo = w[k];
-        float v = (float)(2.0 * wbar[s] - (double)wo);
-        float wn = rho * (2.f * X[k] - v) + (1.f - rho) * wo;
-        w[k] = wn;
+        float wo = wb[k];
+        float v = (float)(2.0 * wbarb[s] - (double)wo);
+        float wn = rho * (2.f * Xb[k] - v) + (1.f - rho) * wo;
+        wb[k] = wn;
         double d = (double)wn - (double)wo;
         d2 += d * d;
         w2 += (double)wn * (double)wn;
@@ -1007,22 +1017,25 @@ __global__ void __launch_bounds__(256) mann_kernel(float *__restrict__ w, const 
     if (lane == 0) { sh[0][wid] = d2; sh[1][wid] = w2; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sh[0][k]; b += sh[1][k]; }
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
+        double a = 0.0, c = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sh[0][k]; c += sh[1][k]; }
+        double *pb = part + 2 * (b * gridDim.x + blockIdx.x);
+        pb[0] = a;
+        pb[1] = c;
     }
 }
 
-__global__ void residual_kernel(const double *__restrict__ part, int nblk, double *__restrict__ out)
+__global__ void residual_kernel(const double *__restrict__ part, int nblk, int B, double *__restrict__ out)
 {
-    // one thread: fixed-order sum of the block partials
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < nblk; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }
-    out[0] = a;
-    out[1] = b;
-    out[2] = b > 0.0 ? sqrt(a / b) : sqrt(a);
+    // thread b: fixed-order sum of reconstruction b's block partials
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double *pb = part + 2 * (int64_t)b * nblk;
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < nblk; ++k) { a += pb[2 * k]; c += pb[2 * k + 1]; }
+    out[3 * b] = a;
+    out[3 * b + 1] = c;
+    out[3 * b + 2] = c > 0.0 ? sqrt(a / c) : sqrt(a);
 }
 
 // --- error sinogram: e = y - A X ---------------------------------------------
@@ -1030,14 +1043,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                                       const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                                                       const int *__restrict__ view_off, float2 *__restrict__ eL,
-                                                      const float *__restrict__ X, int N, int nsv, int nsvx, int S, int nx,
-                                                      int ny, int D)
+                                                      const float *__restrict__ X, int B, int N, int nsv, int nsvx, int S,
+                                                      int nx, int ny, int D, int64_t ne)
 {
-    // one warp per (agent, super-voxel); lane = view; e must hold y on entry
+    // one warp per (reconstruction, agent, super-voxel); lane = view; e must
+    // hold y on entry
     const int lane = threadIdx.x & 31;
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (item >= (int64_t)N * nsv) return;
-    const int g = (int)(item / nsv), sv = (int)(item % nsv);
+    if (item >= (int64_t)B * N * nsv) return;
+    const int pair = (int)(item / nsv), sv = (int)(item % nsv);
+    const int b = pair / N, g = pair - b * N;
     const int si = sv / nsvx, sj = sv % nsvx, S2 = S * S;
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
     const int64_t gsv = (int64_t)g * nsv + sv;
@@ -1045,8 +1060,8 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
     const uint32_t *coff = col_off + gsv * (S2 + 1);
     const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
     const int hdr_bytes = (Vg + 3) & ~3;
-    float2 *eLg = eL + (int64_t)v0 * D;
-    const float *Xg = X + (int64_t)g * nx * ny;
+    float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
+    const float *Xg = X + (int64_t)pair * nx * ny;
     const unsigned FULL = 0xffffffffu, lt_mask = (1u << lane) - 1u;
     for (int t = 0; t < S2; ++t) {
         if (coff[t + 1] == coff[t]) continue;
@@ -1074,15 +1089,18 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
 }
 
 __global__ void pack_kernel(const float *__restrict__ y, const float *__restrict__ lam, const int *__restrict__ agent_view,
-                            int V, int D, float2 *__restrict__ eL, float *__restrict__ yg)
+                            int B, int V, int D, float2 *__restrict__ eL, float *__restrict__ yg)
 {
-    // agent-ordered row k holds view agent_view[k]
+    // agent-ordered row k of reconstruction b holds view agent_view[k]
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (int64_t)V * D) return;
-    int k = (int)(tid / D), c = (int)(tid % D);
+    const int64_t per = (int64_t)V * D;
+    if (tid >= (int64_t)B * per) return;
+    int64_t b = tid / per, r = tid - b * per;
+    int k = (int)(r / D), c = (int)(r % D);
     int m = agent_view[k];
-    float yy = y[(int64_t)m * D + c];
-    eL[tid] = make_float2(yy, lam[(int64_t)m * D + c]);
+    int64_t src = b * per + (int64_t)m * D + c;
+    float yy = y[src];
+    eL[tid] = make_float2(yy, lam[src]);
     yg[tid] = yy;
 }
 
@@ -1092,10 +1110,13 @@ __global__ void reset_error_kernel(const float *__restrict__ yg, float2 *__restr
     if (k < ne) eL[k].x = yg[k];
 }
 
-__global__ void broadcast_kernel(const double *__restrict__ wbar, float *__restrict__ X, int N, int64_t n)
+__global__ void broadcast_kernel(const double *__restrict__ wbar, float *__restrict__ X, int B, int N, int64_t n)
 {
+    // X[b][g][s] = wbar[b][s]
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < (int64_t)N * n) X[k] = (float)wbar[k % n];
+    if (k >= (int64_t)B * N * n) return;
+    int64_t b = k / ((int64_t)N * n);
+    X[k] = (float)wbar[b * n + k % n];
 }
 
 __global__ void check_weights_kernel(const float *__restrict__ y, const float *__restrict__ lam, int64_t m, int *bad)
@@ -1115,15 +1136,17 @@ __device__ __forceinline__ float ld_any(const uint8_t *p, int idx, int dtype)
 
 __global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                   const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
-                                  const int *__restrict__ view_off, const float2 *__restrict__ eL, int N, int nsv,
-                                  int S, int D, int dtype, double *__restrict__ out)
+                                  const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
+                                  int S, int D, int64_t ne, int dtype, double *__restrict__ out)
 {
-    // sum over all agents and voxels of sum_{k in J_i} A^2 Lambda (FP64), for
-    // the normalised sigma; one warp per (agent, super-voxel)
+    // sum over reconstructions, agents and voxels of sum_{k in J_i} A^2 Lambda
+    // (FP64), for the normalised sigma; one warp per (b, agent, super-voxel)
     const int lane = threadIdx.x & 31;
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (item >= (int64_t)N * nsv) return;
-    const int g = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
+    if (item >= (int64_t)B * N * nsv) return;
+    const int pair = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
+    const int b = pair / N, g = pair - b * N;
+    eL += (int64_t)b * ne;
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint32_t *coff = col_off + gsv * (S2 + 1);
@@ -1163,27 +1186,27 @@ __global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+template <typename T>
+static void launch_forward_t(mace_state *st, unsigned blocks)
+{
+    const mace_sysmatrix *M = st->M;
+    forward_kernel<T><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
+                                                      st->d_eL, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                      M->geo.ny, M->geo.D, st->ne);
+}
+
+// e_i = y_i - A_i X_i for every reconstruction and agent
 static int launch_forward(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
-    int64_t items = (int64_t)M->N * M->nsv;
+    int64_t items = (int64_t)st->B * M->N * M->nsv;
     unsigned blocks = (unsigned)((items * 32 + 255) / 256);
-    reset_error_kernel<<<(unsigned)((st->ne + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, st->ne);
+    int64_t tot = (int64_t)st->B * st->ne;
+    reset_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, tot);
     switch (M->dtype) {
-    case MACE_F32:
-        forward_kernel<float><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
-                                                              st->d_eL, st->d_X, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
-                                                              M->geo.ny, M->geo.D);
-        break;
-    case MACE_BF16:
-        forward_kernel<__nv_bfloat16><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band,
-                                                                      M->d_view_off, st->d_eL, st->d_X, M->N, M->nsv, M->nsvx,
-                                                                      M->S, M->geo.nx, M->geo.ny, M->geo.D);
-        break;
-    default:
-        forward_kernel<__half><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
-                                                               st->d_eL, st->d_X, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
-                                                               M->geo.ny, M->geo.D);
+    case MACE_F32: launch_forward_t<float>(st, blocks); break;
+    case MACE_BF16: launch_forward_t<__nv_bfloat16>(st, blocks); break;
+    default: launch_forward_t<__half>(st, blocks); break;
     }
     CUDA_TRY(cudaGetLastError());
     return MACE_OK;
@@ -1191,13 +1214,29 @@ static int launch_forward(mace_state *st)
 
 typedef void (*sweep_fn)(SweepArgs);
 
+template <typename T, int S>
+static sweep_fn sweep_kernel_ptr_s(const mace_sysmatrix *M)
+{
+    return M->max_views <= 64 ? icd_sweep_kernel<T, 2, S> : icd_sweep_kernel<T, 0, S>;
+}
+
+template <typename T>
+static sweep_fn sweep_kernel_ptr_t(const mace_sysmatrix *M)
+{
+    switch (M->S) {
+    case 4: return sweep_kernel_ptr_s<T, 4>(M);
+    case 8: return sweep_kernel_ptr_s<T, 8>(M);
+    case 16: return sweep_kernel_ptr_s<T, 16>(M);
+    default: return nullptr;
+    }
+}
+
 static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M)
 {
-    const bool small = M->max_views <= 64;
     switch (M->dtype) {
-    case MACE_F32: return small ? icd_sweep_kernel<float, 2> : icd_sweep_kernel<float, 0>;
-    case MACE_BF16: return small ? icd_sweep_kernel<__nv_bfloat16, 2> : icd_sweep_kernel<__nv_bfloat16, 0>;
-    default: return small ? icd_sweep_kernel<__half, 2> : icd_sweep_kernel<__half, 0>;
+    case MACE_F32: return sweep_kernel_ptr_t<float>(M);
+    case MACE_BF16: return sweep_kernel_ptr_t<__nv_bfloat16>(M);
+    default: return sweep_kernel_ptr_t<__half>(M);
     }
 }
 
@@ -1210,7 +1249,7 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.col_off = M->d_col_off;
     A.band = M->d_band;
     A.view_off = M->d_view_off;
-    A.sv_order = M->d_sv_order;
+    A.sv_order = st->d_sv_order;
     A.eL = st->d_eL;
     A.X = st->d_X;
     A.w = st->d_w;
@@ -1218,6 +1257,7 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.vexp = vexp;
     A.counter = st->d_counter;
     A.status = st->d_status;
+    A.B = st->B;
     A.N = M->N;
     A.nsv = M->nsv;
     A.nsvx = M->nsvx;
@@ -1225,6 +1265,7 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.nx = M->geo.nx;
     A.ny = M->geo.ny;
     A.D = M->geo.D;
+    A.ne = st->ne;
     A.backward = backward;
     A.max_band = M->max_band;
     A.col_stride = (M->max_col_bytes + 15) & ~15;
@@ -1239,9 +1280,15 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     double bsum = 4.0 + 4.0 / std::sqrt(2.0);
     A.b_edge = (float)(1.0 / bsum);
     A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
-    CUDA_TRY(cudaMemsetAsync(st->d_counter, 0, sizeof(int) * M->N, st->stream));
+    CUDA_TRY(cudaMemsetAsync(st->d_counter, 0, sizeof(int) * st->B * M->N, st->stream));
     dim3 grid(st->sweep_warps / st->sweep_wpb), block(32 * st->sweep_wpb);
+    const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
+    if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
     sweep_kernel_ptr(M)<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    if (rec) {
+        CUDA_TRY(cudaEventRecord(st->ev[st->ev_used + 1], st->stream));
+        st->ev_used += 2;
+    }
     CUDA_TRY(cudaGetLastError());
     return MACE_OK;
 }
@@ -1258,29 +1305,49 @@ static int configure_sweep(mace_state *st)
     st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views);
     int wpb = (int)std::min<size_t>(8, (size_t)max_smem / st->warp_smem);
     if (wpb < 1) return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
-    st->sweep_wpb = wpb;
-    st->sweep_smem = st->warp_smem * wpb;
     sweep_fn fn = sweep_kernel_ptr(M);
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->sweep_smem));
+    if (!fn) return fail(MACE_EINVAL, "unsupported super-voxel size");
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(st->warp_smem * wpb)));
     int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, st->sweep_smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, st->warp_smem * wpb));
     if (per_sm < 1) per_sm = 1;
-    // concurrency C super-voxels per agent: N * C warps, all resident
+    // concurrency C super-voxels per (reconstruction, agent): B N C warps, all resident
+    const int64_t pairs = (int64_t)st->B * M->N;
     int64_t capacity = (int64_t)per_sm * nsm * wpb;
-    int64_t C = capacity / M->N;
+    int64_t C = capacity / pairs;
     if (C < 1) C = 1;
     if (st->P.concurrency > 0) C = std::min<int64_t>(C, st->P.concurrency);
     C = std::min<int64_t>(C, M->nsv);
-    int64_t warps = C * M->N;
-    if (warps > capacity) return fail(MACE_EINVAL, "more agents than resident warps; lower n_agents");
-    // whole blocks of wpb warps; the last block may be smaller, so pick the
-    // largest wpb <= configured that divides the warp count
-    int w = std::min<int64_t>(wpb, warps);
+    int64_t warps = C * pairs;
+    if (warps > capacity) return fail(MACE_EINVAL, "more (reconstruction, agent) pairs than resident warps; lower the batch");
+    // whole blocks of wpb warps: the largest wpb <= configured dividing the warp count
+    int w = (int)std::min<int64_t>(wpb, warps);
     while (warps % w) --w;
     st->sweep_wpb = w;
     st->sweep_smem = st->warp_smem * w;
     st->sweep_warps = (int)warps;
     st->concurrency = (int)C;
+    // super-voxel visiting order.  sv_order 0: the raster list of
+    // super-voxels cut into C contiguous bands, interleaved so the C in flight
+    // come from different bands (plain raster when C = 1); 1: a stride
+    // permutation spreading consecutive super-voxels over the image.
+    st->sv_order.resize(M->nsv);
+    if (st->P.sv_order == 1) {
+        int64_t p = std::max<int64_t>(1, (int64_t)llround(0.6180339887 * M->nsv));
+        while (std::gcd<int64_t>(p, M->nsv) != 1) ++p;
+        for (int k = 0; k < M->nsv; ++k) st->sv_order[k] = (int32_t)(((int64_t)k * p) % M->nsv);
+    } else {
+        std::vector<int> start(C + 1);
+        for (int64_t b = 0; b <= C; ++b) start[b] = (int)((b * M->nsv) / C);
+        int k = 0;
+        for (int j = 0; k < M->nsv; ++j)
+            for (int64_t b = 0; b < C; ++b)
+                if (start[b] + j < start[b + 1]) st->sv_order[k++] = start[b] + j;
+    }
+    if (!st->d_sv_order && cudaMalloc(&st->d_sv_order, sizeof(int32_t) * M->nsv) != cudaSuccess)
+        return fail(MACE_ENOMEM, "cudaMalloc sv order");
+    CUDA_TRY(cudaMemcpyAsync(st->d_sv_order, st->sv_order.data(), sizeof(int32_t) * M->nsv, cudaMemcpyHostToDevice,
+                             st->stream));
     return MACE_OK;
 }
 
@@ -1301,6 +1368,7 @@ static int check_params(const mace_params *P)
     if (P->max_iter < 0) return fail(MACE_EINVAL, "max_iter must be >= 0");
     if (!(P->tol >= 0)) return fail(MACE_EINVAL, "tol must be >= 0");
     if (P->concurrency < 0) return fail(MACE_EINVAL, "concurrency must be >= 0");
+    if (P->sv_order != 0 && P->sv_order != 1) return fail(MACE_EINVAL, "sv_order must be 0 or 1");
     return MACE_OK;
 }
 
@@ -1317,6 +1385,8 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_resid);
     cudaFree(st->d_counter);
     cudaFree(st->d_status);
+    cudaFree(st->d_sv_order);
+    for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
     delete st;
 }
 
@@ -1334,53 +1404,59 @@ static int copy_out(void *dst, const void *src, size_t bytes, int is_dev, cudaSt
     return MACE_OK;
 }
 
+// X^(0) = G(w^(0)) (Algorithm 1 initialisation)
 static int set_X_from_w(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
-    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, st->d_wbar, nullptr);
-    broadcast_kernel<<<(unsigned)((M->N * st->n + 255) / 256), 256, 0, st->stream>>>(st->d_wbar, st->d_X, M->N, st->n);
+    const int64_t Bn = (int64_t)st->B * st->n;
+    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, st->d_wbar, nullptr);
+    broadcast_kernel<<<(unsigned)((Bn * M->N + 255) / 256), 256, 0, st->stream>>>(st->d_wbar, st->d_X, st->B, M->N, st->n);
     CUDA_TRY(cudaGetLastError());
     return MACE_OK;
 }
 
-extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *weights, int32_t ptr_is_device,
-                         const mace_params *params, const float *w0, void *cuda_stream, mace_state **out)
+extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y, const float *weights,
+                         int32_t ptr_is_device, const mace_params *params, const float *w0, void *cuda_stream,
+                         mace_state **out)
 {
     if (!out) return fail(MACE_EINVAL, "out is NULL");
     *out = nullptr;
     if (!M || !y || !weights) return fail(MACE_EINVAL, "NULL sysmatrix, y or weights");
+    if (batch < 1 || batch > 4096) return fail(MACE_EINVAL, "batch must be in [1, 4096]");
     int rc = check_params(params);
     if (rc) return rc;
     mace_state *st = new mace_state();
     st->M = M;
     st->P = *params;
+    st->B = batch;
     st->stream = (cudaStream_t)cuda_stream;
     st->n = (int64_t)M->geo.nx * M->geo.ny;
     st->ne = (int64_t)M->V * M->geo.D;
-    const int64_t NN = (int64_t)M->N * st->n;
+    const int64_t NN = (int64_t)batch * M->N * st->n;
+    const int64_t m = (int64_t)batch * st->ne;
     auto bail = [&](int code, const std::string &msg) {
         mace_free_state(st);
         return fail(code, msg);
     };
-    if (cudaMalloc(&st->d_eL, sizeof(float2) * st->ne) != cudaSuccess ||
-        cudaMalloc(&st->d_y, sizeof(float) * st->ne) != cudaSuccess ||
+    if (cudaMalloc(&st->d_eL, sizeof(float2) * m) != cudaSuccess ||
+        cudaMalloc(&st->d_y, sizeof(float) * m) != cudaSuccess ||
         cudaMalloc(&st->d_w, sizeof(float) * NN) != cudaSuccess ||
         cudaMalloc(&st->d_X, sizeof(float) * NN) != cudaSuccess ||
-        cudaMalloc(&st->d_wbar, sizeof(double) * st->n) != cudaSuccess ||
-        cudaMalloc(&st->d_resid, sizeof(double) * 4) != cudaSuccess ||
-        cudaMalloc(&st->d_counter, sizeof(int) * M->N) != cudaSuccess ||
+        cudaMalloc(&st->d_wbar, sizeof(double) * batch * st->n) != cudaSuccess ||
+        cudaMalloc(&st->d_resid, sizeof(double) * 3 * batch) != cudaSuccess ||
+        cudaMalloc(&st->d_counter, sizeof(int) * batch * M->N) != cudaSuccess ||
         cudaMalloc(&st->d_status, sizeof(int)) != cudaSuccess)
         return bail(MACE_ENOMEM, "cudaMalloc failed for the reconstruction state");
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    st->nblk_mann = std::max(1, std::min<int>(nsm * 4, (int)((NN + 255) / 256)));
-    if (cudaMalloc(&st->d_part, sizeof(double) * 2 * st->nblk_mann) != cudaSuccess)
+    const int64_t per = (int64_t)M->N * st->n;
+    st->nblk_mann = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, nsm * 4 / batch), (per + 255) / 256));
+    if (cudaMalloc(&st->d_part, sizeof(double) * 2 * st->nblk_mann * batch) != cudaSuccess)
         return bail(MACE_ENOMEM, "cudaMalloc failed for residual partials");
     cudaStream_t s = st->stream;
     // inputs: stage on the device, validate, pack agent-major
     float *d_yin = nullptr, *d_lin = nullptr;
-    const int64_t m = st->ne;
     if (ptr_is_device) {
         d_yin = (float *)y;
         d_lin = (float *)weights;
@@ -1403,7 +1479,7 @@ extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *w
     if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
     if (ce == cudaSuccess) {
         check_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, m, st->d_status);
-        pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, d_av, M->V, M->geo.D, st->d_eL, st->d_y);
+        pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, d_av, batch, M->V, M->geo.D, st->d_eL, st->d_y);
         ce = cudaMemcpyAsync(&bad, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1411,7 +1487,7 @@ extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *w
     if (!ptr_is_device) { cudaFree(d_yin); cudaFree(d_lin); }
     if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("input packing: ") + cudaGetErrorString(ce));
     if (bad) return bail(MACE_EINVAL, "y and weights must be finite and weights >= 0");
-    CUDA_TRY(cudaMemsetAsync(st->d_status, 0, sizeof(int), s));
+    if (cudaMemsetAsync(st->d_status, 0, sizeof(int), s) != cudaSuccess) return bail(MACE_ECUDA, "memset status");
     // w^(0), X^(0) = G(w^(0)), e = y - A X
     if (w0) {
         rc = copy_in(st->d_w, w0, sizeof(float) * NN, ptr_is_device, s);
@@ -1429,16 +1505,16 @@ extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *w
         ce = cudaMalloc(&d_t2, sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_t2, 0, sizeof(double), s);
         if (ce == cudaSuccess) {
-            int64_t items = (int64_t)M->N * M->nsv;
+            int64_t items = (int64_t)batch * M->N * M->nsv;
             theta2_sum_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
-                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, M->N, M->nsv, M->S,
-                M->geo.D, (int)M->dtype, d_t2);
+                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->S,
+                M->geo.D, st->ne, (int)M->dtype, d_t2);
             ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         cudaFree(d_t2);
         if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("theta2: ") + cudaGetErrorString(ce));
-        double mean_t2 = h_t2 / ((double)M->N * (double)st->n);
+        double mean_t2 = h_t2 / ((double)batch * M->N * (double)st->n);
         if (!(mean_t2 > 0)) return bail(MACE_EINVAL, "all weights are zero");
         st->sigma_abs = params->sigma / std::sqrt(mean_t2);
     } else {
@@ -1455,36 +1531,44 @@ extern "C" int mace_init(const mace_sysmatrix *M, const float *y, const float *w
 static int run_iteration(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
-    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, st->d_wbar, nullptr);
+    const int64_t Bn = (int64_t)st->B * st->n;
+    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, st->d_wbar, nullptr);
     CUDA_TRY(cudaGetLastError());
     for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
         int rc = launch_sweep(st, st->P.symmetric ? (k & 1) : 0, nullptr);
         if (rc) return rc;
     }
-    mann_kernel<<<st->nblk_mann, 256, 0, st->stream>>>(st->d_w, st->d_X, st->d_wbar, M->N, st->n, (float)st->P.rho,
-                                                       st->d_part);
-    residual_kernel<<<1, 32, 0, st->stream>>>(st->d_part, st->nblk_mann, st->d_resid);
+    mann_kernel<<<dim3(st->nblk_mann, st->B), 256, 0, st->stream>>>(st->d_w, st->d_X, st->d_wbar, M->N, st->n,
+                                                                    (float)st->P.rho, st->d_part);
+    residual_kernel<<<(st->B + 127) / 128, 128, 0, st->stream>>>(st->d_part, st->nblk_mann, st->B, st->d_resid);
     CUDA_TRY(cudaGetLastError());
     st->iters++;
     if (st->P.recompute_every > 0 && st->iters % st->P.recompute_every == 0) return launch_forward(st);
     return MACE_OK;
 }
 
+// largest relative Mann residual over the batch
 static int read_status(mace_state *st, double *r)
 {
-    double h[4];
+    std::vector<double> h(3 * st->B);
     int status = 0;
-    CUDA_TRY(cudaMemcpyAsync(h, st->d_resid, sizeof(double) * 3, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaMemcpyAsync(h.data(), st->d_resid, sizeof(double) * 3 * st->B, cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));
     if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
-    *r = h[2];
-    st->last_resid = h[2];
-    if (!std::isfinite(h[2])) return fail(MACE_ENUMERIC, "non-finite Mann residual (divergence)");
+    double worst = 0.0;
+    for (int b = 0; b < st->B; ++b) {
+        double rb = h[3 * b + 2];
+        if (!std::isfinite(rb)) { worst = rb; break; }
+        worst = std::max(worst, rb);
+    }
+    *r = worst;
+    st->last_resid = worst;
+    if (!std::isfinite(worst)) return fail(MACE_ENUMERIC, "non-finite Mann residual (divergence)");
     return MACE_OK;
 }
 
-extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out, int32_t *converged_out)
+extern "C" int mace_launch(mace_state *st, int32_t n_iters)
 {
     if (!st) return fail(MACE_EINVAL, "state is NULL");
     if (n_iters < 0) return fail(MACE_EINVAL, "n_iters must be >= 0");
@@ -1492,8 +1576,14 @@ extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_ou
         int rc = run_iteration(st);
         if (rc) return rc;
     }
+    return MACE_OK;
+}
+
+extern "C" int mace_poll(mace_state *st, double *residual_out, int32_t *converged_out)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
     double r = st->last_resid;
-    if (n_iters > 0) {
+    if (st->iters > 0) {
         int rc = read_status(st, &r);
         if (rc) return rc;
     }
@@ -1502,16 +1592,56 @@ extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_ou
     return MACE_OK;
 }
 
+extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out, int32_t *converged_out)
+{
+    int rc = mace_launch(st, n_iters);
+    if (rc) return rc;
+    return mace_poll(st, residual_out, converged_out);
+}
+
+extern "C" int mace_set_timing(mace_state *st, int32_t enable, int32_t max_launches)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    if (enable && max_launches < 1) return fail(MACE_EINVAL, "max_launches must be >= 1");
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    st->ev_used = 0;
+    st->timing = enable != 0;
+    size_t need = enable ? (size_t)2 * max_launches : 0;
+    while (st->ev.size() < need) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        st->ev.push_back(e);
+    }
+    return MACE_OK;
+}
+
+extern "C" int mace_get_timing(mace_state *st, double *sweep_ms, int32_t *launches)
+{
+    if (!st || !sweep_ms || !launches) return fail(MACE_EINVAL, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    double tot = 0.0;
+    for (int k = 0; k + 1 < st->ev_used; k += 2) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, st->ev[k], st->ev[k + 1]));
+        tot += ms;
+    }
+    *sweep_ms = tot;
+    *launches = st->ev_used / 2;
+    st->ev_used = 0;
+    return MACE_OK;
+}
+
 extern "C" int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device)
 {
     if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
     const mace_sysmatrix *M = st->M;
+    const int64_t Bn = (int64_t)st->B * st->n;
     float *d_x = ptr_is_device ? x_out : nullptr;
-    if (!d_x && cudaMalloc(&d_x, sizeof(float) * st->n) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc x");
-    consensus_kernel<<<(unsigned)((st->n + 255) / 256), 256, 0, st->stream>>>(st->d_w, M->N, st->n, nullptr, d_x);
+    if (!d_x && cudaMalloc(&d_x, sizeof(float) * Bn) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc x");
+    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, nullptr, d_x);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess && !ptr_is_device) {
-        ce = cudaMemcpyAsync(x_out, d_x, sizeof(float) * st->n, cudaMemcpyDeviceToHost, st->stream);
+        ce = cudaMemcpyAsync(x_out, d_x, sizeof(float) * Bn, cudaMemcpyDeviceToHost, st->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st->stream);
     }
     if (!ptr_is_device) cudaFree(d_x);
@@ -1546,7 +1676,7 @@ extern "C" int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_dev
 extern "C" int mace_get_state(mace_state *st, float *w, float *X, int32_t ptr_is_device)
 {
     if (!st) return fail(MACE_EINVAL, "state is NULL");
-    size_t bytes = sizeof(float) * st->M->N * st->n;
+    size_t bytes = sizeof(float) * st->B * st->M->N * st->n;
     if (w) { int rc = copy_out(w, st->d_w, bytes, ptr_is_device, st->stream); if (rc) return rc; }
     if (X) { int rc = copy_out(X, st->d_X, bytes, ptr_is_device, st->stream); if (rc) return rc; }
     return MACE_OK;
@@ -1555,7 +1685,7 @@ extern "C" int mace_get_state(mace_state *st, float *w, float *X, int32_t ptr_is
 extern "C" int mace_set_state(mace_state *st, const float *w, const float *X, int32_t ptr_is_device)
 {
     if (!st || !w || !X) return fail(MACE_EINVAL, "NULL argument");
-    size_t bytes = sizeof(float) * st->M->N * st->n;
+    size_t bytes = sizeof(float) * st->B * st->M->N * st->n;
     int rc = copy_in(st->d_w, w, bytes, ptr_is_device, st->stream);
     if (!rc) rc = copy_in(st->d_X, X, bytes, ptr_is_device, st->stream);
     if (!rc) rc = launch_forward(st);
@@ -1569,7 +1699,7 @@ extern "C" int mace_set_state(mace_state *st, const float *w, const float *X, in
 extern "C" int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_device, int32_t backward)
 {
     if (!st || !v) return fail(MACE_EINVAL, "NULL argument");
-    size_t bytes = sizeof(float) * st->M->N * st->n;
+    size_t bytes = sizeof(float) * st->B * st->M->N * st->n;
     if (!st->d_vexp && cudaMalloc(&st->d_vexp, bytes) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc v");
     int rc = copy_in(st->d_vexp, v, bytes, ptr_is_device, st->stream);
     if (!rc) rc = launch_sweep(st, backward ? 1 : 0, st->d_vexp);
@@ -1582,13 +1712,28 @@ extern "C" int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_dev
     return rc;
 }
 
-extern "C" int64_t mace_error_size(const mace_state *st) { return st ? st->ne : -1; }
+extern "C" int64_t mace_error_size(const mace_state *st) { return st ? (int64_t)st->B * st->ne : -1; }
+
+extern "C" int mace_get_visit_order(const mace_state *st, int64_t *order)
+{
+    if (!st || !order) return fail(MACE_EINVAL, "NULL argument");
+    const mace_sysmatrix *M = st->M;
+    int64_t k = 0;
+    for (int q = 0; q < M->nsv; ++q) {
+        int sv = st->sv_order[q], si = sv / M->nsvx, sj = sv % M->nsvx;
+        for (int t = 0; t < M->S2; ++t) {
+            int i = si * M->S + t / M->S, j = sj * M->S + t % M->S;
+            if (i < M->geo.ny && j < M->geo.nx) order[k++] = (int64_t)i * M->geo.nx + j;
+        }
+    }
+    return MACE_OK;
+}
 
 extern "C" int mace_get_error(mace_state *st, float *e, int32_t ptr_is_device)
 {
     if (!st || !e) return fail(MACE_EINVAL, "NULL argument");
     // strided copy of the .x components
-    CUDA_TRY(cudaMemcpy2DAsync(e, sizeof(float), st->d_eL, sizeof(float2), sizeof(float), st->ne,
+    CUDA_TRY(cudaMemcpy2DAsync(e, sizeof(float), st->d_eL, sizeof(float2), sizeof(float), (size_t)st->B * st->ne,
                                ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));
     return MACE_OK;

@@ -217,10 +217,10 @@ def prior_sigma_x(lam, n_views, frac=0.1):
 CONFIGS = {
     # 64^2, 90 views, 95 channels, 4 interleaved agents, quadratic prior
     "cfg1": dict(n=64, n_views=90, n_channels=95, I0=1e4, mu_max=0.02, n_agents=4,
-                 prior="quadratic", seed=1, noise_seed=101),
+                 prior="quadratic", seed=1, noise_seed=101, prior_frac=1.0),
     # 512^2, 720 views, 725 channels, 16 agents x 45 views, Q-GGMRF
     "cfg2": dict(n=512, n_views=720, n_channels=725, I0=2e4, mu_max=0.02 * 64 / 512,
-                 n_agents=16, prior="qggmrf", seed=2, noise_seed=102),
+                 n_agents=16, prior="qggmrf", seed=2, noise_seed=102, prior_frac=1.0),
 }
 
 

@@ -1,0 +1,64 @@
+"""Write the FP64 oracle's converged MAP image for a synthetic workload.
+
+Calls only the oracle (and the seeded input generator): the stored image is
+the oracle's, never the CUDA library's.  The reference is partial-update MACE
+(Algorithm 1, small normalised sigma = 0.1 where Theorem 2 guarantees
+convergence, symmetric ICD passes in raster order) run until the relative
+KKT residual of the MAP cost (Sec. II-A), ||grad f(x)|| / ||grad f(0)||,
+is below the target; the value reached is stored beside the image.
+
+Usage: python tests/golden/make_reference.py cfg2 [threads]
+"""
+import hashlib
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+def inputs_digest(y, lam):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(y, np.float32).tobytes())
+    h.update(np.ascontiguousarray(lam, np.float32).tobytes())
+    return h.hexdigest()
+
+
+def main(name, threads=0, target=1e-9, max_iter=20000, chunk=50):
+    cfg = dict(synth.CONFIGS[name])
+    c = synth.make_case(**cfg)
+    y, lam = c["y"][0], c["lam"][0]
+    n, V, D, N = cfg["n"], cfg["n_views"], cfg["n_channels"], cfg["n_agents"]
+    sx = synth.prior_sigma_x(lam, V, frac=cfg.get("prior_frac", 1.0))
+    P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior=cfg["prior"], sigma_x=sx)
+    t0 = time.time()
+    t2 = oracle.mean_theta2(P)
+    sigma = 0.1 / math.sqrt(t2)
+    g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
+    out = os.path.join(HERE, "%s_reference.npz" % name)
+    w = X = None
+    iters = 0
+    kkt = 1.0
+    while iters < max_iter and kkt > target:
+        res = P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=chunk, tol=0.0,
+                     w0=w, X0=X, n_threads=threads)
+        w, X = res["w"], res["X"]
+        iters += res["iters"]
+        x = res["x"]
+        kkt = np.linalg.norm(P.gradient(x)) / g0
+        print("%s: iters=%d resid=%.2e kkt=%.2e time=%.0fs" % (name, iters, res["resid"], kkt,
+                                                            time.time() - t0), flush=True)
+        np.savez_compressed(out, x=x.astype(np.float64), iters=iters, resid=res["resid"],
+                            kkt=kkt, sigma_x=sx, digest=inputs_digest(y, lam))
+    print("-> %s" % out)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1], int(sys.argv[2]) if len(sys.argv) > 2 else 0)
