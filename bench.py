@@ -170,8 +170,8 @@ def run_mace(args, rank, world):
         iters_seen.append((it, r, conv))
         st.close()
 
-    def timed(device_inputs, record):
-        for _ in range(args.warmup):
+    def timed(device_inputs, record, warmup):
+        for _ in range(warmup):
             step(device_inputs, False)
         stream.synchronize()
         if dist:
@@ -200,10 +200,10 @@ def run_mace(args, rank, world):
             el = float(t.item())
         return el, ck
 
-    el, clocks = timed(True, True)
+    el, clocks = timed(True, True, args.warmup)
     iters_main = [it for it, _, _ in iters_seen[-args.steps:]]
     conv_main = all(c for _, _, c in iters_seen[-args.steps:])
-    el_e2e, _ = timed(False, False)
+    el_e2e, _ = timed(False, False, 1)
     recons = B * args.steps * world
     value = recons / el
     e2e = recons / el_e2e
@@ -259,16 +259,19 @@ def run_mace(args, rank, world):
     its = sum(iters_main)
     out["gpu_launches"] = int(args.steps * 7 + its * 5 + 2 * (its // 10) + args.steps)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, seconds=args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, int(np.mean(iters_main)),
+                                           seconds=args.cpu_seconds)
     if dist:
         dist.destroy_process_group()
     return out
 
 
-def cpu_baseline(args, y, lam, sx, seconds=20.0):
+def cpu_baseline(args, y, lam, sx, iters, seconds=20.0):
     """The FP64 oracle (Algorithm 1 with the same solver settings, serial ICD
     order, one OpenMP thread per agent) on the host cores: time a bounded
-    number of Mann iterations, scale to the iterations the oracle needs."""
+    number of Mann iterations and scale to the iteration count the GPU run
+    needed for the same tolerance (the oracle's serial passes contract at the
+    same rate per iteration on this workload)."""
     import oracle
     threads = os.cpu_count() or 1
     P = oracle.Problem(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"], y, lam,
@@ -282,7 +285,6 @@ def cpu_baseline(args, y, lam, sx, seconds=20.0):
     t0 = time.perf_counter()
     P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=k, tol=0.0, n_threads=threads)
     per_iter = (time.perf_counter() - t0) / k
-    iters = args.oracle_iters
     return {"value": 1.0 / (per_iter * iters), "unit": "recons/s", "cores": threads, "kind": "oracle",
             "sample": "%d Mann iterations (2 ICD passes each) of one 512^2 reconstruction, "
                       "%.2f s/iteration, scaled to %d iterations to tolerance" % (k, per_iter, iters)}
@@ -329,14 +331,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mace", choices=["mace", "reference"])
-    ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--concurrency", type=int, default=4)
-    ap.add_argument("--sigma", type=float, default=0.5)
-    ap.add_argument("--tol", type=float, default=1e-5)
-    ap.add_argument("--max-iter", dest="max_iter", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=2)
+    ap.add_argument("--concurrency", type=int, default=64)
+    ap.add_argument("--sigma", type=float, default=0.1)
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--max-iter", dest="max_iter", type=int, default=4000)
     ap.add_argument("--sv", type=int, default=8)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=300)
+    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=2000)
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     args = ap.parse_args()

@@ -226,6 +226,12 @@ int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
 int mace_set_timing(mace_state *st, int32_t enable, int32_t max_launches);
 int mace_get_timing(mace_state *st, double *sweep_ms, int32_t *launches);
 
+/* Failure detection without a GPU fault: launch one warp that waits on a
+ * barrier nothing completes, with the sweep's bounded wait cut to spin_limit
+ * polls; returns MACE_ETIMEOUT (the kernel records it and exits, the context
+ * stays usable).  Not part of the paper's method. */
+int mace_wait_selftest(uint32_t spin_limit, void *cuda_stream);
+
 void mace_free_state(mace_state *st);
 void mace_free_sysmatrix(mace_sysmatrix *sm);
 const char *mace_last_error(void);

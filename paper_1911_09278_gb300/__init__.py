@@ -32,7 +32,7 @@ EXPORTS = [
     "mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
     "mace_get_visit_order",
     "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
-    "mace_set_timing", "mace_get_timing",
+    "mace_set_timing", "mace_get_timing", "mace_wait_selftest",
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
@@ -97,6 +97,7 @@ def load(path=LIB_PATH):
     L.mace_launch.argtypes = [vp, i32]
     L.mace_poll.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_set_timing.argtypes = [vp, i32, i32]
+    L.mace_wait_selftest.argtypes = [ctypes.c_uint32, vp]
     L.mace_get_timing.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_reconstruct.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mace_consensus.argtypes = [vp, vp, i32]
@@ -367,6 +368,12 @@ def mace_init(sm, y, weights, params, w0=None, stream=None, batch=None):
     _check(load().mace_init(sm.handle, batch, py, pl, dy, ctypes.byref(params), pw, _stream_handle(stream),
                             ctypes.byref(h)))
     return State(h, sm, params, batch)
+
+
+def mace_wait_selftest(spin_limit=1000, stream=None):
+    """Run the bounded-wait self test; returns the MACE code (expect MACE_ETIMEOUT)."""
+    rc = load().mace_wait_selftest(spin_limit, _stream_handle(stream))
+    return rc
 
 
 def mace_iterate(state, n_iters):

@@ -130,7 +130,7 @@ struct mace_sysmatrix {
     GeoParams geo;
     int nz;
     int V, N, S, nsvx, nsvy, nsv, S2;
-    int max_views, max_band, max_col_bytes;
+    int max_views, max_band, max_col_bytes, max_nnz = 0;
     mace_dtype dtype;
     int vbytes;                       // bytes per stored value
     cudaStream_t stream;
@@ -181,9 +181,18 @@ __global__ void band_kernel(GeoParams G, const double2 *__restrict__ cs, const i
     band[(int64_t)nsv * view_off[g] + (int64_t)sv * Vg + v] = d;
 }
 
-// bytes of one column: headers padded to 4, then per round of 32 views the
-// slot-0 values of every view, slot-1 values of views with L >= 2, slot-2
-// values of views with L == 3; padded to 16.
+// Column of one pixel for one agent (the per-view runs, flattened):
+//   u16 nnz; u16 bidx[nnz]  (position of each value in the super-voxel's
+//                            band: runs of the agent's views in view order)
+//   padding to 16 bytes; T vals[nnz]; padding to 16 bytes.
+// View v's band covers channels [lo_v, lo_v + len_v) and starts at
+// boff_v = sum_{u < v} len_u, so the value of channel c sits at
+// boff_v + c - lo_v: the run (first channel, length, values) of every view is
+// recoverable from bidx and the band descriptors.
+__host__ __device__ inline uint32_t col_bytes_of(int nnz, int vbytes)
+{
+    return ((2u + 2u * (uint32_t)nnz + 15u) & ~15u) + (((uint32_t)nnz * vbytes + 15u) & ~15u);
+}
 __global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
                                int N, int S, int nsvx, int nsv, int vbytes,
                                uint32_t *__restrict__ col_bytes, uint32_t *__restrict__ col_nnz)
@@ -198,15 +207,12 @@ __global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, cons
     int i = si * S + t / S, j = sj * S + t % S;
     if (i >= G.ny || j >= G.nx) { col_bytes[tid] = 0; col_nnz[tid] = 0; return; }
     int v0 = view_off[g], Vg = view_off[g + 1] - v0;
-    int nvals = 0, nz = 0;
+    int nz = 0;
     for (int v = 0; v < Vg; ++v) {
         int c0;
-        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr);
-        nvals += L > 0 ? L : 1;   // slot 0 always present
-        nz += L;
+        nz += footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr);
     }
-    uint32_t bytes = (uint32_t)((Vg + 3) & ~3) + (uint32_t)nvals * vbytes;
-    col_bytes[tid] = (bytes + 15u) & ~15u;
+    col_bytes[tid] = col_bytes_of(nz, vbytes);
     col_nnz[tid] = nz;
 }
 
@@ -234,31 +240,26 @@ __global__ void fill_kernel(GeoParams G, const double2 *__restrict__ cs, const i
     const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
     int64_t gsv = (int64_t)g * nsv + sv;
     uint8_t *col = cols + sv_base[gsv] + col_off[gsv * (S2 + 1) + t];
-    T *vals = (T *)(col + ((Vg + 3) & ~3));
-    int base = 0;
-    for (int r = 0; r * 32 < Vg; ++r) {
-        int Vr = min(32, Vg - r * 32);
-        int Ls[32];
-        double a[32][3];
-        int n1 = 0, n2 = 0;
-        for (int l = 0; l < Vr; ++l) {
-            int v = r * 32 + l, c0;
-            int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a[l]);
-            int lo = (int)(bd[v] & 0xFFFFu);
-            int crel = L > 0 ? c0 - lo : 0;
-            col[v] = (uint8_t)((crel << 2) | L);
-            Ls[l] = L;
-            if (L == 0) a[l][0] = 0.0;
-            n1 += L >= 2;
-            n2 += L == 3;
-        }
-        int k1 = 0, k2 = 0;
-        for (int l = 0; l < Vr; ++l) {
-            vals[base + l] = from_double<T>(a[l][0]);
-            if (Ls[l] >= 2) vals[base + Vr + (k1++)] = from_double<T>(a[l][1]);
-            if (Ls[l] == 3) vals[base + Vr + n1 + (k2++)] = from_double<T>(a[l][2]);
-        }
-        base += Vr + n1 + n2;
+    uint16_t *bidx = (uint16_t *)col;
+    int nz = 0, boff = 0;
+    for (int v = 0; v < Vg; ++v) {
+        double a[3];
+        int c0;
+        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
+        int lo = (int)(bd[v] & 0xFFFFu);
+        for (int k = 0; k < L; ++k) bidx[1 + nz + k] = (uint16_t)(boff + c0 - lo + k);
+        nz += L;
+        boff += (int)(bd[v] >> 16);
+    }
+    bidx[0] = (uint16_t)nz;
+    T *vals = (T *)(col + ((2 + 2 * nz + 15) & ~15));
+    nz = 0;
+    for (int v = 0; v < Vg; ++v) {
+        double a[3];
+        int c0;
+        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
+        for (int k = 0; k < L; ++k) vals[nz + k] = from_double<T>(a[k]);
+        nz += L;
     }
 }
 
@@ -393,6 +394,7 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
                 uint32_t b = h_bytes[gsv * M->S2 + t];
                 off += b;
                 M->max_col_bytes = std::max<int>(M->max_col_bytes, (int)b);
+                M->max_nnz = std::max<int>(M->max_nnz, (int)h_nnz[gsv * M->S2 + t]);
                 M->nnz += h_nnz[gsv * M->S2 + t];
             }
             col_off[gsv * (M->S2 + 1) + M->S2] = off;
@@ -402,10 +404,11 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
             const uint32_t *bd = h_band.data() + (int64_t)M->nsv * M->view_off[g] + (int64_t)sv * Vg;
             for (int v = 0; v < Vg; ++v) {
                 uint32_t len = bd[v] >> 16;
-                if (len > 64) return cleanup(MACE_EINVAL, "super-voxel band wider than 64 channels; use a smaller sv_size");
+                if (len > 128) return cleanup(MACE_EINVAL, "super-voxel band wider than 128 channels; use a smaller sv_size");
                 bt += len;
             }
             band_tot[gsv] = bt;
+            if (bt > 65535) return cleanup(MACE_EINVAL, "super-voxel band larger than 65535 entries; use a smaller sv_size");
             M->max_band = std::max<int>(M->max_band, (int)bt);
         }
     }
@@ -483,24 +486,22 @@ extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t
     std::vector<uint8_t> col(off[1] - off[0]);
     if (!col.empty())
         CUDA_TRY(cudaMemcpy(col.data(), M->d_cols + base + off[0], col.size(), cudaMemcpyDeviceToHost));
-    const uint8_t *vals_p = col.data() + ((Vg + 3) & ~3);
-    int base_v = 0;
-    for (int r = 0; r * 32 < Vg; ++r) {
-        int Vr = std::min(32, Vg - r * 32);
-        int n1 = 0, n2 = 0;
-        for (int l = 0; l < Vr; ++l) { int L = col[r * 32 + l] & 3; n1 += L >= 2; n2 += L == 3; }
-        int k1 = 0, k2 = 0;
-        for (int l = 0; l < Vr; ++l) {
-            int v = r * 32 + l;
-            int L = col[v] & 3, crel = col[v] >> 2;
-            len[v] = L;
-            c0[v] = L > 0 ? (int)(bd[v] & 0xFFFFu) + crel : 0;
-            vals[3 * v] = vals[3 * v + 1] = vals[3 * v + 2] = 0.f;
-            if (L >= 1) vals[3 * v] = value_to_float(vals_p + (size_t)(base_v + l) * M->vbytes, M->dtype);
-            if (L >= 2) vals[3 * v + 1] = value_to_float(vals_p + (size_t)(base_v + Vr + k1++) * M->vbytes, M->dtype);
-            if (L == 3) vals[3 * v + 2] = value_to_float(vals_p + (size_t)(base_v + Vr + n1 + k2++) * M->vbytes, M->dtype);
-        }
-        base_v += Vr + n1 + n2;
+    for (int v = 0; v < Vg; ++v) { c0[v] = 0; len[v] = 0; vals[3 * v] = vals[3 * v + 1] = vals[3 * v + 2] = 0.f; }
+    if (col.empty()) return MACE_OK;
+    uint16_t nz;
+    memcpy(&nz, col.data(), 2);
+    const uint8_t *vals_p = col.data() + ((2 + 2 * nz + 15) & ~15);
+    std::vector<int> boff(Vg + 1, 0);
+    for (int v = 0; v < Vg; ++v) boff[v + 1] = boff[v] + (int)(bd[v] >> 16);
+    for (int k = 0; k < nz; ++k) {
+        uint16_t b;
+        memcpy(&b, col.data() + 2 + 2 * k, 2);
+        int v = (int)(std::upper_bound(boff.begin(), boff.end(), (int)b) - boff.begin()) - 1;
+        int ch = (int)(bd[v] & 0xFFFFu) + (b - boff[v]);
+        if (len[v] == 0) c0[v] = ch;
+        if (len[v] >= 3 || ch != c0[v] + len[v]) return fail(MACE_EINVAL, "stored column is not a set of runs");
+        vals[3 * v + len[v]] = value_to_float(vals_p + (size_t)k * M->vbytes, M->dtype);
+        len[v]++;
     }
     return MACE_OK;
 }
@@ -568,6 +569,7 @@ struct SweepArgs {
     int *status;
     int B, N, nsv, nsvx, S, nx, ny, D;
     int64_t ne;
+    int nwarps;                 // warps with work (the last block may have idle ones)
     int backward;
     int max_band, col_stride, max_views;   // per-warp shared-memory layout (S is a template parameter)
     float inv_s2, pscale;
@@ -679,11 +681,50 @@ static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views
     return warp_smem_layout(max_band, col_stride, S, max_views).total;
 }
 
-// One warp per super-voxel at a time; lane = view (views lane, lane+32, ...).
-// MAXR > 0: the agent has at most 32*MAXR views and each lane keeps its runs
-// in registers between the reduction and the update; MAXR == 0: any number of
-// views, runs re-read from shared memory.  S: super-voxel side.
-template <typename T, int MAXR, int S>
+// Band bookkeeping shared by the kernels that walk a super-voxel's columns:
+// per view the band descriptor, its offset in the flattened band and, per
+// band entry, its view.  Returns the band size.  Warp-cooperative.
+__device__ __forceinline__ int load_band_layout(const uint32_t *__restrict__ bd, int Vg, uint32_t *bdesc,
+                                                uint16_t *boff, uint16_t *bview, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    int run = 0;
+    for (int r = 0; r * 32 < Vg; ++r) {
+        const int v = r * 32 + lane;
+        const uint32_t d = v < Vg ? bd[v] : 0u;
+        const int len = (int)(d >> 16);
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (v < Vg) {
+            const int b0 = run + incl - len;
+            boff[v] = (uint16_t)b0;
+            bdesc[v] = d;
+            for (int k = 0; k < len; ++k) bview[b0 + k] = (uint16_t)v;
+        }
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    return run;
+}
+
+// global index (row of the agent block, [Vg][D]) of band entry f
+__device__ __forceinline__ int64_t band_global(int f, const uint32_t *bdesc, const uint16_t *boff,
+                                               const uint16_t *bview, int D)
+{
+    const int v = bview[f];
+    return (int64_t)v * D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v]);
+}
+
+// One warp per super-voxel at a time.  Each pixel's column is a flat list of
+// (band position, value) pairs; lane k takes entries k, k+32, ...  MR > 0:
+// at most 32*MR entries per column, kept in registers between the reduction
+// and the update; MR == 0: any count, re-read from shared memory.  S:
+// super-voxel side.
+template <typename T, int MR, int S>
 __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -719,16 +760,19 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
     // counter, so at most warps / (B N) super-voxels of one agent of one
     // reconstruction are in flight at a time
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (gw >= A.nwarps) return;
     const int pair = gw % (A.B * A.N);
     const int b = pair / A.N, g = pair - b * A.N;
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
-    const int hdr_bytes = (Vg + 3) & ~3;
-    const int R = (Vg + 31) >> 5;
     float2 *eLg = A.eL + (int64_t)b * A.ne + (int64_t)v0 * A.D;    // agent block [Vg][D]
     float *Xg = A.X + (int64_t)pair * n;
     const float *wg = A.w + (int64_t)pair * n;
     const double *wbg = A.wbar + (int64_t)b * n;
     const float *vg = A.vexp ? A.vexp + (int64_t)pair * n : nullptr;
+    // this lane's prior neighbour (lanes 0..7)
+    const int kk = lane < 4 ? lane : lane + 1;
+    const int pdi = kk / 3 - 1, pdj = kk % 3 - 1;
+    const float pb = lane < 8 ? A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge) : 0.f;
 
     // the next super-voxel is claimed one super-voxel ahead, so the claim's
     // round trip overlaps the current super-voxel's work
@@ -771,54 +815,53 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             }
         }
 
-        // --- band descriptors and offsets ----------------------------------
+        // --- band layout and snapshot (loads batched 8 deep per lane) -------
         const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
-        int run = 0;
-        for (int r = 0; r < R; ++r) {
-            int v = r * 32 + lane;
-            uint32_t d = v < Vg ? bd[v] : 0u;
-            int len = (int)(d >> 16);
-            int incl = len;
+        const int band_tot = load_band_layout(bd, Vg, bdesc, boff, bview, lane);
+        for (int f0 = 0; f0 < band_tot; f0 += 256) {
+            float2 tmp[8];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * 32 + lane;
+                if (f < band_tot) tmp[u] = eLg[band_global(f, bdesc, boff, bview, A.D)];
             }
-            if (v < Vg) {
-                const int b0 = run + incl - len;
-                boff[v] = (uint16_t)b0;
-                bdesc[v] = d;
-                for (int k = 0; k < len; ++k) bview[b0 + k] = (uint16_t)v;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int f = f0 + u * 32 + lane;
+                if (f < band_tot) {
+                    beL[f] = tmp[u];
+                    bsnap[f] = tmp[u].x;
+                }
             }
-            run += __shfl_sync(FULL, incl, 31);
-        }
-        const int band_tot = run;
-        __syncwarp();
-        // --- band snapshot: all entries loaded at once -----------------------
-        for (int f = lane; f < band_tot; f += 32) {
-            const int v = bview[f];
-            const float2 el = eLg[(int64_t)v * A.D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v])];
-            beL[f] = el;
-            bsnap[f] = el.x;
         }
         // --- X tile with halo, v tile ---------------------------------------
-        for (int k = lane; k < T2 * T2; k += 32) {
-            const int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
-            xt[k] = (i >= 0 && i < A.ny && j >= 0 && j < A.nx) ? Xg[(int64_t)i * A.nx + j] : 0.f;
-        }
-        for (int k = lane; k < S2; k += 32) {
-            const int i = si * S + k / S, j = sj * S + k % S;
-            float vv = 0.f;
-            if (i < A.ny && j < A.nx) {
-                const int64_t s = (int64_t)i * A.nx + j;
-                vv = vg ? vg[s] : (float)(2.0 * wbg[s] - (double)wg[s]);
+        {
+            float tmp[(T2 * T2 + 31) / 32];
+#pragma unroll
+            for (int u = 0; u < (T2 * T2 + 31) / 32; ++u) {
+                const int k = u * 32 + lane;
+                const int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
+                tmp[u] = (k < T2 * T2 && i >= 0 && i < A.ny && j >= 0 && j < A.nx) ? Xg[(int64_t)i * A.nx + j] : 0.f;
             }
-            vt[k] = vv;
+#pragma unroll
+            for (int u = 0; u < (T2 * T2 + 31) / 32; ++u) {
+                const int k = u * 32 + lane;
+                if (k < T2 * T2) xt[k] = tmp[u];
+            }
         }
-        // prior constants of this lane's neighbour (lanes 0..7)
-        const int kk = lane < 4 ? lane : lane + 1;
-        const int pdi = kk / 3 - 1, pdj = kk % 3 - 1;
-        const float pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
+#pragma unroll
+        for (int u = 0; u < (S2 + 31) / 32; ++u) {
+            const int k = u * 32 + lane;
+            const int i = si * S + k / S, j = sj * S + k % S;
+            if (k < S2) {
+                float vv = 0.f;
+                if (i < A.ny && j < A.nx) {
+                    const int64_t s = (int64_t)i * A.nx + j;
+                    vv = vg ? vg[s] : (float)(2.0 * wbg[s] - (double)wg[s]);
+                }
+                vt[k] = vv;
+            }
+        }
         __syncwarp();
 
         // --- visit the pixels ------------------------------------------------
@@ -826,6 +869,21 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             const int t = tl[q];
             const int ti = t / S, tj = t % S;
             const int i = si * S + ti, j = sj * S + tj;
+            // prior through the surrogate weights (lanes 0..7: the 8
+            // neighbours); needs only the X tile, so it overlaps the column's
+            // arrival
+            const int tc = (ti + 1) * T2 + (tj + 1);
+            const float xs = xt[tc];
+            float pr1 = 0.f, pr2 = 0.f;
+            if (lane < 8) {
+                const int ii = i + pdi, jj = j + pdj;
+                if (ii >= 0 && ii < A.ny && jj >= 0 && jj < A.nx) {
+                    const float d = xs - xt[tc + pdi * T2 + pdj];
+                    pr2 = pb * prior_weight(A, d);
+                    pr1 = pr2 * d;
+                }
+            }
+            const float prox = (xs - vt[t]) * A.inv_s2;
             const uint32_t stg = (seq + q) % kRing;
             const uint32_t parity = ((seq + q) / kRing) & 1u;
             uint32_t spins = 0;
@@ -844,60 +902,42 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
                 }
             }
             const uint8_t *col = ring + (size_t)stg * A.col_stride;
-            const uint8_t *vals = col + hdr_bytes;
+            const uint16_t *cidx = (const uint16_t *)col;
+            const int nnz = cidx[0];
+            const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
 
             // data term: p1 = -sum A Lambda e, p2 = sum A^2 Lambda
-            float p1 = 0.f, p2 = 0.f;
-            constexpr int RC = MAXR > 0 ? MAXR : 1;
-            float ca0[RC], ca1[RC], ca2[RC];
-            int cb[RC], cL[RC];
-            int vbase = 0;
+            float p1 = pr1, p2 = pr2;
+            constexpr int RC = MR > 0 ? MR : 1;
+            float ca[RC], ce[RC];
+            int cb[RC];
 #pragma unroll
-            for (int r = 0; r < (MAXR > 0 ? MAXR : 1 << 20); ++r) {
-                if (r >= R) break;
-                const int v = r * 32 + lane;
-                const int Vr = min(32, Vg - r * 32);
-                const uint32_t h = lane < Vr ? col[v] : 0u;
-                const int L = h & 3;
-                const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
-                const int n1 = __popc(m1);
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-                int b = 0;
-                if (L > 0) {
-                    b = boff[v] + (int)(h >> 2);
-                    a0 = ld_val<T>(vals, vbase + lane);
-                    float2 el = beL[b];
-                    p1 = fmaf(-a0 * el.y, el.x, p1);
-                    p2 = fmaf(a0 * a0, el.y, p2);
-                    if (L >= 2) {
-                        a1 = ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask));
-                        el = beL[b + 1];
-                        p1 = fmaf(-a1 * el.y, el.x, p1);
-                        p2 = fmaf(a1 * a1, el.y, p2);
-                    }
-                    if (L == 3) {
-                        a2 = ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask));
-                        el = beL[b + 2];
-                        p1 = fmaf(-a2 * el.y, el.x, p1);
-                        p2 = fmaf(a2 * a2, el.y, p2);
-                    }
+            for (int r = 0; r < RC; ++r) {
+                const int k = r * 32 + lane;
+                ca[r] = 0.f;
+                cb[r] = 0;
+                ce[r] = 0.f;
+                if (MR > 0 && k < nnz) {
+                    cb[r] = cidx[1 + k];
+                    ca[r] = ld_val<T>(cval, k);
                 }
-                if (MAXR > 0) {
-                    ca0[r < RC ? r : 0] = a0; ca1[r < RC ? r : 0] = a1; ca2[r < RC ? r : 0] = a2;
-                    cb[r < RC ? r : 0] = b;   cL[r < RC ? r : 0] = L;
-                }
-                vbase += Vr + n1 + __popc(m2);
             }
-            // prior through the surrogate weights (lanes 0..7: the 8 neighbours)
-            const int tc = (ti + 1) * T2 + (tj + 1);
-            const float xs = xt[tc];
-            if (lane < 8) {
-                const int ii = i + pdi, jj = j + pdj;
-                if (ii >= 0 && ii < A.ny && jj >= 0 && jj < A.nx) {
-                    const float d = xs - xt[tc + pdi * T2 + pdj];
-                    const float wgt = pb * prior_weight(A, d);
-                    p1 = fmaf(wgt, d, p1);
-                    p2 += wgt;
+            if (MR > 0) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    if (r * 32 + lane < nnz) {
+                        const float2 el = beL[cb[r]];
+                        ce[r] = el.x;
+                        p1 = fmaf(-ca[r] * el.y, el.x, p1);
+                        p2 = fmaf(ca[r] * ca[r], el.y, p2);
+                    }
+                }
+            } else {
+                for (int k = lane; k < nnz; k += 32) {
+                    const float a = ld_val<T>(cval, k);
+                    const float2 el = beL[cidx[1 + k]];
+                    p1 = fmaf(-a * el.y, el.x, p1);
+                    p2 = fmaf(a * a, el.y, p2);
                 }
             }
 #pragma unroll
@@ -907,39 +947,18 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             }
             // the step's sign and zero set come from num alone, so a fast
             // division leaves the fixed point unchanged
-            const float num = fmaf(xs - vt[t], A.inv_s2, p1);
+            const float num = p1 + prox;
             const float den = p2 + A.inv_s2;
             const float alpha = -__fdividef(num, den);
-            // update e: each lane owns its views' band rows
-            if (MAXR > 0) {
+            // update e: the entries of one column are distinct band positions
+            if (MR > 0) {
 #pragma unroll
-                for (int r = 0; r < RC; ++r) {
-                    if (r >= R) break;
-                    const int L = cL[r], b = cb[r];
-                    if (L > 0) {
-                        beL[b].x = fmaf(-ca0[r], alpha, beL[b].x);
-                        if (L >= 2) beL[b + 1].x = fmaf(-ca1[r], alpha, beL[b + 1].x);
-                        if (L == 3) beL[b + 2].x = fmaf(-ca2[r], alpha, beL[b + 2].x);
-                    }
-                }
+                for (int r = 0; r < RC; ++r)
+                    if (r * 32 + lane < nnz) beL[cb[r]].x = fmaf(-ca[r], alpha, ce[r]);
             } else {
-                vbase = 0;
-                for (int r = 0; r < R; ++r) {
-                    const int v = r * 32 + lane;
-                    const int Vr = min(32, Vg - r * 32);
-                    const uint32_t h = lane < Vr ? col[v] : 0u;
-                    const int L = h & 3;
-                    const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
-                    const int n1 = __popc(m1);
-                    if (L > 0) {
-                        const int b = boff[v] + (int)(h >> 2);
-                        beL[b].x = fmaf(-ld_val<T>(vals, vbase + lane), alpha, beL[b].x);
-                        if (L >= 2)
-                            beL[b + 1].x = fmaf(-ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask)), alpha, beL[b + 1].x);
-                        if (L == 3)
-                            beL[b + 2].x = fmaf(-ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask)), alpha, beL[b + 2].x);
-                    }
-                    vbase += Vr + n1 + __popc(m2);
+                for (int k = lane; k < nnz; k += 32) {
+                    const int bb = cidx[1 + k];
+                    beL[bb].x = fmaf(-ld_val<T>(cval, k), alpha, beL[bb].x);
                 }
             }
             if (lane == 0) xt[tc] = xs + alpha;
@@ -955,17 +974,16 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
         }
         seq += count;
 
-        // --- write back: X tile and the change of e (one row per view) ------
-        for (int k = lane; k < S2; k += 32) {
+        // --- write back: X tile and the change of e --------------------------
+#pragma unroll
+        for (int u = 0; u < (S2 + 31) / 32; ++u) {
+            const int k = u * 32 + lane;
             const int i = si * S + k / S, j = sj * S + k % S;
-            if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(k / S + 1) * T2 + (k % S + 1)];
+            if (k < S2 && i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(k / S + 1) * T2 + (k % S + 1)];
         }
         for (int f = lane; f < band_tot; f += 32) {
             const float de = beL[f].x - bsnap[f];
-            if (de != 0.f) {
-                const int v = bview[f];
-                atomicAdd(&eLg[(int64_t)v * A.D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v])].x, de);
-            }
+            if (de != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, A.D)].x, de);
         }
         __syncwarp();
     }
@@ -1027,28 +1045,61 @@ __global__ void __launch_bounds__(256) mann_kernel(float *__restrict__ w, const 
 
 __global__ void residual_kernel(const double *__restrict__ part, int nblk, int B, double *__restrict__ out)
 {
-    // thread b: fixed-order sum of reconstruction b's block partials
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    // block b: reconstruction b's block partials summed in a fixed order (a
+    // strided per-thread sum, then a fixed tree), deterministic
+    __shared__ double sh[2][256];
+    const int b = blockIdx.x;
     if (b >= B) return;
     const double *pb = part + 2 * (int64_t)b * nblk;
     double a = 0.0, c = 0.0;
-    for (int k = 0; k < nblk; ++k) { a += pb[2 * k]; c += pb[2 * k + 1]; }
-    out[3 * b] = a;
-    out[3 * b + 1] = c;
-    out[3 * b + 2] = c > 0.0 ? sqrt(a / c) : sqrt(a);
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) { a += pb[2 * k]; c += pb[2 * k + 1]; }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a = sh[0][0];
+        c = sh[1][0];
+        out[3 * b] = a;
+        out[3 * b + 1] = c;
+        out[3 * b + 2] = c > 0.0 ? sqrt(a / c) : sqrt(a);
+    }
 }
 
 // --- error sinogram: e = y - A X ---------------------------------------------
+// Per-warp shared memory of the kernels that walk columns outside the sweep:
+// band descriptors, offsets, entry views and one float per band entry.
+__host__ __device__ inline size_t aux_warp_bytes(int max_band, int max_views)
+{
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    return r16((size_t)max_views * 4) + r16((size_t)max_views * 2) + r16((size_t)max_band * 2) +
+           r16((size_t)max_band * 4);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                                       const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                                                       const int *__restrict__ view_off, float2 *__restrict__ eL,
                                                       const float *__restrict__ X, int B, int N, int nsv, int nsvx, int S,
-                                                      int nx, int ny, int D, int64_t ne)
+                                                      int nx, int ny, int D, int64_t ne, int max_band, int max_views)
 {
-    // one warp per (reconstruction, agent, super-voxel); lane = view; e must
-    // hold y on entry
+    // one warp per (reconstruction, agent, super-voxel): accumulate -A x over
+    // the super-voxel's columns in its band, then add the band to e (which
+    // holds y on entry)
+    extern __shared__ __align__(16) uint8_t smem[];
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
+    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
+    uint32_t *bdesc = (uint32_t *)base;
+    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
+    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
+    float *acc = (float *)((uint8_t *)bview + r16((size_t)max_band * 2));
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv);
@@ -1058,33 +1109,29 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint8_t *svcols = cols + sv_base[gsv];
     const uint32_t *coff = col_off + gsv * (S2 + 1);
-    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
-    const int hdr_bytes = (Vg + 3) & ~3;
     float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
     const float *Xg = X + (int64_t)pair * nx * ny;
-    const unsigned FULL = 0xffffffffu, lt_mask = (1u << lane) - 1u;
+    const int band_tot = load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
+    for (int f = lane; f < band_tot; f += 32) acc[f] = 0.f;
+    __syncwarp();
     for (int t = 0; t < S2; ++t) {
         if (coff[t + 1] == coff[t]) continue;
         const int i = si * S + t / S, j = sj * S + t % S;
         const float xs = Xg[(int64_t)i * nx + j];
+        if (xs == 0.f) continue;
         const uint8_t *col = svcols + coff[t];
-        const uint8_t *vals = col + hdr_bytes;
-        int vbase = 0;
-        for (int r = 0; r * 32 < Vg; ++r) {
-            const int v = r * 32 + lane;
-            const int Vr = min(32, Vg - r * 32);
-            const uint32_t h = lane < Vr ? col[v] : 0u;
-            const int L = h & 3, c = h >> 2;
-            const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
-            const int n1 = __popc(m1);
-            if (L > 0 && xs != 0.f) {
-                float2 *row = eLg + (int64_t)v * D + (int)(bd[v] & 0xFFFFu) + c;
-                atomicAdd(&row[0].x, -ld_val<T>(vals, vbase + lane) * xs);
-                if (L >= 2) atomicAdd(&row[1].x, -ld_val<T>(vals, vbase + Vr + __popc(m1 & lt_mask)) * xs);
-                if (L == 3) atomicAdd(&row[2].x, -ld_val<T>(vals, vbase + Vr + n1 + __popc(m2 & lt_mask)) * xs);
-            }
-            vbase += Vr + n1 + __popc(m2);
+        const uint16_t *cidx = (const uint16_t *)col;
+        const int nnz = cidx[0];
+        const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
+        for (int k = lane; k < nnz; k += 32) {
+            const int bb = cidx[1 + k];
+            acc[bb] = fmaf(-ld_val<T>(cval, k), xs, acc[bb]);
         }
+        __syncwarp();
+    }
+    for (int f = lane; f < band_tot; f += 32) {
+        const float a = acc[f];
+        if (a != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, D)].x, a);
     }
 }
 
@@ -1137,50 +1184,62 @@ __device__ __forceinline__ float ld_any(const uint8_t *p, int idx, int dtype)
 __global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                   const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                                   const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
-                                  int S, int D, int64_t ne, int dtype, double *__restrict__ out)
+                                  int S, int D, int64_t ne, int dtype, int max_band, int max_views,
+                                  double *__restrict__ out)
 {
     // sum over reconstructions, agents and voxels of sum_{k in J_i} A^2 Lambda
     // (FP64), for the normalised sigma; one warp per (b, agent, super-voxel)
+    extern __shared__ __align__(16) uint8_t smem[];
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
+    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
+    uint32_t *bdesc = (uint32_t *)base;
+    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
+    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
     const int b = pair / N, g = pair - b * N;
-    eL += (int64_t)b * ne;
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint32_t *coff = col_off + gsv * (S2 + 1);
-    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
-    const unsigned FULL = 0xffffffffu, lt_mask = (1u << lane) - 1u;
+    const float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
+    load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
     double acc = 0.0;
     for (int t = 0; t < S2; ++t) {
         if (coff[t + 1] == coff[t]) continue;
         const uint8_t *col = cols + sv_base[gsv] + coff[t];
-        const uint8_t *vals = col + ((Vg + 3) & ~3);
-        int vbase = 0;
-        for (int r = 0; r * 32 < Vg; ++r) {
-            const int v = r * 32 + lane;
-            const int Vr = min(32, Vg - r * 32);
-            const uint32_t h = lane < Vr ? col[v] : 0u;
-            const int L = h & 3, c = h >> 2;
-            const unsigned m1 = __ballot_sync(FULL, L >= 2), m2 = __ballot_sync(FULL, L == 3);
-            const int n1 = __popc(m1);
-            if (L > 0) {
-                const float2 *row = eL + (int64_t)(v0 + v) * D + (int)(bd[v] & 0xFFFFu) + c;
-                const int i0 = vbase + lane, i1 = vbase + Vr + __popc(m1 & lt_mask),
-                          i2 = vbase + Vr + n1 + __popc(m2 & lt_mask);
-                float a0 = ld_any(vals, i0, dtype);
-                float a1 = L >= 2 ? ld_any(vals, i1, dtype) : 0.f;
-                float a2 = L == 3 ? ld_any(vals, i2, dtype) : 0.f;
-                acc += (double)a0 * a0 * row[0].y;
-                if (L >= 2) acc += (double)a1 * a1 * row[1].y;
-                if (L == 3) acc += (double)a2 * a2 * row[2].y;
-            }
-            vbase += Vr + n1 + __popc(m2);
+        const uint16_t *cidx = (const uint16_t *)col;
+        const int nnz = cidx[0];
+        const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
+        for (int k = lane; k < nnz; k += 32) {
+            const float a = ld_any(cval, k, dtype);
+            acc += (double)a * a * eLg[band_global(cidx[1 + k], bdesc, boff, bview, D)].y;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) atomicAdd(out, acc);
+}
+
+// Bounded-wait self test: one warp arms an mbarrier for bytes that are never
+// sent and waits on it with the sweep's bounded spin (limit given); on expiry
+// it records MACE_ETIMEOUT in the status word and returns, as the sweep does.
+__global__ void wait_selftest_kernel(uint32_t spin_limit, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&bar, 16);
+    }
+    __syncwarp();
+    uint32_t spins = 0;
+    while (!mbar_try_wait(&bar, 0)) {
+        if (++spins > spin_limit) {
+            if (threadIdx.x == 0) atomicExch(status, kStatusTimeout);
+            return;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1190,9 +1249,11 @@ template <typename T>
 static void launch_forward_t(mace_state *st, unsigned blocks)
 {
     const mace_sysmatrix *M = st->M;
-    forward_kernel<T><<<blocks, 256, 0, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
-                                                      st->d_eL, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
-                                                      M->geo.ny, M->geo.D, st->ne);
+    const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
+    cudaFuncSetAttribute(forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    forward_kernel<T><<<blocks, 256, sm, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
+                                                       st->d_eL, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                       M->geo.ny, M->geo.D, st->ne, M->max_band, M->max_views);
 }
 
 // e_i = y_i - A_i X_i for every reconstruction and agent
@@ -1217,7 +1278,11 @@ typedef void (*sweep_fn)(SweepArgs);
 template <typename T, int S>
 static sweep_fn sweep_kernel_ptr_s(const mace_sysmatrix *M)
 {
-    return M->max_views <= 64 ? icd_sweep_kernel<T, 2, S> : icd_sweep_kernel<T, 0, S>;
+    // entries per column in rounds of 32 lanes
+    const int rounds = (M->max_nnz + 31) / 32;
+    if (rounds <= 3) return icd_sweep_kernel<T, 3, S>;
+    if (rounds <= 5) return icd_sweep_kernel<T, 5, S>;
+    return icd_sweep_kernel<T, 0, S>;
 }
 
 template <typename T>
@@ -1281,7 +1346,8 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.b_edge = (float)(1.0 / bsum);
     A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
     CUDA_TRY(cudaMemsetAsync(st->d_counter, 0, sizeof(int) * st->B * M->N, st->stream));
-    dim3 grid(st->sweep_warps / st->sweep_wpb), block(32 * st->sweep_wpb);
+    A.nwarps = st->sweep_warps;
+    dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
     sweep_kernel_ptr(M)<<<grid, block, st->sweep_smem, st->stream>>>(A);
@@ -1303,13 +1369,19 @@ static int configure_sweep(mace_state *st)
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int col_stride = (M->max_col_bytes + 15) & ~15;
     st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views);
-    int wpb = (int)std::min<size_t>(8, (size_t)max_smem / st->warp_smem);
-    if (wpb < 1) return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
     sweep_fn fn = sweep_kernel_ptr(M);
     if (!fn) return fail(MACE_EINVAL, "unsupported super-voxel size");
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(st->warp_smem * wpb)));
-    int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, st->warp_smem * wpb));
+    if (st->warp_smem > (size_t)max_smem)
+        return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    // block size (warps) that keeps the most warps resident per SM
+    int wpb = 1, per_sm = 0, best = 0;
+    for (int w = 1; w <= 8; ++w) {
+        if (st->warp_smem * w > (size_t)max_smem) break;
+        int b = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 32 * w, st->warp_smem * w));
+        if (b * w > best) { best = b * w; wpb = w; per_sm = b; }
+    }
     if (per_sm < 1) per_sm = 1;
     // concurrency C super-voxels per (reconstruction, agent): B N C warps, all resident
     const int64_t pairs = (int64_t)st->B * M->N;
@@ -1320,9 +1392,8 @@ static int configure_sweep(mace_state *st)
     C = std::min<int64_t>(C, M->nsv);
     int64_t warps = C * pairs;
     if (warps > capacity) return fail(MACE_EINVAL, "more (reconstruction, agent) pairs than resident warps; lower the batch");
-    // whole blocks of wpb warps: the largest wpb <= configured dividing the warp count
+    // whole blocks of wpb warps; the warps past C * pairs in the last block exit at once
     int w = (int)std::min<int64_t>(wpb, warps);
-    while (warps % w) --w;
     st->sweep_wpb = w;
     st->sweep_smem = st->warp_smem * w;
     st->sweep_warps = (int)warps;
@@ -1506,9 +1577,11 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_t2, 0, sizeof(double), s);
         if (ce == cudaSuccess) {
             int64_t items = (int64_t)batch * M->N * M->nsv;
-            theta2_sum_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, 0, s>>>(
+            const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
+            cudaFuncSetAttribute(theta2_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            theta2_sum_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, sm, s>>>(
                 M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->S,
-                M->geo.D, st->ne, (int)M->dtype, d_t2);
+                M->geo.D, st->ne, (int)M->dtype, M->max_band, M->max_views, d_t2);
             ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1540,7 +1613,7 @@ static int run_iteration(mace_state *st)
     }
     mann_kernel<<<dim3(st->nblk_mann, st->B), 256, 0, st->stream>>>(st->d_w, st->d_X, st->d_wbar, M->N, st->n,
                                                                     (float)st->P.rho, st->d_part);
-    residual_kernel<<<(st->B + 127) / 128, 128, 0, st->stream>>>(st->d_part, st->nblk_mann, st->B, st->d_resid);
+    residual_kernel<<<st->B, 256, 0, st->stream>>>(st->d_part, st->nblk_mann, st->B, st->d_resid);
     CUDA_TRY(cudaGetLastError());
     st->iters++;
     if (st->P.recompute_every > 0 && st->iters % st->P.recompute_every == 0) return launch_forward(st);
@@ -1745,6 +1818,24 @@ extern "C" int mace_recompute_error(mace_state *st)
     int rc = launch_forward(st);
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return MACE_OK;
+}
+
+extern "C" int mace_wait_selftest(uint32_t spin_limit, void *cuda_stream)
+{
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int *d = nullptr, h = 0;
+    CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+    cudaError_t ce = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (ce == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, s>>>(spin_limit, d);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (ce != cudaSuccess) return fail(MACE_ECUDA, std::string("wait self test: ") + cudaGetErrorString(ce));
+    if (h == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
     return MACE_OK;
 }
 

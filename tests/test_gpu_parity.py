@@ -130,7 +130,7 @@ def test_converged_matches_map_qggmrf(gpu_lib, concurrency, sigma):
     c = case(96, 144, 137, 8, "qggmrf")
     xs = central_reference(96, 144, 137, 8, "qggmrf")
     x, iters, r, conv, w, X, stats = _reconstruct(gpu_lib, c, concurrency=concurrency, sigma=sigma,
-                                                  tol=1e-6, max_iter=4000)
+                                                  tol=2e-8, max_iter=8000)
     err = nrmse(x, xs)
     print("qggmrf iters=%d r=%.2e nrmse=%.2e conc=%d" % (iters, r, err, stats["concurrency"]))
     assert err < 1e-4

@@ -1,0 +1,136 @@
+"""GPU tests on the benchmark workloads: full-size 512^2 parity, batches,
+reduced-precision matrices, failure detection (bounded device waits)."""
+import hashlib
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import case, central_reference, nrmse
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# solver settings of the 512^2 workload: normalised sigma 0.1 with symmetric
+# ICD passes and 64 concurrent super-voxels per agent
+PROD = dict(sigma=0.1, sigma_mode=1, rho=0.8, sweeps_per_iter=2, symmetric=True,
+            recompute_every=10, concurrency=64, sv_order=0)
+
+
+def _digest(y, lam):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(y, np.float32).tobytes())
+    h.update(np.ascontiguousarray(lam, np.float32).tobytes())
+    return h.hexdigest()
+
+
+def test_bounded_wait_reports_timeout(gpu_lib):
+    """A device wait that nothing completes ends with MACE_ETIMEOUT and the
+    context stays usable (a normal reconstruction runs afterwards)."""
+    mace = gpu_lib
+    assert mace.mace_wait_selftest(2000) == mace.MACE_ETIMEOUT
+    c = case(37, 30, 53, 3, "quadratic")
+    sm = mace.mace_build_sysmatrix(37, 37, 30, 53, 3, sv_size=4)
+    st = mace.mace_init(sm, c["y"], c["lam"], mace.make_params(prior="quadratic", sigma_x=c["sigma_x"],
+                                                               concurrency=1, sigma=0.5))
+    r, _ = st.iterate(5)
+    assert math.isfinite(r)
+
+
+def test_full_size_512_parity(gpu_lib):
+    """The 512^2 / 720-view / 725-channel / 16-agent Q-GGMRF workload at full
+    size, in the benchmark's launch configuration: the converged image matches
+    the oracle's reference MAP image (tests/golden, written by the oracle)
+    within relative RMSE 1e-4, and the oracle's KKT residual of the GPU image
+    is small."""
+    mace = gpu_lib
+    cfg = synth.CONFIGS["cfg2"]
+    c = synth.make_case(**cfg)
+    y, lam = c["y"][0], c["lam"][0]
+    sx = synth.prior_sigma_x(lam, 720, frac=1.0)
+    sm = mace.mace_build_sysmatrix(512, 512, 720, 725, 16, sv_size=8)
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, tol=1e-7, max_iter=4000, **PROD)
+    st = mace.mace_init(sm, y, lam, prm)
+    x, iters, r, conv = st.reconstruct()
+    w, X = st.get_state()
+    st.close()
+    print("512^2: iters=%d residual=%.2e" % (iters, r))
+    P = oracle.Problem(512, 512, 720, 725, y, lam, n_agents=16, prior="qggmrf", sigma_x=sx)
+    g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
+    kkt = np.linalg.norm(P.gradient(x.ravel().astype(np.float64))) / g0
+    print("512^2: KKT %.2e" % kkt)
+    assert kkt < 1e-5
+    # equilibrium: every agent state equals the consensus (Theorem 1 proof)
+    wbar = w.astype(np.float64).mean(0)
+    for g in range(16):
+        assert nrmse(X[g], wbar) < 1e-3
+    ref = os.path.join(GOLDEN, "cfg2_reference.npz")
+    if os.path.exists(ref):
+        d = np.load(ref)
+        if str(d["digest"]) == _digest(y, lam):
+            err = nrmse(x, d["x"])
+            print("512^2: NRMSE vs oracle %.2e (oracle KKT %.1e)" % (err, float(d["kkt"])))
+            assert err < 1e-4
+        else:
+            print("512^2: inputs differ from the stored reference's; NRMSE check skipped")
+
+
+def test_batch_same_alone_and_in_the_mix(gpu_lib):
+    """Three different scans in one batch reconstruct to the same images as
+    each alone (within the FP32 tolerance), at the concurrency a batch uses."""
+    mace = gpu_lib
+    n, V, D, N = 64, 90, 95, 4
+    ys, ls = [], []
+    for k in range(3):
+        cc = synth.make_case(n=n, n_views=V, n_channels=D, I0=1e4, mu_max=0.02, seed=40 + k, noise_seed=140 + k)
+        ys.append(cc["y"][0])
+        ls.append(cc["lam"][0])
+    sx = synth.prior_sigma_x(ls[0], V, frac=1.0)
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=8)
+    prm = mace.make_params(prior="quadratic", sigma_x=sx, sigma=0.5, rho=0.8, sweeps_per_iter=2, symmetric=True,
+                           concurrency=1, tol=1e-7, max_iter=5000, recompute_every=10)
+    stb = mace.mace_init(sm, np.stack(ys), np.stack(ls), prm, batch=3)
+    xb, itb, rb, cb = stb.reconstruct()
+    assert cb
+    for k in range(3):
+        st = mace.mace_init(sm, ys[k], ls[k], prm)
+        x1, it1, r1, c1 = st.reconstruct()
+        assert c1
+        assert nrmse(xb[k], x1) < 1e-5, k
+        P = oracle.Problem(n, n, V, D, ys[k], ls[k], n_agents=N, prior="quadratic", sigma_x=sx)
+        xs, _, _ = P.central_icd(max_sweeps=20000, tol=1e-13)
+        assert nrmse(xb[k], xs) < 1e-4, k
+
+
+@pytest.mark.parametrize("dtype,tol", [("f16", 1e-3), ("bf16", 2e-3)])
+def test_reduced_precision_matrix(gpu_lib, dtype, tol):
+    """Matrix values stored in FP16 / BF16 with FP32 accumulation, FP64
+    consensus and residual, e recomputed every 5 iterations.  FP16 (11-bit
+    significand) stays within relative RMSE 1e-3 of the FP64 oracle; BF16
+    (8-bit significand, values rounded by up to 2^-9 relative) solves the MAP
+    problem of the rounded matrix, measured at 1.3e-3 from the FP64 image, so
+    its bound here is 2e-3."""
+    mace = gpu_lib
+    c = case(96, 144, 137, 8, "qggmrf")
+    xs = central_reference(96, 144, 137, 8, "qggmrf")
+    sm = mace.mace_build_sysmatrix(96, 96, 144, 137, 8, dtype=dtype, sv_size=8)
+    prm = mace.make_params(prior="qggmrf", sigma_x=c["sigma_x"], sigma=0.1, sigma_mode=1, rho=0.8,
+                           sweeps_per_iter=2, symmetric=True, recompute_every=5, concurrency=8,
+                           tol=2e-8, max_iter=8000)
+    st = mace.mace_init(sm, c["y"], c["lam"], prm)
+    x, iters, r, conv = st.reconstruct()
+    err = nrmse(x, xs)
+    print("%s: iters=%d r=%.2e nrmse=%.2e" % (dtype, iters, r, err))
+    assert err < tol
+    # stored values are the FP64 strip integrals rounded to the type
+    P = c["P"]
+    c0, ln, vals = sm.column(0, 40, 50)
+    views = P.agent_views(0)
+    for k, m in enumerate(views[:10]):
+        oc0, ov = P.footprint(int(m), 40, 50)
+        assert ln[k] == len(ov) and (len(ov) == 0 or c0[k] == oc0)
+        np.testing.assert_allclose(vals[k, :len(ov)], ov, rtol=4e-3 if dtype == "bf16" else 5e-4)
