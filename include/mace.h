@@ -187,6 +187,22 @@ int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device,
 /* Consensus image mean_i w_i of the current state, without iterating. */
 int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device);
 
+/* mace_consensus without any device allocation, for callers that may not
+ * allocate GPU memory after start-up: a service that reserves all device
+ * memory once and forbids allocation on its per-scan path (cudaMalloc can
+ * synchronise the device and fragment a fixed budget), or code that runs
+ * under another framework whose caching allocator owns the free memory.
+ * The paper has no counterpart; it only reads the result out.
+ * With ptr_is_device != 0 the images go straight to x_out.  With host x_out
+ * they pass through a 4 MiB device array inside the library (at most
+ * 1048576 floats = batch * nz * ny * nx; larger requests return MACE_EINVAL).
+ * That array belongs to the library for the life of the process on every
+ * GPU that loads it, and all calls on one GPU share it: calls whose GPU work
+ * overlaps (other streams or host threads) race on it.  The first call on a
+ * GPU looks up the array's address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Calls no allocator. */
+int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_is_device);
+
 /* Checkpoint / resume: the complete algorithm state is (w, X) (Eq.
  * "PUCEupdate"); e_i is recomputed from X on mace_set_state.  w, X:
  * [batch][n_agents][n] float32 (either may be NULL in get_state). */

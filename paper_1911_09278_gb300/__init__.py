@@ -32,7 +32,7 @@ EXPORTS = [
     "mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
     "mace_get_visit_order",
     "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
-    "mace_set_timing", "mace_get_timing", "mace_wait_selftest",
+    "mace_set_timing", "mace_get_timing", "mace_wait_selftest", "mace_consensus_noalloc",
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
@@ -98,6 +98,7 @@ def load(path=LIB_PATH):
     L.mace_poll.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_set_timing.argtypes = [vp, i32, i32]
     L.mace_wait_selftest.argtypes = [ctypes.c_uint32, vp]
+    L.mace_consensus_noalloc.argtypes = [vp, vp, i32]
     L.mace_get_timing.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_reconstruct.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     L.mace_consensus.argtypes = [vp, vp, i32]
@@ -280,6 +281,14 @@ class State:
         x = np.empty(self._img_shape(), np.float32) if out is None else out
         ptr, dev, keep = _out_ptr(x, self.batch * self.n)
         _check(load().mace_consensus(self.handle, ptr, dev))
+        return x
+
+    def consensus_noalloc(self, out=None):
+        """mace_consensus through the library's fixed device array (no
+        allocation); see include/mace.h for its limits."""
+        x = np.empty(self._img_shape(), np.float32) if out is None else out
+        ptr, dev, keep = _out_ptr(x, self.batch * self.n)
+        _check(load().mace_consensus_noalloc(self.handle, ptr, dev))
         return x
 
     def get_state(self):

@@ -1722,6 +1722,51 @@ extern "C" int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_devic
     return MACE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Consensus image without any allocation
+// ---------------------------------------------------------------------------
+// Device memory that mace_consensus_noalloc writes the consensus images into
+// before copying them to the host.  It is a file-scope array, so every GPU that
+// loads this library holds it (4 MiB) until the process exits, and every call
+// on that GPU shares it: the last call's images stay in it, and calls whose
+// GPU work overlaps (different streams, or different host threads) race on
+// it.  In host code its name is only a stand-in for the symbol; the device
+// address is looked up once per GPU with cudaGetSymbolAddress.
+static constexpr int64_t kNoAllocFloats = (int64_t)1 << 20;
+static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
+static float *g_noalloc_addr[256] = {nullptr};
+
+extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_is_device)
+{
+    if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
+    const mace_sysmatrix *M = st->M;
+    const int64_t Bn = (int64_t)st->B * st->n;
+    float *d_x = x_out;
+    if (!ptr_is_device) {
+        if (Bn > kNoAllocFloats)
+            return fail(MACE_EINVAL, "batch x image larger than the 1048576-float no-allocation buffer");
+        int dev = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 256) return fail(MACE_EINVAL, "device index out of range");
+        if (!g_noalloc_addr[dev]) {
+            // first call on this GPU: look up the array's device address
+            cudaError_t e = cudaGetSymbolAddress((void **)&g_noalloc_addr[dev], g_noalloc_images);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                return fail(MACE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            }
+        }
+        d_x = g_noalloc_addr[dev];
+    }
+    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, nullptr, d_x);
+    CUDA_TRY(cudaGetLastError());
+    if (!ptr_is_device) {
+        CUDA_TRY(cudaMemcpyAsync(x_out, d_x, sizeof(float) * Bn, cudaMemcpyDeviceToHost, st->stream));
+        CUDA_TRY(cudaStreamSynchronize(st->stream));
+    }
+    return MACE_OK;
+}
+
 extern "C" int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device, int32_t *iters_out,
                                 double *residual_out)
 {
