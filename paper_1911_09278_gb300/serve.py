@@ -1,0 +1,142 @@
+"""Continuous-batching reconstruction server over the C ABI.
+
+Requests (a scan: geometry, partition, y, Lambda) arrive over time.  Each
+admitted request gets its own reconstruction state on its own CUDA stream;
+the server enqueues its Mann iterations in short chunks (mace_launch), so the
+iterations of every active request run on the GPU at the same time, polls
+them (mace_poll), retires converged requests (consensus image copied to the
+host) and admits waiting ones as slots and device memory free up.  Stored
+system matrices are shared by every request with the same geometry and
+partition and stay resident.
+
+Admission is by device-memory footprint: the request's state plus, for a new
+geometry, its system matrix must fit the budget next to what is resident.
+This module only orchestrates; every step of a reconstruction runs in
+libmace.so.
+"""
+import collections
+import time
+
+import numpy as np
+
+from . import (Sysmatrix, load, make_params, mace_build_sysmatrix, mace_init)  # noqa: F401
+
+Request = collections.namedtuple(
+    "Request", "rid arrival nx ny n_views n_channels n_agents y lam sigma_x view_agent")
+
+
+def state_bytes(nx, ny, n_views, n_channels, n_agents):
+    """Device bytes of one reconstruction state (mace_init): (e, Lambda) and y
+    per measurement, w and X per agent and pixel, the FP64 consensus and
+    small per-agent counters."""
+    m = n_views * n_channels
+    n = nx * ny
+    return m * (8 + 4) + n_agents * n * (4 + 4) + n * 8 + 65536
+
+
+class Server:
+    """Host-side scheduler; see the module docstring.
+
+    params: keyword arguments for make_params (sigma_x comes per request).
+    max_active: requests on the GPU at once.  budget: device bytes the
+    server may hold (system matrices + states).  chunk: iterations enqueued
+    per request between polls."""
+
+    def __init__(self, params, dtype="bf16", sv_size=8, max_active=8, budget=64 << 30,
+                 chunk=10, max_iter=4000):
+        import torch
+        self.torch = torch
+        self.params = dict(params)
+        self.dtype = dtype
+        self.sv_size = sv_size
+        self.max_active = max_active
+        self.budget = budget
+        self.chunk = chunk
+        self.max_iter = max_iter
+        self.matrices = {}      # geometry key -> Sysmatrix
+        self.matrix_bytes = {}
+
+    def _key(self, r):
+        va = None if r.view_agent is None else bytes(np.asarray(r.view_agent, np.int32))
+        return (r.nx, r.ny, r.n_views, r.n_channels, r.n_agents, va)
+
+    def _resident(self):
+        return sum(self.matrix_bytes.values())
+
+    def _matrix(self, r):
+        k = self._key(r)
+        if k not in self.matrices:
+            sm = mace_build_sysmatrix(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents,
+                                      view_agent=r.view_agent, dtype=self.dtype, sv_size=self.sv_size)
+            info = sm.info()
+            self.matrices[k] = sm
+            self.matrix_bytes[k] = info["bytes_columns"] + info["bytes_meta"]
+        return self.matrices[k]
+
+    def _matrix_estimate(self, r):
+        # nnz ~ pixels * views * (1 + 4/pi) for square pixels on channels of the
+        # same pitch; (index, value) per entry plus padding
+        vb = 4 if self.dtype == "f32" else 2
+        return int(r.nx * r.ny * r.n_views * 2.3 * (2 + vb) * 1.1)
+
+    def run(self, requests, serial=False, now=time.perf_counter):
+        """Serve `requests` (arrival times in seconds from the start).  With
+        serial=True one request at a time (the plain GPU form).  Returns a dict
+        with per-request results and throughput / latency figures."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        active = []
+        done = {}
+        t0 = now()
+        while pending or active:
+            t = now() - t0
+            # admission
+            limit = 1 if serial else self.max_active
+            while pending and pending[0].arrival <= t and len(active) < limit:
+                r = pending[0]
+                new_matrix = self._key(r) not in self.matrices
+                need = state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)
+                need += self._matrix_estimate(r) if new_matrix else 0
+                held = self._resident() + sum(a["bytes"] for a in active)
+                if held + need > self.budget and active:
+                    break
+                pending.popleft()
+                sm = self._matrix(r)
+                stream = torch.cuda.Stream()
+                prm = make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
+                st = mace_init(sm, r.y, r.lam, prm, stream=stream)
+                active.append(dict(req=r, st=st, stream=stream, start=now() - t0,
+                                   bytes=state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)))
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - (now() - t0))))
+                continue
+            for a in active:
+                a["st"].launch(self.chunk)
+            still = []
+            for a in active:
+                r_, conv = a["st"].poll()
+                it = a["st"].stats()["iters"]
+                if conv or it >= self.max_iter:
+                    x = a["st"].consensus()
+                    fin = now() - t0
+                    done[a["req"].rid] = dict(x=x, iters=it, residual=r_, converged=conv,
+                                              latency=fin - a["req"].arrival, finish=fin,
+                                              start=a["start"])
+                    a["st"].close()
+                else:
+                    still.append(a)
+            active = still
+        makespan = max(d["finish"] for d in done.values()) if done else 0.0
+        lat = np.array([d["latency"] for d in done.values()])
+        first = min(r.arrival for r in requests) if requests else 0.0
+        return dict(results=done, recons_per_s=len(done) / max(1e-9, makespan - first),
+                    p50=float(np.percentile(lat, 50)) if len(lat) else None,
+                    p99=float(np.percentile(lat, 99)) if len(lat) else None,
+                    makespan=makespan)
+
+    def close(self):
+        for sm in self.matrices.values():
+            sm.close()
+        self.matrices.clear()
+        self.matrix_bytes.clear()
