@@ -83,7 +83,12 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   prior 1: Q-GGMRF, rho(D) = (D^2/(2 sigma_x^2)) / (1 + |D/(T sigma_x)|^(p-q)),
  *            p must be 2 (the paper cites the prior without defining it).
  *   h(x) = sum over neighbour pairs of b_sr rho(x_s - x_r), b_sr ~ 1/distance
- *   over the 8-neighbourhood, normalised to sum 1; neighbourhood must be 8.
+ *   over the neighbourhood, normalised to sum 1.  neighbourhood 8: in-plane;
+ *   neighbourhood 26: the batch of mace_init is the z-stack of ONE volume
+ *   (batch element b is slice z = b, all slices share the 2D matrix) and the
+ *   prior couples neighbouring slices; slices are then updated one per warp,
+ *   each reading its neighbour slices as they were when its super-voxel
+ *   began.
  *   sigma: the proximal parameter of Eq. "prox_F"; sigma_mode 0 takes it in
  *   image units, 1 scales it by 1/sqrt(mean_{i,s} sum_{k in J_i} A^2 Lambda).
  *   rho in (0, 1): Mann parameter (Eq. "Mann").
@@ -98,7 +103,10 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   sv_order: 0 visits super-voxels in raster order cut into `concurrency`
  *   bands that run side by side (plain raster when concurrency is 1);
  *   1 a stride permutation spreading consecutive super-voxels apart.
- *   Pixels inside a super-voxel are visited in raster order. */
+ *   Pixels inside a super-voxel are visited in raster order.
+ *   chains: reconstructions of a batch one warp updates together, sharing
+ *   every column load (0 or 1: one; 2 or 4: that many when they divide the
+ *   batch).  Results do not depend on it. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -113,6 +121,7 @@ typedef struct {
     double tol;
     int32_t concurrency;
     int32_t sv_order;
+    int32_t chains;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */
@@ -231,9 +240,10 @@ int64_t mace_error_size(const mace_state *st);
 int mace_recompute_error(mace_state *st);
 
 /* Iterations run so far, the proximal sigma in image units, the last
- * residual and the super-voxels of one agent in flight per pass. */
+ * residual, the super-voxels of one agent in flight per pass and the
+ * reconstructions one warp updates together. */
 int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
-                   double *last_residual, int32_t *concurrency);
+                   double *last_residual, int32_t *concurrency, int32_t *chains);
 
 /* CUDA-event timing of the ICD sweep launches on the state's stream:
  * mace_set_timing(st, 1, max_launches) starts recording (up to max_launches

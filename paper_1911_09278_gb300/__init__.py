@@ -64,7 +64,8 @@ class Params(ctypes.Structure):
                 ("rho", ctypes.c_double), ("sweeps_per_iter", ctypes.c_int32),
                 ("symmetric", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32)]
+                ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32),
+                ("chains", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -110,7 +111,7 @@ def load(path=LIB_PATH):
     L.mace_error_size.restype = i64
     L.mace_recompute_error.argtypes = [vp]
     L.mace_get_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
-                                 ctypes.POINTER(i32)]
+                                 ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.mace_free_state.argtypes = [vp]
     L.mace_free_state.restype = None
     L.mace_free_sysmatrix.argtypes = [vp]
@@ -221,10 +222,10 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
-                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0):
+                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0):
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
-                  max_iter, tol, concurrency, sv_order)
+                  max_iter, tol, concurrency, sv_order, chains)
 
 
 class State:
@@ -332,9 +333,11 @@ class State:
         s = ctypes.c_double()
         r = ctypes.c_double()
         c = ctypes.c_int32()
+        k = ctypes.c_int32()
         _check(load().mace_get_stats(self.handle, ctypes.byref(it), ctypes.byref(s), ctypes.byref(r),
-                                     ctypes.byref(c)))
-        return dict(iters=it.value, sigma_abs=s.value, last_residual=r.value, concurrency=c.value)
+                                     ctypes.byref(c), ctypes.byref(k)))
+        return dict(iters=it.value, sigma_abs=s.value, last_residual=r.value, concurrency=c.value,
+                    chains=k.value)
 
     def close(self):
         if self.handle:

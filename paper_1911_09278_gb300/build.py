@@ -7,7 +7,7 @@ SRC = os.path.join(HERE, "csrc", "mace.cu")
 HDR = os.path.join(os.path.dirname(HERE), "include", "mace.h")
 LIB = os.path.join(HERE, "libmace.so")
 
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo",
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--split-compile", "0",
               "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-shared"]
 

@@ -549,7 +549,7 @@ struct mace_state {
     int nblk_mann = 0;
     int iters = 0;
     double last_resid = INFINITY;
-    int sweep_warps = 0, sweep_wpb = 0, concurrency = 0;
+    int sweep_warps = 0, sweep_wpb = 0, concurrency = 0, chains = 1;
     size_t sweep_smem = 0, warp_smem = 0;
 };
 
@@ -575,7 +575,9 @@ struct SweepArgs {
     float inv_s2, pscale;
     int prior;                  // 0 quadratic, 1 Q-GGMRF
     float inv_sx2, inv_Tsx, qexp, qq;   // prior constants
-    float b_edge, b_diag;
+    float b_edge, b_diag;       // 8-neighbourhood weights (face, diagonal)
+    int nb26;                   // 1: the batch is the z-stack of one volume, 26-neighbourhood prior
+    float b26[3];               // 26-neighbourhood weights by squared distance 1, 2, 3
 };
 
 // --- PTX helpers -------------------------------------------------------------
@@ -640,51 +642,76 @@ template <> __device__ __forceinline__ float ld_val<__half>(const uint8_t *p, in
     return __half2float(((const __half *)p)[idx]);
 }
 
-// Per-warp shared-memory layout (bytes, each part 16-aligned):
+// Per-warp shared-memory layout (bytes, each part 16-aligned).  Shared by
+// the warp's K chains (reconstructions of one batch group that run the same
+// agent over the same super-voxels, so every column is loaded once for all):
 //   ring:   kRing * col_stride            column staging (TMA destination)
 //   bars:   kRing * 8                     mbarriers
+//   bdesc:  2 * max_views * 4             band descriptors (lo | len << 16), current and next super-voxel
+//   boff:   max_views * 2                 band offset of each view (u16)
+//   bview:  max_band * 2                  view of each band entry (u16)
+//   coff:   2 * (S^2 + 1) * 4             column byte offsets, current and next super-voxel
+//   tl:     2 * S^2 * 2                   non-empty pixels in visiting order, current and next
+//   halo:   2 * (S+2)^2 * 4               X tiles of the slices below and above (volumes)
+// and per chain:
 //   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
 //   bsnap:  max_band * 4                  e of the band when the super-voxel began
-//   bdesc:  max_views * 4                 band descriptor of each view (lo | len << 16)
-//   bview:  max_band * 2                  view of each band entry (u16)
-//   boff:   max_views * 2                 band offset of each view (u16)
-//   coff:   (S^2 + 1) * 4                 column byte offsets of the super-voxel
-//   tl:     S^2 * 2                       non-empty pixels in visiting order
 //   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
+//   wst:    S^2 * 12                      staged consensus (FP64) and w of the tile
 //   vt:     S^2 * 4                       v tile
 struct WarpSmem {
-    size_t ring, bars, beL, bsnap, bdesc, bview, boff, coff, tl, xt, vt, total;
+    size_t ring, bars, bdesc, boff, bview, coff, tl, halo, chain0, chain_size;
+    size_t beL, bsnap, xt, wst, vt;   // offsets inside a chain block
+    size_t total;
 };
 
-__host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views)
+__host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views, int K)
 {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    const size_t S2 = (size_t)S * S, T2 = (size_t)(S + 2) * (S + 2);
     WarpSmem L;
     size_t o = 0;
     L.ring = o;  o += r16((size_t)kRing * col_stride);
     L.bars = o;  o += r16(kRing * 8);
-    L.beL = o;   o += r16((size_t)max_band * 8);
-    L.bsnap = o; o += r16((size_t)max_band * 4);
-    L.bdesc = o; o += r16((size_t)max_views * 4);
-    L.bview = o; o += r16((size_t)max_band * 2);
+    L.bdesc = o; o += r16((size_t)2 * max_views * 4);
     L.boff = o;  o += r16((size_t)max_views * 2);
-    L.coff = o;  o += r16((size_t)(S * S + 1) * 4);
-    L.tl = o;    o += r16((size_t)S * S * 2);
-    L.xt = o;    o += r16((size_t)(S + 2) * (S + 2) * 4);
-    L.vt = o;    o += r16((size_t)S * S * 4);
-    L.total = o;
+    L.bview = o; o += r16((size_t)max_band * 2);
+    L.coff = o;  o += r16((size_t)2 * (S2 + 1) * 4);
+    L.tl = o;    o += r16((size_t)2 * S2 * 2);
+    L.halo = o;  o += r16(2 * T2 * 4);
+    L.chain0 = o;
+    size_t c = 0;
+    L.beL = c;   c += r16((size_t)max_band * 8);
+    L.bsnap = c; c += r16((size_t)max_band * 4);
+    L.xt = c;    c += r16(T2 * 4);
+    L.wst = c;   c += r16(S2 * 12);
+    L.vt = c;    c += r16(S2 * 4);
+    L.chain_size = c;
+    L.total = o + (size_t)K * c;
     return L;
 }
 
-static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views)
+static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views, int K)
 {
-    return warp_smem_layout(max_band, col_stride, S, max_views).total;
+    return warp_smem_layout(max_band, col_stride, S, max_views, K).total;
 }
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Band bookkeeping shared by the kernels that walk a super-voxel's columns:
 // per view the band descriptor, its offset in the flattened band and, per
-// band entry, its view.  Returns the band size.  Warp-cooperative.
-__device__ __forceinline__ int load_band_layout(const uint32_t *__restrict__ bd, int Vg, uint32_t *bdesc,
+// band entry, its view.  Returns the band size.  Warp-cooperative.  bd may
+// point to global or shared memory; bdesc may alias bd.
+__device__ __forceinline__ int load_band_layout(const uint32_t *bd, int Vg, uint32_t *bdesc,
                                                 uint16_t *boff, uint16_t *bview, int lane)
 {
     const unsigned FULL = 0xffffffffu;
@@ -719,184 +746,264 @@ __device__ __forceinline__ int64_t band_global(int f, const uint32_t *bdesc, con
     return (int64_t)v * D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v]);
 }
 
-// One warp per super-voxel at a time.  Each pixel's column is a flat list of
-// (band position, value) pairs; lane k takes entries k, k+32, ...  MR > 0:
-// at most 32*MR entries per column, kept in registers between the reduction
-// and the update; MR == 0: any count, re-read from shared memory.  S:
-// super-voxel side.
-template <typename T, int MR, int S>
+// One warp runs K chains (reconstructions b0 .. b0+K-1 of one batch group,
+// all on agent g) over a fixed sequence of super-voxels: slots c, c+C, c+2C,
+// ... of the visiting order, where C warps serve the same (group, agent) -- so
+// about C super-voxels of one agent of one reconstruction are in flight at a
+// time.  Inside a super-voxel the pixels are visited in order; each pixel's
+// column (a flat list of (band position, value) pairs, lane k taking entries
+// k, k+32, ...) is streamed once by TMA for all K chains.  The next
+// super-voxel's metadata and first columns are fetched while the current one
+// is processed.  MR > 0: at most 32*MR entries per column, kept in registers
+// between the reduction and the update; MR == 0: any count (K must be 1).
+template <typename T, int MR, int S, int K>
 __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int S2 = S * S, T2 = S + 2;
+    static_assert(MR > 0 || K == 1, "uncached columns support one chain");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views);
+    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views, K);
     uint8_t *base = smem + wib * Ly.total;
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
-    float2 *beL = (float2 *)(base + Ly.beL);
-    float *bsnap = (float *)(base + Ly.bsnap);
-    uint32_t *bdesc = (uint32_t *)(base + Ly.bdesc);
-    uint16_t *bview = (uint16_t *)(base + Ly.bview);
+    uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
     uint16_t *boff = (uint16_t *)(base + Ly.boff);
-    uint32_t *scoff = (uint32_t *)(base + Ly.coff);
-    uint16_t *tl = (uint16_t *)(base + Ly.tl);
-    float *xt = (float *)(base + Ly.xt);
-    float *vt = (float *)(base + Ly.vt);
+    uint16_t *bview = (uint16_t *)(base + Ly.bview);
+    uint32_t *scoff2 = (uint32_t *)(base + Ly.coff);
+    uint16_t *tl2 = (uint16_t *)(base + Ly.tl);
+    uint8_t *chains = base + Ly.chain0;
+    float *halo_lo = (float *)(base + Ly.halo);
+    float *halo_hi = halo_lo + T2 * T2;
 
     if (lane == 0)
         for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncwarp();
 
-    uint32_t seq = 0;   // columns consumed by this warp so far (ring position)
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = (int64_t)A.nx * A.ny;
-
-    // warp w serves agent g of reconstruction b, (b, g) = w mod (B N); the
-    // pair's super-voxels are handed out in visiting order through its
-    // counter, so at most warps / (B N) super-voxels of one agent of one
-    // reconstruction are in flight at a time
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     if (gw >= A.nwarps) return;
-    const int pair = gw % (A.B * A.N);
-    const int b = pair / A.N, g = pair - b * A.N;
+    const int G = A.B / K;                      // batch groups
+    const int pair = gw % (G * A.N);            // (group, agent)
+    const int cidx = gw / (G * A.N);            // this warp's place among the C serving the pair
+    const int grp = pair / A.N, g = pair - grp * A.N;
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
-    float2 *eLg = A.eL + (int64_t)b * A.ne + (int64_t)v0 * A.D;    // agent block [Vg][D]
-    float *Xg = A.X + (int64_t)pair * n;
-    const float *wg = A.w + (int64_t)pair * n;
-    const double *wbg = A.wbar + (int64_t)b * n;
-    const float *vg = A.vexp ? A.vexp + (int64_t)pair * n : nullptr;
-    // this lane's prior neighbour (lanes 0..7)
-    const int kk = lane < 4 ? lane : lane + 1;
-    const int pdi = kk / 3 - 1, pdj = kk % 3 - 1;
-    const float pb = lane < 8 ? A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge) : 0.f;
+    const int Cw = A.nwarps / (G * A.N);
+    // this lane's prior neighbour: lanes 0..7 the in-plane 8-neighbourhood,
+    // or (volumes) lanes 0..25 the 26-neighbourhood
+    int pdz = 0, pdi, pdj;
+    float pb;
+    if (A.nb26) {
+        const int kk = lane < 13 ? lane : lane + 1;   // skip the centre of the 3x3x3
+        pdz = kk / 9 - 1;
+        pdi = (kk / 3) % 3 - 1;
+        pdj = kk % 3 - 1;
+        const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
+        pb = lane < 26 ? A.pscale * A.b26[d2 - 1] : 0.f;
+    } else {
+        const int kk = lane < 4 ? lane : lane + 1;
+        pdi = kk / 3 - 1;
+        pdj = kk % 3 - 1;
+        pb = lane < 8 ? A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge) : 0.f;
+    }
+    const int nlanes = A.nb26 ? 26 : 8;
 
-    // the next super-voxel is claimed one super-voxel ahead, so the claim's
-    // round trip overlaps the current super-voxel's work
-    int next_slot = 0;
-    if (lane == 0) next_slot = atomicAdd(&A.counter[pair], 1);
-    while (true) {
-        int slot = __shfl_sync(FULL, next_slot, 0);
-        if (lane == 0 && slot < A.nsv && *((volatile int *)A.status) != 0) slot = A.nsv;
-        slot = __shfl_sync(FULL, slot, 0);
-        if (slot >= A.nsv) break;
-        if (lane == 0) next_slot = atomicAdd(&A.counter[pair], 1);
-        if (A.backward) slot = A.nsv - 1 - slot;
-        const int sv = A.sv_order[slot];
-        const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
-        const int64_t gsv = (int64_t)g * A.nsv + sv;
-        const uint8_t *svcols = A.cols + A.sv_base[gsv];
-        const uint32_t *coff = A.col_off + gsv * (S2 + 1);
+    // chain k: reconstruction grp*K + k
+    auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
+    auto Xk = [&](int k) { return A.X + ((int64_t)(grp * K + k) * A.N + g) * n; };
+    auto chain = [&](int k) { return chains + (size_t)k * Ly.chain_size; };
 
-        // --- column offsets and the list of pixels to visit -----------------
-        for (int k = lane; k <= S2; k += 32) scoff[k] = coff[k];
-        __syncwarp();
+    // --- super-voxel metadata -------------------------------------------
+    auto sv_of = [&](int m) {           // m-th super-voxel of this warp, -1 past the end
+        const int slot = cidx + m * Cw;
+        if (slot >= A.nsv) return -1;
+        return A.sv_order[A.backward ? A.nsv - 1 - slot : slot];
+    };
+    // visiting list of a super-voxel from its column offsets; returns count
+    auto build_list = [&](const uint32_t *sc, uint16_t *tl) {
         int count = 0;
         for (int k0 = 0; k0 < S2; k0 += 32) {
             const int k = k0 + lane;
             const int t = A.backward ? S2 - 1 - k : k;
-            const bool ne = k < S2 && scoff[t + 1] != scoff[t];
+            const bool ne = k < S2 && sc[t + 1] != sc[t];
             const unsigned m = __ballot_sync(FULL, ne);
             if (ne) tl[count + __popc(m & lt_mask)] = (uint16_t)t;
             count += __popc(m);
         }
         __syncwarp();
-        // --- prefetch the first columns --------------------------------------
-        if (lane == 0) {
-            const int pre = min(count, kRing);
-            for (int q = 0; q < pre; ++q) {
-                const int t = tl[q];
-                const uint32_t stg = (seq + q) % kRing;
-                mbar_expect_tx(&bars[stg], scoff[t + 1] - scoff[t]);
-                tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + scoff[t], scoff[t + 1] - scoff[t], &bars[stg]);
-            }
-        }
+        return count;
+    };
+    // issue TMA for column q of a super-voxel into ring position idx
+    auto issue = [&](uint32_t idx, const uint8_t *svcols, const uint32_t *sc, const uint16_t *tl, int q) {
+        const int t = tl[q];
+        const uint32_t stg = idx % kRing;
+        const uint32_t bytes = sc[t + 1] - sc[t];
+        mbar_expect_tx(&bars[stg], bytes);
+        tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + sc[t], bytes, &bars[stg]);
+    };
 
-        // --- band layout and snapshot (loads batched 8 deep per lane) -------
+    int sv = sv_of(0);
+    if (sv < 0) return;
+    // first super-voxel: metadata with plain loads
+    {
+        const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv) * (S2 + 1);
+        for (int k = lane; k <= S2; k += 32) scoff2[k] = coff[k];
         const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
-        const int band_tot = load_band_layout(bd, Vg, bdesc, boff, bview, lane);
-        for (int f0 = 0; f0 < band_tot; f0 += 256) {
-            float2 tmp[8];
+        for (int v = lane; v < Vg; v += 32) bdesc2[v] = bd[v];
+        __syncwarp();
+    }
+    int count = build_list(scoff2, tl2);
+    const uint8_t *svcols = A.cols + A.sv_base[(int64_t)g * A.nsv + sv];
+    uint32_t issued = 0, seq = 0;     // ring positions issued / consumed (per warp)
+    if (lane == 0)
+        for (int q = 0; q < min(count, kRing); ++q) issue(issued + q, svcols, scoff2, tl2, q);
+    issued += min(count, kRing);
+    int cur = 0;
+    int status_seen = 0;
+
+    for (int m = 0; sv >= 0; ++m) {
+        uint32_t *bdesc = bdesc2 + cur * A.max_views;
+        uint32_t *scoff = scoff2 + cur * (S2 + 1);
+        uint16_t *tl = tl2 + cur * S2;
+        uint32_t *bdesc_n = bdesc2 + (cur ^ 1) * A.max_views;
+        uint32_t *scoff_n = scoff2 + (cur ^ 1) * (S2 + 1);
+        uint16_t *tl_n = tl2 + (cur ^ 1) * S2;
+        const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
+
+        // --- band layout; band, X and consensus tiles of every chain --------
+        const int band_tot = load_band_layout(bdesc, Vg, bdesc, boff, bview, lane);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = f0 + u * 32 + lane;
-                if (f < band_tot) tmp[u] = eLg[band_global(f, bdesc, boff, bview, A.D)];
+        for (int k = 0; k < K; ++k) {
+            uint8_t *ch = chain(k);
+            float2 *beL = (float2 *)(ch + Ly.beL);
+            float *xt = (float *)(ch + Ly.xt);
+            double *wbs = (double *)(ch + Ly.wst);
+            float *ws = (float *)(ch + Ly.wst + (size_t)S2 * 8);
+            const float2 *eL = eLk(k);
+            for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[band_global(f, bdesc, boff, bview, A.D)]);
+            const float *Xg = Xk(k);
+            for (int q = lane; q < T2 * T2; q += 32) {
+                const int i = si * S + q / T2 - 1, j = sj * S + q % T2 - 1;
+                if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&xt[q], &Xg[(int64_t)i * A.nx + j]);
+                else xt[q] = 0.f;
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int f = f0 + u * 32 + lane;
-                if (f < band_tot) {
-                    beL[f] = tmp[u];
-                    bsnap[f] = tmp[u].x;
+            if (!A.vexp) {
+                const double *wb = A.wbar + (int64_t)(grp * K + k) * n;
+                const float *wk = A.w + ((int64_t)(grp * K + k) * A.N + g) * n;
+                for (int q = lane; q < S2; q += 32) {
+                    const int i = si * S + q / S, j = sj * S + q % S;
+                    if (i < A.ny && j < A.nx) {
+                        cp_async8(&wbs[q], &wb[(int64_t)i * A.nx + j]);
+                        cp_async4(&ws[q], &wk[(int64_t)i * A.nx + j]);
+                    }
                 }
             }
         }
-        // --- X tile with halo, v tile ---------------------------------------
-        {
-            float tmp[(T2 * T2 + 31) / 32];
-#pragma unroll
-            for (int u = 0; u < (T2 * T2 + 31) / 32; ++u) {
-                const int k = u * 32 + lane;
-                const int i = si * S + k / T2 - 1, j = sj * S + k % T2 - 1;
-                tmp[u] = (k < T2 * T2 && i >= 0 && i < A.ny && j >= 0 && j < A.nx) ? Xg[(int64_t)i * A.nx + j] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < (T2 * T2 + 31) / 32; ++u) {
-                const int k = u * 32 + lane;
-                if (k < T2 * T2) xt[k] = tmp[u];
+        if (A.nb26) {
+            // X tiles of the neighbouring slices (volumes run one chain per warp)
+            const int z = grp * K;
+            for (int h = 0; h < 2; ++h) {
+                const int zz = z + (h ? 1 : -1);
+                float *ht = h ? halo_hi : halo_lo;
+                const float *Xz = (zz >= 0 && zz < A.B) ? A.X + ((int64_t)zz * A.N + g) * n : nullptr;
+                for (int q = lane; q < T2 * T2; q += 32) {
+                    const int i = si * S + q / T2 - 1, j = sj * S + q % T2 - 1;
+                    if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&ht[q], &Xz[(int64_t)i * A.nx + j]);
+                    else ht[q] = 0.f;
+                }
             }
         }
+        cp_async_commit();
+        // next super-voxel: claim its metadata while this one runs
+        const int sv_n = sv_of(m + 1);
+        const uint8_t *svcols_n = nullptr;
+        if (sv_n >= 0) {
+            svcols_n = A.cols + A.sv_base[(int64_t)g * A.nsv + sv_n];
+            const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv_n) * (S2 + 1);
+            for (int k = lane; k <= S2; k += 32) cp_async4(&scoff_n[k], &coff[k]);
+            const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv_n * Vg;
+            for (int v = lane; v < Vg; v += 32) cp_async4(&bdesc_n[v], &bd[v]);
+        }
+        cp_async_commit();
+        if (lane == 0) status_seen = *((volatile int *)A.status);
+        cp_async_wait_all();
+        __syncwarp();
+        status_seen = __shfl_sync(FULL, status_seen, 0);
+        int count_n = 0;
+        if (sv_n >= 0) count_n = build_list(scoff_n, tl_n);
 #pragma unroll
-        for (int u = 0; u < (S2 + 31) / 32; ++u) {
-            const int k = u * 32 + lane;
-            const int i = si * S + k / S, j = sj * S + k % S;
-            if (k < S2) {
+        for (int k = 0; k < K; ++k) {
+            uint8_t *ch = chain(k);
+            const float2 *beL = (const float2 *)(ch + Ly.beL);
+            float *bsnap = (float *)(ch + Ly.bsnap);
+            float *vt = (float *)(ch + Ly.vt);
+            const double *wbs = (const double *)(ch + Ly.wst);
+            const float *ws = (const float *)(ch + Ly.wst + (size_t)S2 * 8);
+            for (int f = lane; f < band_tot; f += 32) bsnap[f] = beL[f].x;
+            for (int q = lane; q < S2; q += 32) {
+                const int i = si * S + q / S, j = sj * S + q % S;
                 float vv = 0.f;
                 if (i < A.ny && j < A.nx) {
                     const int64_t s = (int64_t)i * A.nx + j;
-                    vv = vg ? vg[s] : (float)(2.0 * wbg[s] - (double)wg[s]);
+                    vv = A.vexp ? A.vexp[((int64_t)(grp * K + k) * A.N + g) * n + s]
+                                : (float)(2.0 * wbs[q] - (double)ws[q]);
                 }
-                vt[k] = vv;
+                vt[q] = vv;
             }
         }
         __syncwarp();
+        if (status_seen != 0) {
+            // another warp gave up: drain this warp's copies in flight and stop
+            for (uint32_t q2 = seq; q2 < issued; ++q2) {
+                uint32_t sp2 = 0;
+                while (!mbar_try_wait(&bars[q2 % kRing], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
+            }
+            return;
+        }
 
         // --- visit the pixels ------------------------------------------------
+        int nq = 0;   // columns of the next super-voxel issued so far
         for (int q = 0; q < count; ++q) {
             const int t = tl[q];
             const int ti = t / S, tj = t % S;
             const int i = si * S + ti, j = sj * S + tj;
-            // prior through the surrogate weights (lanes 0..7: the 8
-            // neighbours); needs only the X tile, so it overlaps the column's
-            // arrival
             const int tc = (ti + 1) * T2 + (tj + 1);
-            const float xs = xt[tc];
-            float pr1 = 0.f, pr2 = 0.f;
-            if (lane < 8) {
-                const int ii = i + pdi, jj = j + pdj;
-                if (ii >= 0 && ii < A.ny && jj >= 0 && jj < A.nx) {
-                    const float d = xs - xt[tc + pdi * T2 + pdj];
-                    pr2 = pb * prior_weight(A, d);
-                    pr1 = pr2 * d;
+            // prior through the surrogate weights (lanes 0..7: the 8
+            // neighbours), from the X tile only: overlaps the column's arrival
+            float xs[K], pr1[K], pr2[K], prox[K];
+            const int zc = grp * K;   // slice of chain 0 (volumes)
+            const bool nb_in = lane < nlanes && i + pdi >= 0 && i + pdi < A.ny && j + pdj >= 0 && j + pdj < A.nx &&
+                               (pdz == 0 || (zc + pdz >= 0 && zc + pdz < A.B));
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float *xt = (const float *)(chain(k) + Ly.xt);
+                const float *vt = (const float *)(chain(k) + Ly.vt);
+                xs[k] = xt[tc];
+                pr1[k] = 0.f;
+                pr2[k] = 0.f;
+                if (nb_in) {
+                    const float *nt = pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi);
+                    const float d = xs[k] - nt[tc + pdi * T2 + pdj];
+                    pr2[k] = pb * prior_weight(A, d);
+                    pr1[k] = pr2[k] * d;
                 }
+                prox[k] = (xs[k] - vt[t]) * A.inv_s2;
             }
-            const float prox = (xs - vt[t]) * A.inv_s2;
-            const uint32_t stg = (seq + q) % kRing;
-            const uint32_t parity = ((seq + q) / kRing) & 1u;
+            const uint32_t stg = seq % kRing;
+            const uint32_t parity = (seq / kRing) & 1u;
             uint32_t spins = 0;
             while (!mbar_try_wait(&bars[stg], parity)) {
                 if (++spins > kSpinLimit) {
                     // give up: flag the host, then wait (bounded) for this
                     // warp's copies still in flight before leaving
                     if (lane == 0) atomicExch(A.status, kStatusTimeout);
-                    const int last = min(count, q + kRing);
-                    for (int q2 = q + 1; q2 < last; ++q2) {
+                    for (uint32_t q2 = seq + 1; q2 < issued; ++q2) {
                         uint32_t sp2 = 0;
-                        while (!mbar_try_wait(&bars[(seq + q2) % kRing], ((seq + q2) / kRing) & 1u) &&
-                               ++sp2 < kSpinLimit) {}
+                        while (!mbar_try_wait(&bars[q2 % kRing], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
                     }
                     return;
                 }
@@ -906,86 +1013,128 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             const int nnz = cidx[0];
             const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
 
-            // data term: p1 = -sum A Lambda e, p2 = sum A^2 Lambda
-            float p1 = pr1, p2 = pr2;
-            constexpr int RC = MR > 0 ? MR : 1;
-            float ca[RC], ce[RC];
-            int cb[RC];
+            // data term of each chain: p1 = -sum A Lambda e, p2 = sum A^2 Lambda
+            float p1[K], p2[K];
 #pragma unroll
-            for (int r = 0; r < RC; ++r) {
-                const int k = r * 32 + lane;
-                ca[r] = 0.f;
-                cb[r] = 0;
-                ce[r] = 0.f;
-                if (MR > 0 && k < nnz) {
-                    cb[r] = cidx[1 + k];
-                    ca[r] = ld_val<T>(cval, k);
-                }
-            }
+            for (int k = 0; k < K; ++k) { p1[k] = pr1[k]; p2[k] = pr2[k]; }
+            constexpr int RC = MR > 0 ? MR : 1;
+            float ca[RC], ce[K][RC];
+            int cb[RC];
             if (MR > 0) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r) {
+                    const int e = r * 32 + lane;
+                    ca[r] = 0.f;
+                    cb[r] = 0;
+                    if (e < nnz) {
+                        cb[r] = cidx[1 + e];
+                        ca[r] = ld_val<T>(cval, e);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
                     if (r * 32 + lane < nnz) {
-                        const float2 el = beL[cb[r]];
-                        ce[r] = el.x;
-                        p1 = fmaf(-ca[r] * el.y, el.x, p1);
-                        p2 = fmaf(ca[r] * ca[r], el.y, p2);
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const float2 el = ((const float2 *)(chain(k) + Ly.beL))[cb[r]];
+                            ce[k][r] = el.x;
+                            p1[k] = fmaf(-ca[r] * el.y, el.x, p1[k]);
+                            p2[k] = fmaf(ca[r] * ca[r], el.y, p2[k]);
+                        }
                     }
                 }
             } else {
-                for (int k = lane; k < nnz; k += 32) {
-                    const float a = ld_val<T>(cval, k);
-                    const float2 el = beL[cidx[1 + k]];
-                    p1 = fmaf(-a * el.y, el.x, p1);
-                    p2 = fmaf(a * a, el.y, p2);
+                const float2 *beL = (const float2 *)(chain(0) + Ly.beL);
+                for (int e = lane; e < nnz; e += 32) {
+                    const float a = ld_val<T>(cval, e);
+                    const float2 el = beL[cidx[1 + e]];
+                    p1[0] = fmaf(-a * el.y, el.x, p1[0]);
+                    p2[0] = fmaf(a * a, el.y, p2[0]);
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                p1 += __shfl_xor_sync(FULL, p1, o);
-                p2 += __shfl_xor_sync(FULL, p2, o);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    p1[k] += __shfl_xor_sync(FULL, p1[k], o);
+                    p2[k] += __shfl_xor_sync(FULL, p2[k], o);
+                }
             }
-            // the step's sign and zero set come from num alone, so a fast
-            // division leaves the fixed point unchanged
-            const float num = p1 + prox;
-            const float den = p2 + A.inv_s2;
-            const float alpha = -__fdividef(num, den);
+            // the step's sign and zero set come from the numerator alone, so a
+            // fast division leaves the fixed point unchanged
+            float alpha[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) alpha[k] = -__fdividef(p1[k] + prox[k], p2[k] + A.inv_s2);
             // update e: the entries of one column are distinct band positions
             if (MR > 0) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r)
-                    if (r * 32 + lane < nnz) beL[cb[r]].x = fmaf(-ca[r], alpha, ce[r]);
+                    if (r * 32 + lane < nnz) {
+#pragma unroll
+                        for (int k = 0; k < K; ++k)
+                            ((float2 *)(chain(k) + Ly.beL))[cb[r]].x = fmaf(-ca[r], alpha[k], ce[k][r]);
+                    }
             } else {
-                for (int k = lane; k < nnz; k += 32) {
-                    const int bb = cidx[1 + k];
-                    beL[bb].x = fmaf(-ld_val<T>(cval, k), alpha, beL[bb].x);
+                float2 *beL = (float2 *)(chain(0) + Ly.beL);
+                for (int e = lane; e < nnz; e += 32) {
+                    const int bb = cidx[1 + e];
+                    beL[bb].x = fmaf(-ld_val<T>(cval, e), alpha[0], beL[bb].x);
                 }
             }
-            if (lane == 0) xt[tc] = xs + alpha;
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) ((float *)(chain(k) + Ly.xt))[tc] = xs[k] + alpha[k];
+            }
+            ++seq;
             __syncwarp();
-            // refill the ring slot just freed.  Every read of the slot has
+            // refill the ring slot just freed (the next column of this
+            // super-voxel, else of the next one).  Every read of the slot has
             // completed: its values fed the reduction all lanes joined before
             // the __syncwarp above, so the TMA write cannot overtake them.
-            if (lane == 0 && q + kRing < count) {
-                const int t2 = tl[q + kRing];
-                mbar_expect_tx(&bars[stg], scoff[t2 + 1] - scoff[t2]);
-                tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + scoff[t2], scoff[t2 + 1] - scoff[t2], &bars[stg]);
+            if (q + kRing < count) {
+                if (lane == 0) issue(issued, svcols, scoff, tl, q + kRing);
+                ++issued;
+            } else if (nq < count_n) {
+                if (lane == 0) issue(issued, svcols_n, scoff_n, tl_n, nq);
+                ++issued;
+                ++nq;
             }
         }
-        seq += count;
 
-        // --- write back: X tile and the change of e --------------------------
+        // --- write back: X tiles and the change of e --------------------------
 #pragma unroll
-        for (int u = 0; u < (S2 + 31) / 32; ++u) {
-            const int k = u * 32 + lane;
-            const int i = si * S + k / S, j = sj * S + k % S;
-            if (k < S2 && i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(k / S + 1) * T2 + (k % S + 1)];
-        }
-        for (int f = lane; f < band_tot; f += 32) {
-            const float de = beL[f].x - bsnap[f];
-            if (de != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, A.D)].x, de);
+        for (int k = 0; k < K; ++k) {
+            uint8_t *ch = chain(k);
+            const float *xt = (const float *)(ch + Ly.xt);
+            float *Xg = Xk(k);
+            for (int q = lane; q < S2; q += 32) {
+                const int i = si * S + q / S, j = sj * S + q % S;
+                if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(q / S + 1) * T2 + (q % S + 1)];
+            }
+            const float2 *beL = (const float2 *)(ch + Ly.beL);
+            const float *bsnap = (const float *)(ch + Ly.bsnap);
+            float2 *eL = eLk(k);
+            for (int f = lane; f < band_tot; f += 32) {
+                const float de = beL[f].x - bsnap[f];
+                if (de != 0.f) atomicAdd(&eL[band_global(f, bdesc, boff, bview, A.D)].x, de);
+            }
         }
         __syncwarp();
+        // the next super-voxel's first columns: those not issued yet
+        if (sv_n >= 0) {
+            while (nq < min(count_n, kRing) && (int)(issued - seq) < kRing) {
+                if (lane == 0) issue(issued, svcols_n, scoff_n, tl_n, nq);
+                ++issued;
+                ++nq;
+            }
+        }
+        // hand the staged next-super-voxel state over
+        sv = sv_n;
+        svcols = svcols_n;
+        count = count_n;
+        cur ^= 1;
+        // now exactly min(count, kRing) columns of the new super-voxel are in
+        // flight, as the pixel loop's refill (column q + kRing) assumes
     }
 }
 
@@ -1276,32 +1425,33 @@ static int launch_forward(mace_state *st)
 typedef void (*sweep_fn)(SweepArgs);
 
 template <typename T, int S>
-static sweep_fn sweep_kernel_ptr_s(const mace_sysmatrix *M)
+static sweep_fn sweep_kernel_ptr_s(const mace_sysmatrix *M, int K)
 {
     // entries per column in rounds of 32 lanes
     const int rounds = (M->max_nnz + 31) / 32;
-    if (rounds <= 3) return icd_sweep_kernel<T, 3, S>;
-    if (rounds <= 5) return icd_sweep_kernel<T, 5, S>;
-    return icd_sweep_kernel<T, 0, S>;
+    if (rounds <= 3) return K == 4 ? icd_sweep_kernel<T, 3, S, 4> : K == 2 ? icd_sweep_kernel<T, 3, S, 2> : icd_sweep_kernel<T, 3, S, 1>;
+    if (rounds <= 4) return K == 4 ? icd_sweep_kernel<T, 4, S, 4> : K == 2 ? icd_sweep_kernel<T, 4, S, 2> : icd_sweep_kernel<T, 4, S, 1>;
+    if (rounds <= 5) return K == 4 ? icd_sweep_kernel<T, 5, S, 4> : K == 2 ? icd_sweep_kernel<T, 5, S, 2> : icd_sweep_kernel<T, 5, S, 1>;
+    return K == 1 ? icd_sweep_kernel<T, 0, S, 1> : nullptr;
 }
 
 template <typename T>
-static sweep_fn sweep_kernel_ptr_t(const mace_sysmatrix *M)
+static sweep_fn sweep_kernel_ptr_t(const mace_sysmatrix *M, int K)
 {
     switch (M->S) {
-    case 4: return sweep_kernel_ptr_s<T, 4>(M);
-    case 8: return sweep_kernel_ptr_s<T, 8>(M);
-    case 16: return sweep_kernel_ptr_s<T, 16>(M);
+    case 4: return sweep_kernel_ptr_s<T, 4>(M, K);
+    case 8: return sweep_kernel_ptr_s<T, 8>(M, K);
+    case 16: return K == 1 ? sweep_kernel_ptr_s<T, 16>(M, 1) : nullptr;
     default: return nullptr;
     }
 }
 
-static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M)
+static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K)
 {
     switch (M->dtype) {
-    case MACE_F32: return sweep_kernel_ptr_t<float>(M);
-    case MACE_BF16: return sweep_kernel_ptr_t<__nv_bfloat16>(M);
-    default: return sweep_kernel_ptr_t<__half>(M);
+    case MACE_F32: return sweep_kernel_ptr_t<float>(M, K);
+    case MACE_BF16: return sweep_kernel_ptr_t<__nv_bfloat16>(M, K);
+    default: return sweep_kernel_ptr_t<__half>(M, K);
     }
 }
 
@@ -1345,12 +1495,16 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     double bsum = 4.0 + 4.0 / std::sqrt(2.0);
     A.b_edge = (float)(1.0 / bsum);
     A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
-    CUDA_TRY(cudaMemsetAsync(st->d_counter, 0, sizeof(int) * st->B * M->N, st->stream));
+    A.nb26 = st->P.neighbourhood == 26;
+    double b3 = 6.0 + 12.0 / std::sqrt(2.0) + 8.0 / std::sqrt(3.0);
+    A.b26[0] = (float)(1.0 / b3);
+    A.b26[1] = (float)(1.0 / std::sqrt(2.0) / b3);
+    A.b26[2] = (float)(1.0 / std::sqrt(3.0) / b3);
     A.nwarps = st->sweep_warps;
     dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
-    sweep_kernel_ptr(M)<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    sweep_kernel_ptr(M, st->chains)<<<grid, block, st->sweep_smem, st->stream>>>(A);
     if (rec) {
         CUDA_TRY(cudaEventRecord(st->ev[st->ev_used + 1], st->stream));
         st->ev_used += 2;
@@ -1368,11 +1522,29 @@ static int configure_sweep(mace_state *st)
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int col_stride = (M->max_col_bytes + 15) & ~15;
-    st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views);
-    sweep_fn fn = sweep_kernel_ptr(M);
+    // chains per warp: reconstructions of the batch that share each column
+    // load (a divisor of the batch; 1 when the columns are not cached)
+    int K = 1;
+    if ((M->max_nnz + 31) / 32 <= 5 && M->S != 16 && st->P.neighbourhood != 26) {
+        // one chain unless asked: sharing the column between chains saves
+        // column traffic but costs registers and shared memory, and measured
+        // slower on the 512^2 workload
+        const int want = st->P.chains > 0 ? st->P.chains : 1;
+        for (int k : {4, 2})
+            if (k <= want && st->B % k == 0) { K = k; break; }
+    }
+    sweep_fn fn = nullptr;
+    for (;;) {
+        st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views, K);
+        fn = sweep_kernel_ptr(M, K);
+        if (fn && st->warp_smem <= (size_t)max_smem) break;
+        if (K == 1) break;
+        K /= 2;
+    }
     if (!fn) return fail(MACE_EINVAL, "unsupported super-voxel size");
     if (st->warp_smem > (size_t)max_smem)
         return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
+    st->chains = K;
     CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     // block size (warps) that keeps the most warps resident per SM
     int wpb = 1, per_sm = 0, best = 0;
@@ -1383,8 +1555,9 @@ static int configure_sweep(mace_state *st)
         if (b * w > best) { best = b * w; wpb = w; per_sm = b; }
     }
     if (per_sm < 1) per_sm = 1;
-    // concurrency C super-voxels per (reconstruction, agent): B N C warps, all resident
-    const int64_t pairs = (int64_t)st->B * M->N;
+    // C warps per (batch group, agent): super-voxels of one agent of one
+    // reconstruction in flight at a time; all warps resident
+    const int64_t pairs = (int64_t)(st->B / K) * M->N;
     int64_t capacity = (int64_t)per_sm * nsm * wpb;
     int64_t C = capacity / pairs;
     if (C < 1) C = 1;
@@ -1426,7 +1599,7 @@ static int check_params(const mace_params *P)
 {
     if (!P) return fail(MACE_EINVAL, "params is NULL");
     if (P->prior != 0 && P->prior != 1) return fail(MACE_EINVAL, "prior must be 0 (quadratic) or 1 (Q-GGMRF)");
-    if (P->neighbourhood != 8) return fail(MACE_EINVAL, "neighbourhood must be 8 for 2D");
+    if (P->neighbourhood != 8 && P->neighbourhood != 26) return fail(MACE_EINVAL, "neighbourhood must be 8 or 26");
     if (!(P->beta >= 0) || !(P->sigma_x > 0) || !std::isfinite(P->beta) || !std::isfinite(P->sigma_x))
         return fail(MACE_EINVAL, "beta must be >= 0 and sigma_x > 0");
     if (P->prior == 1 && (P->p != 2.0 || !(P->q >= 1.0 && P->q <= 2.0) || !(P->T > 0)))
@@ -1440,6 +1613,8 @@ static int check_params(const mace_params *P)
     if (!(P->tol >= 0)) return fail(MACE_EINVAL, "tol must be >= 0");
     if (P->concurrency < 0) return fail(MACE_EINVAL, "concurrency must be >= 0");
     if (P->sv_order != 0 && P->sv_order != 1) return fail(MACE_EINVAL, "sv_order must be 0 or 1");
+    if (P->chains != 0 && P->chains != 1 && P->chains != 2 && P->chains != 4)
+        return fail(MACE_EINVAL, "chains must be 0, 1, 2 or 4");
     return MACE_OK;
 }
 
@@ -1885,10 +2060,11 @@ extern "C" int mace_wait_selftest(uint32_t spin_limit, void *cuda_stream)
 }
 
 extern "C" int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs, double *last_residual,
-                              int32_t *concurrency)
+                              int32_t *concurrency, int32_t *chains)
 {
     if (!st) return fail(MACE_EINVAL, "state is NULL");
     if (concurrency) *concurrency = st->concurrency;
+    if (chains) *chains = st->chains;
     if (iters) *iters = st->iters;
     if (sigma_abs) *sigma_abs = st->sigma_abs;
     if (last_residual) *last_residual = st->last_resid;

@@ -57,7 +57,8 @@ def test_visit_order_is_permutation(gpu_lib, sv_order, conc):
 
 @pytest.mark.parametrize("prior", ["quadratic", "qggmrf"])
 @pytest.mark.parametrize("backward", [False, True])
-def test_one_pass_matches_algorithm2(gpu_lib, prior, backward):
+@pytest.mark.parametrize("batch", [1, 4])
+def test_one_pass_matches_algorithm2(gpu_lib, prior, backward, batch):
     """With one super-voxel per agent in flight, a GPU pass is Algorithm 2 in
     the library's visiting order: compare X after one pass from a random state."""
     mace = gpu_lib
@@ -66,26 +67,31 @@ def test_one_pass_matches_algorithm2(gpu_lib, prior, backward):
     sm = _build(mace, c)
     rng = np.random.default_rng(1)
     xs = central_reference(64, 90, 95, 4, prior)
-    X0 = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
+    # the same scan in every batch slot, different starting states
+    X0 = (xs[None, None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((batch, N, n))).astype(np.float32)
     w0 = X0.copy()
-    v = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
-    prm = mace.make_params(prior=prior, sigma_x=c["sigma_x"], sigma=0.5, sigma_mode=1, concurrency=1)
-    st = mace.mace_init(sm, c["y"], c["lam"], prm)
+    v = (xs[None, None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((batch, N, n))).astype(np.float32)
+    prm = mace.make_params(prior=prior, sigma_x=c["sigma_x"], sigma=0.5, sigma_mode=1, concurrency=1,
+                           chains=batch)
+    st = mace.mace_init(sm, np.stack([c["y"]] * batch), np.stack([c["lam"]] * batch), prm, batch=batch)
+    assert st.stats()["chains"] == batch
     st.set_state(w0, X0)
     st.prox_pass(v, backward=backward)
     _, Xg = st.get_state()
+    Xg = Xg.reshape(batch, N, n)
     sigma = st.stats()["sigma_abs"]
     order = st.visit_order()
     if backward:
         order = order[::-1].copy()
-    for g in range(N):
-        x = X0[g].astype(np.float64)
-        e = P.error_sinogram(g, x)
-        P.icd_sweep(g, x, e, v=v[g].astype(np.float64), sigma=sigma, order=order)
-        err = nrmse(Xg[g], x)
-        assert err < 2e-5, (g, err)
-        # the pass moved the state
-        assert nrmse(X0[g], x) > 1e-3
+    for b in range(batch):
+        for g in range(N):
+            x = X0[b, g].astype(np.float64)
+            e = P.error_sinogram(g, x)
+            P.icd_sweep(g, x, e, v=v[b, g].astype(np.float64), sigma=sigma, order=order)
+            err = nrmse(Xg[b, g], x)
+            assert err < 2e-5, (b, g, err)
+            # the pass moved the state
+            assert nrmse(X0[b, g], x) > 1e-3
     st.close()
     sm.close()
 

@@ -79,24 +79,27 @@ def test_full_size_512_parity(gpu_lib):
             print("512^2: inputs differ from the stored reference's; NRMSE check skipped")
 
 
-def test_batch_same_alone_and_in_the_mix(gpu_lib):
-    """Three different scans in one batch reconstruct to the same images as
-    each alone (within the FP32 tolerance), at the concurrency a batch uses."""
+@pytest.mark.parametrize("batch,chains", [(3, 0), (4, 4), (4, 2)])
+def test_batch_same_alone_and_in_the_mix(gpu_lib, batch, chains):
+    """Different scans in one batch reconstruct to the same images as each
+    alone (within the FP32 tolerance), whether one warp updates one, two or
+    four of them together over shared column loads."""
     mace = gpu_lib
     n, V, D, N = 64, 90, 95, 4
     ys, ls = [], []
-    for k in range(3):
+    for k in range(batch):
         cc = synth.make_case(n=n, n_views=V, n_channels=D, I0=1e4, mu_max=0.02, seed=40 + k, noise_seed=140 + k)
         ys.append(cc["y"][0])
         ls.append(cc["lam"][0])
     sx = synth.prior_sigma_x(ls[0], V, frac=1.0)
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=8)
     prm = mace.make_params(prior="quadratic", sigma_x=sx, sigma=0.5, rho=0.8, sweeps_per_iter=2, symmetric=True,
-                           concurrency=1, tol=1e-7, max_iter=5000, recompute_every=10)
-    stb = mace.mace_init(sm, np.stack(ys), np.stack(ls), prm, batch=3)
+                           concurrency=1, tol=1e-7, max_iter=5000, recompute_every=10, chains=chains)
+    stb = mace.mace_init(sm, np.stack(ys), np.stack(ls), prm, batch=batch)
+    print("batch %d: %d chains per warp" % (batch, stb.stats()["chains"]))
     xb, itb, rb, cb = stb.reconstruct()
     assert cb
-    for k in range(3):
+    for k in range(batch):
         st = mace.mace_init(sm, ys[k], ls[k], prm)
         x1, it1, r1, c1 = st.reconstruct()
         assert c1
