@@ -224,6 +224,55 @@ CONFIGS = {
 }
 
 
+def ellipsoids(seed, n, nz, mu_max, count=12):
+    """Random ellipsoids (x0, y0, z0, a, b, c, phi, value) in pixel units, the
+    volume centred at the origin (slices at z = k - (nz-1)/2), axis c along z;
+    values scaled so the volume's maximum is mu_max."""
+    rng = CounterRNG(seed)
+    u = rng.uniform(2, np.arange(8 * count)).reshape(count, 8)
+    r = 0.4 * n * np.sqrt(u[:, 0])
+    ang = 2.0 * np.pi * u[:, 1]
+    x0, y0 = r * np.cos(ang), r * np.sin(ang)
+    z0 = (u[:, 2] - 0.5) * 0.8 * nz
+    a = n * (0.05 + 0.25 * u[:, 3])
+    b = n * (0.05 + 0.25 * u[:, 4])
+    c = nz * (0.2 + 0.5 * u[:, 5])
+    phi = np.pi * u[:, 6]
+    val = mu_max * (0.1 + 0.4 * u[:, 7])
+    Q = np.stack([x0, y0, z0, a, b, c, phi, val], axis=1)
+    peak = max(phantom_image(slice_ellipses(Q, z, nz), n, supersample=2).max() for z in range(nz))
+    if peak > 0:
+        Q[:, 7] *= mu_max / peak
+    return Q
+
+
+def slice_ellipses(Q, z, nz):
+    """Cross-section of the ellipsoids with slice z: ellipses (x0, y0, a, b, phi, value)."""
+    zc = z - 0.5 * (nz - 1)
+    out = []
+    for x0, y0, z0, a, b, c, phi, val in Q:
+        t = (zc - z0) / c
+        if abs(t) < 1.0:
+            f = math.sqrt(1.0 - t * t)
+            out.append([x0, y0, a * f, b * f, phi, val])
+    return np.array(out).reshape(-1, 6)
+
+
+def make_volume(n, nz, n_views, n_channels, I0, mu_max, seed, noise_seed, **_):
+    """Ellipsoid phantom -> per-slice analytic sinograms -> Poisson data:
+    y, lam [nz, n_views, n_channels] float32 (parallel beam, one 2D geometry
+    for every slice)."""
+    Q = ellipsoids(seed, n, nz, mu_max)
+    ys, ls = [], []
+    for z in range(nz):
+        E = slice_ellipses(Q, z, nz)
+        p = sinogram(E, n_views, n_channels) if len(E) else np.zeros((n_views, n_channels))
+        y, lam = measurements(p, I0, CounterRNG(noise_seed * 1000 + z))
+        ys.append(y)
+        ls.append(lam)
+    return dict(y=np.stack(ys), lam=np.stack(ls), ellipsoids=Q)
+
+
 def make_case(n, n_views, n_channels, I0, mu_max, seed, noise_seed, nz=1, **_):
     """Phantom -> analytic sinogram -> Poisson data for nz identical-geometry
     slices (each slice its own phantom seed offset).  Returns dict with y, lam
