@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+# the timed launch configuration (the full-size parity test runs the same)
+DEFAULTS = dict(batch=2, concurrency=64, sigma=0.1, tol=2.5e-7, max_iter=4000, sv=8, dtype="f32")
+
 WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
                      "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
                 n=512, n_views=720, n_channels=725, n_agents=16)
@@ -108,6 +111,27 @@ def make_inputs(batch, rank):
     y = np.stack(ys).astype(np.float32)
     lam = np.stack(ls).astype(np.float32)
     return y, lam
+
+
+def oracle_match(x, y, lam):
+    """Relative RMSE of the first reconstruction of the batch against the
+    oracle's stored MAP image of the same scan (written by
+    tests/golden/make_reference.py from the oracle alone), when the stored
+    image's input digest matches."""
+    import hashlib
+    path = os.path.join(ROOT, "tests", "golden", "cfg2_reference.npz")
+    if not os.path.exists(path):
+        return {"nrmse_vs_oracle": None, "why": "no stored oracle image"}
+    d = np.load(path)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(y, np.float32).tobytes())
+    h.update(np.ascontiguousarray(lam, np.float32).tobytes())
+    if str(d["digest"]) != h.hexdigest():
+        return {"nrmse_vs_oracle": None, "why": "stored oracle image is of other inputs"}
+    ref = d["x"].reshape(x.shape)
+    err = float(np.sqrt(np.mean((x.astype(np.float64) - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
+    return {"nrmse_vs_oracle": err, "bound": 1e-4, "oracle_kkt": float(d["kkt"]),
+            "oracle_iters": int(d["iters"])}
 
 
 def solver_params(mace, sigma_x, args):
@@ -203,6 +227,7 @@ def run_mace(args, rank, world):
     el, clocks = timed(True, True, args.warmup)
     iters_main = [it for it, _, _ in iters_seen[-args.steps:]]
     conv_main = all(c for _, _, c in iters_seen[-args.steps:])
+    accuracy = oracle_match(d_x[0].cpu().numpy(), y[0], lam[0])
     el_e2e, _ = timed(False, False, 1)
     recons = B * args.steps * world
     value = recons / el
@@ -210,9 +235,11 @@ def run_mace(args, rank, world):
     hbm, peak_kind = peaks()
     # roofline of the ICD sweep kernel: algorithmic bytes per launch = the
     # stored matrix once + per reconstruction the state it reads and writes
+    # (X read and written, w and theta2 read per agent and pixel, the FP64
+    # consensus, the error sinogram read and written once)
     n = WORKLOAD["n"] ** 2
     N = WORKLOAD["n_agents"]
-    per_recon = N * n * (4 + 4 + 4) + n * 8 + 2 * WORKLOAD["n_views"] * WORKLOAD["n_channels"] * 8
+    per_recon = N * n * (4 + 4 + 4 + 4) + n * 8 + 2 * WORKLOAD["n_views"] * WORKLOAD["n_channels"] * 8
     alg_bytes = info["bytes_columns"] + B * per_recon
     avg_launch_s = (timing["ms"] / 1000.0) / max(1, timing["launches"])
     achieved = alg_bytes / avg_launch_s / 1e9 if timing["launches"] else None
@@ -242,6 +269,7 @@ def run_mace(args, rank, world):
         "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv,
                    "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma,
                    "tol": args.tol, "iterations": iters_main, "converged": conv_main,
+                   "accuracy": accuracy,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (stored matrix %.2f GB)" % (info["bytes_columns"] / 1e9)},
         "e2e": {"value": e2e, "unit": "recons/s",
@@ -331,17 +359,27 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mace", choices=["mace", "reference"])
-    ap.add_argument("--batch", type=int, default=2)
-    ap.add_argument("--concurrency", type=int, default=64)
-    ap.add_argument("--sigma", type=float, default=0.1)
-    ap.add_argument("--tol", type=float, default=1e-7)
-    ap.add_argument("--max-iter", dest="max_iter", type=int, default=4000)
-    ap.add_argument("--sv", type=int, default=8)
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--batch", type=int, default=DEFAULTS["batch"])
+    ap.add_argument("--concurrency", type=int, default=DEFAULTS["concurrency"])
+    ap.add_argument("--sigma", type=float, default=DEFAULTS["sigma"])
+    ap.add_argument("--tol", type=float, default=DEFAULTS["tol"])
+    ap.add_argument("--max-iter", dest="max_iter", type=int, default=DEFAULTS["max_iter"])
+    ap.add_argument("--sv", type=int, default=DEFAULTS["sv"])
+    ap.add_argument("--dtype", default=DEFAULTS["dtype"], choices=["f32", "bf16", "f16"])
     ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=2000)
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=0,
+                    help="profiling only: an n x n image with 1.40625 n views and ceil(sqrt(2) n) channels "
+                         "(the same geometry family, smaller), instead of the 512^2 workload")
     args = ap.parse_args()
+    if args.size:
+        n = args.size
+        D = int(math.ceil(math.sqrt(2.0) * n))
+        WORKLOAD.update(n=n, n_views=int(round(1.40625 * n)), n_channels=D,
+                        name="parallel-beam 2D %dx%d, %d views over 180 deg, %d channels, 16 interleaved agents, "
+                             "Q-GGMRF (p=2, q=1.2, T=1), FP32 (profiling size)"
+                             % (n, n, int(round(1.40625 * n)), D))
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

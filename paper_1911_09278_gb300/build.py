@@ -1,15 +1,24 @@
-"""Build the CUDA library libmace.so in-tree for sm_103a (GB300) with nvcc."""
+"""Build the CUDA library libmace.so in-tree for sm_103a (GB300) with nvcc.
+
+The device code is split over a few translation units (the host side with
+the builder and the small kernels, and the ICD sweep kernels once per stored
+value type), compiled in parallel and linked into one shared library."""
+import concurrent.futures
 import os
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "csrc", "mace.cu")
+CSRC = os.path.join(HERE, "csrc")
 HDR = os.path.join(os.path.dirname(HERE), "include", "mace.h")
+UNITS = ["mace.cu", "sweep_f32.cu", "sweep_bf16.cu", "sweep_f16.cu"]
+HEADERS = ["common.cuh", "sweep.cuh"]
 LIB = os.path.join(HERE, "libmace.so")
+OBJDIR = os.path.join(HERE, "_build")
 
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--split-compile", "0",
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo",
               "-gencode", "arch=compute_103a,code=sm_103a",
-              "-Xcompiler", "-fPIC", "-shared"]
+              "-Xcompiler", "-fPIC"]
 
 
 def nvcc():
@@ -17,16 +26,37 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def _sources():
+    return [os.path.join(CSRC, u) for u in UNITS] + [os.path.join(CSRC, h) for h in HEADERS] + [HDR, __file__]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    newest = max(os.path.getmtime(p) for p in _sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", tmp, SRC]
-    subprocess.check_call(cmd)
+    os.makedirs(OBJDIR, exist_ok=True)
+    tag = "%d" % os.getpid()
+
+    def compile_unit(u):
+        obj = os.path.join(OBJDIR, u.replace(".cu", ".%s.o" % tag))
+        cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", "-o", obj,
+                                                                               os.path.join(CSRC, u)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0 or verbose:
+            sys.stderr.write(r.stdout + r.stderr)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed on %s" % u)
+        return obj
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(compile_unit, UNITS))
+    tmp = LIB + ".tmp." + tag
+    subprocess.check_call([nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    print(build(force=True, verbose="-v" in sys.argv))

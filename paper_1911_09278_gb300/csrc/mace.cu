@@ -11,17 +11,14 @@
 //                      ||w^(k+1) - w^(k)||^2 and ||w^(k+1)||^2.
 //
 // The stored system matrix is voxel-column-major per super-voxel (an SxS tile
-// of pixels): for every agent, super-voxel and pixel, a column holding, per
-// view of the agent, a run (first channel relative to the super-voxel's
-// sinogram band, length 0..3) and its values.  One warp owns one super-voxel
-// at a time: it stages the super-voxel's band of the agent's error sinogram
-// e_i and weights Lambda_i in shared memory, streams the columns in with TMA
-// bulk copies into a per-warp ring, visits the pixels in order (lane = view),
-// and flushes its change of e back to global memory at the end.
-#include <cuda_runtime.h>
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <stdint.h>
+// of pixels): for every agent, super-voxel and pixel, a column listing the
+// pixel's non-zeros as (position in the super-voxel's band of the agent's
+// sinogram, value) pairs; the format is in common.cuh.  One warp owns one
+// super-voxel at a time (sweep.cuh): it stages the super-voxel's band of the
+// agent's error sinogram e_i and weights Lambda_i in shared memory, streams
+// the columns in with TMA bulk copies into a per-warp ring, visits the pixels
+// in order, and flushes its change of e back to global memory at the end.
+// This file holds the matrix builder, the other kernels and the host side.
 #include <string.h>
 #include <math.h>
 
@@ -32,7 +29,8 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mace.h"
+#include "common.cuh"
+#include "sweep.cuh"
 
 // ---------------------------------------------------------------------------
 // error handling
@@ -57,11 +55,6 @@ extern "C" const char *mace_last_error(void) { return g_last_error.c_str(); }
 // ---------------------------------------------------------------------------
 // constants
 // ---------------------------------------------------------------------------
-static constexpr int kMaxViews = 4096;     // per geometry
-static constexpr int kRing = 8;            // column ring stages per warp
-static constexpr uint32_t kSpinLimit = 1u << 26;  // bounded device waits
-static constexpr int kStatusTimeout = 1;
-
 // ---------------------------------------------------------------------------
 // geometry: strip-integral footprint of a square pixel (FP64, IEEE ops only)
 // ---------------------------------------------------------------------------
@@ -181,18 +174,6 @@ __global__ void band_kernel(GeoParams G, const double2 *__restrict__ cs, const i
     band[(int64_t)nsv * view_off[g] + (int64_t)sv * Vg + v] = d;
 }
 
-// Column of one pixel for one agent (the per-view runs, flattened):
-//   u16 nnz; u16 bidx[nnz]  (position of each value in the super-voxel's
-//                            band: runs of the agent's views in view order)
-//   padding to 16 bytes; T vals[nnz]; padding to 16 bytes.
-// View v's band covers channels [lo_v, lo_v + len_v) and starts at
-// boff_v = sum_{u < v} len_u, so the value of channel c sits at
-// boff_v + c - lo_v: the run (first channel, length, values) of every view is
-// recoverable from bidx and the band descriptors.
-__host__ __device__ inline uint32_t col_bytes_of(int nnz, int vbytes)
-{
-    return ((2u + 2u * (uint32_t)nnz + 15u) & ~15u) + (((uint32_t)nnz * vbytes + 15u) & ~15u);
-}
 __global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
                                int N, int S, int nsvx, int nsv, int vbytes,
                                uint32_t *__restrict__ col_bytes, uint32_t *__restrict__ col_nnz)
@@ -247,12 +228,12 @@ __global__ void fill_kernel(GeoParams G, const double2 *__restrict__ cs, const i
         int c0;
         int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
         int lo = (int)(bd[v] & 0xFFFFu);
-        for (int k = 0; k < L; ++k) bidx[1 + nz + k] = (uint16_t)(boff + c0 - lo + k);
+        for (int k = 0; k < L; ++k) bidx[2 + nz + k] = (uint16_t)(boff + c0 - lo + k);
         nz += L;
         boff += (int)(bd[v] >> 16);
     }
-    bidx[0] = (uint16_t)nz;
-    T *vals = (T *)(col + ((2 + 2 * nz + 15) & ~15));
+    *(uint32_t *)col = (uint32_t)nz;
+    T *vals = (T *)(col + col_idx_bytes(nz));
     nz = 0;
     for (int v = 0; v < Vg; ++v) {
         double a[3];
@@ -488,14 +469,14 @@ extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t
         CUDA_TRY(cudaMemcpy(col.data(), M->d_cols + base + off[0], col.size(), cudaMemcpyDeviceToHost));
     for (int v = 0; v < Vg; ++v) { c0[v] = 0; len[v] = 0; vals[3 * v] = vals[3 * v + 1] = vals[3 * v + 2] = 0.f; }
     if (col.empty()) return MACE_OK;
-    uint16_t nz;
-    memcpy(&nz, col.data(), 2);
-    const uint8_t *vals_p = col.data() + ((2 + 2 * nz + 15) & ~15);
+    uint32_t nz;
+    memcpy(&nz, col.data(), 4);
+    const uint8_t *vals_p = col.data() + col_idx_bytes((int)nz);
     std::vector<int> boff(Vg + 1, 0);
     for (int v = 0; v < Vg; ++v) boff[v + 1] = boff[v] + (int)(bd[v] >> 16);
     for (int k = 0; k < nz; ++k) {
         uint16_t b;
-        memcpy(&b, col.data() + 2 + 2 * k, 2);
+        memcpy(&b, col.data() + 4 + 2 * k, 2);
         int v = (int)(std::upper_bound(boff.begin(), boff.end(), (int)b) - boff.begin()) - 1;
         int ch = (int)(bd[v] & 0xFFFFu) + (b - boff[v]);
         if (len[v] == 0) c0[v] = ch;
@@ -535,10 +516,10 @@ struct mace_state {
     float *d_w = nullptr;      // [B][N][n]
     float *d_X = nullptr;      // [B][N][n]
     float *d_vexp = nullptr;   // [B][N][n] explicit v (prox-pass entry point)
+    float *d_theta2 = nullptr; // [B][N][n] sum_{k in J_g} A_ks^2 Lambda_k
     double *d_wbar = nullptr;  // [B][n]
     double *d_part = nullptr;  // [B][nblk_mann][2] residual partials
     double *d_resid = nullptr; // [B][3]: dw2, ww2, r
-    int *d_counter = nullptr;  // work counters [B][N]
     int *d_status = nullptr;   // device status word
     std::vector<int32_t> sv_order;   // super-voxel visiting order of a forward pass
     int32_t *d_sv_order = nullptr;
@@ -552,591 +533,6 @@ struct mace_state {
     int sweep_warps = 0, sweep_wpb = 0, concurrency = 0, chains = 1;
     size_t sweep_smem = 0, warp_smem = 0;
 };
-
-struct SweepArgs {
-    const uint8_t *cols;
-    const int64_t *sv_base;
-    const uint32_t *col_off;
-    const uint32_t *band;
-    const int *view_off;
-    const int32_t *sv_order;
-    float2 *eL;
-    float *X;
-    const float *w;
-    const double *wbar;
-    const float *vexp;
-    int *counter;
-    int *status;
-    int B, N, nsv, nsvx, S, nx, ny, D;
-    int64_t ne;
-    int nwarps;                 // warps with work (the last block may have idle ones)
-    int backward;
-    int max_band, col_stride, max_views;   // per-warp shared-memory layout (S is a template parameter)
-    float inv_s2, pscale;
-    int prior;                  // 0 quadratic, 1 Q-GGMRF
-    float inv_sx2, inv_Tsx, qexp, qq;   // prior constants
-    float b_edge, b_diag;       // 8-neighbourhood weights (face, diagonal)
-    int nb26;                   // 1: the batch is the z-stack of one volume, 26-neighbourhood prior
-    float b26[3];               // 26-neighbourhood weights by squared distance 1, 2, 3
-};
-
-// --- PTX helpers -------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// 1D TMA bulk copy global -> shared, completion counted on the mbarrier
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
-{
-    if (A.prior == 0) return A.inv_sx2;
-    float a = __powf(fabsf(d * A.inv_Tsx), A.qexp);
-    float opa = 1.f + a;
-    return (2.f + A.qq * a) * 0.5f * A.inv_sx2 / (opa * opa);
-}
-
-template <typename T> __device__ __forceinline__ float ld_val(const uint8_t *p, int idx);
-template <> __device__ __forceinline__ float ld_val<float>(const uint8_t *p, int idx) { return ((const float *)p)[idx]; }
-template <> __device__ __forceinline__ float ld_val<__nv_bfloat16>(const uint8_t *p, int idx)
-{
-    return __bfloat162float(((const __nv_bfloat16 *)p)[idx]);
-}
-template <> __device__ __forceinline__ float ld_val<__half>(const uint8_t *p, int idx)
-{
-    return __half2float(((const __half *)p)[idx]);
-}
-
-// Per-warp shared-memory layout (bytes, each part 16-aligned).  Shared by
-// the warp's K chains (reconstructions of one batch group that run the same
-// agent over the same super-voxels, so every column is loaded once for all):
-//   ring:   kRing * col_stride            column staging (TMA destination)
-//   bars:   kRing * 8                     mbarriers
-//   bdesc:  2 * max_views * 4             band descriptors (lo | len << 16), current and next super-voxel
-//   boff:   max_views * 2                 band offset of each view (u16)
-//   bview:  max_band * 2                  view of each band entry (u16)
-//   coff:   2 * (S^2 + 1) * 4             column byte offsets, current and next super-voxel
-//   tl:     2 * S^2 * 2                   non-empty pixels in visiting order, current and next
-//   halo:   2 * (S+2)^2 * 4               X tiles of the slices below and above (volumes)
-// and per chain:
-//   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
-//   bsnap:  max_band * 4                  e of the band when the super-voxel began
-//   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
-//   wst:    S^2 * 12                      staged consensus (FP64) and w of the tile
-//   vt:     S^2 * 4                       v tile
-struct WarpSmem {
-    size_t ring, bars, bdesc, boff, bview, coff, tl, halo, chain0, chain_size;
-    size_t beL, bsnap, xt, wst, vt;   // offsets inside a chain block
-    size_t total;
-};
-
-__host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views, int K)
-{
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    const size_t S2 = (size_t)S * S, T2 = (size_t)(S + 2) * (S + 2);
-    WarpSmem L;
-    size_t o = 0;
-    L.ring = o;  o += r16((size_t)kRing * col_stride);
-    L.bars = o;  o += r16(kRing * 8);
-    L.bdesc = o; o += r16((size_t)2 * max_views * 4);
-    L.boff = o;  o += r16((size_t)max_views * 2);
-    L.bview = o; o += r16((size_t)max_band * 2);
-    L.coff = o;  o += r16((size_t)2 * (S2 + 1) * 4);
-    L.tl = o;    o += r16((size_t)2 * S2 * 2);
-    L.halo = o;  o += r16(2 * T2 * 4);
-    L.chain0 = o;
-    size_t c = 0;
-    L.beL = c;   c += r16((size_t)max_band * 8);
-    L.bsnap = c; c += r16((size_t)max_band * 4);
-    L.xt = c;    c += r16(T2 * 4);
-    L.wst = c;   c += r16(S2 * 12);
-    L.vt = c;    c += r16(S2 * 4);
-    L.chain_size = c;
-    L.total = o + (size_t)K * c;
-    return L;
-}
-
-static size_t warp_smem_bytes(int max_band, int col_stride, int S, int max_views, int K)
-{
-    return warp_smem_layout(max_band, col_stride, S, max_views, K).total;
-}
-
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Band bookkeeping shared by the kernels that walk a super-voxel's columns:
-// per view the band descriptor, its offset in the flattened band and, per
-// band entry, its view.  Returns the band size.  Warp-cooperative.  bd may
-// point to global or shared memory; bdesc may alias bd.
-__device__ __forceinline__ int load_band_layout(const uint32_t *bd, int Vg, uint32_t *bdesc,
-                                                uint16_t *boff, uint16_t *bview, int lane)
-{
-    const unsigned FULL = 0xffffffffu;
-    int run = 0;
-    for (int r = 0; r * 32 < Vg; ++r) {
-        const int v = r * 32 + lane;
-        const uint32_t d = v < Vg ? bd[v] : 0u;
-        const int len = (int)(d >> 16);
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (v < Vg) {
-            const int b0 = run + incl - len;
-            boff[v] = (uint16_t)b0;
-            bdesc[v] = d;
-            for (int k = 0; k < len; ++k) bview[b0 + k] = (uint16_t)v;
-        }
-        run += __shfl_sync(FULL, incl, 31);
-    }
-    __syncwarp();
-    return run;
-}
-
-// global index (row of the agent block, [Vg][D]) of band entry f
-__device__ __forceinline__ int64_t band_global(int f, const uint32_t *bdesc, const uint16_t *boff,
-                                               const uint16_t *bview, int D)
-{
-    const int v = bview[f];
-    return (int64_t)v * D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v]);
-}
-
-// One warp runs K chains (reconstructions b0 .. b0+K-1 of one batch group,
-// all on agent g) over a fixed sequence of super-voxels: slots c, c+C, c+2C,
-// ... of the visiting order, where C warps serve the same (group, agent) -- so
-// about C super-voxels of one agent of one reconstruction are in flight at a
-// time.  Inside a super-voxel the pixels are visited in order; each pixel's
-// column (a flat list of (band position, value) pairs, lane k taking entries
-// k, k+32, ...) is streamed once by TMA for all K chains.  The next
-// super-voxel's metadata and first columns are fetched while the current one
-// is processed.  MR > 0: at most 32*MR entries per column, kept in registers
-// between the reduction and the update; MR == 0: any count (K must be 1).
-template <typename T, int MR, int S, int K>
-__global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    constexpr int S2 = S * S, T2 = S + 2;
-    static_assert(MR > 0 || K == 1, "uncached columns support one chain");
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views, K);
-    uint8_t *base = smem + wib * Ly.total;
-    uint8_t *ring = base + Ly.ring;
-    uint64_t *bars = (uint64_t *)(base + Ly.bars);
-    uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
-    uint16_t *boff = (uint16_t *)(base + Ly.boff);
-    uint16_t *bview = (uint16_t *)(base + Ly.bview);
-    uint32_t *scoff2 = (uint32_t *)(base + Ly.coff);
-    uint16_t *tl2 = (uint16_t *)(base + Ly.tl);
-    uint8_t *chains = base + Ly.chain0;
-    float *halo_lo = (float *)(base + Ly.halo);
-    float *halo_hi = halo_lo + T2 * T2;
-
-    if (lane == 0)
-        for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    __syncwarp();
-
-    const unsigned FULL = 0xffffffffu;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t n = (int64_t)A.nx * A.ny;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (gw >= A.nwarps) return;
-    const int G = A.B / K;                      // batch groups
-    const int pair = gw % (G * A.N);            // (group, agent)
-    const int cidx = gw / (G * A.N);            // this warp's place among the C serving the pair
-    const int grp = pair / A.N, g = pair - grp * A.N;
-    const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
-    const int Cw = A.nwarps / (G * A.N);
-    // this lane's prior neighbour: lanes 0..7 the in-plane 8-neighbourhood,
-    // or (volumes) lanes 0..25 the 26-neighbourhood
-    int pdz = 0, pdi, pdj;
-    float pb;
-    if (A.nb26) {
-        const int kk = lane < 13 ? lane : lane + 1;   // skip the centre of the 3x3x3
-        pdz = kk / 9 - 1;
-        pdi = (kk / 3) % 3 - 1;
-        pdj = kk % 3 - 1;
-        const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
-        pb = lane < 26 ? A.pscale * A.b26[d2 - 1] : 0.f;
-    } else {
-        const int kk = lane < 4 ? lane : lane + 1;
-        pdi = kk / 3 - 1;
-        pdj = kk % 3 - 1;
-        pb = lane < 8 ? A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge) : 0.f;
-    }
-    const int nlanes = A.nb26 ? 26 : 8;
-
-    // chain k: reconstruction grp*K + k
-    auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
-    auto Xk = [&](int k) { return A.X + ((int64_t)(grp * K + k) * A.N + g) * n; };
-    auto chain = [&](int k) { return chains + (size_t)k * Ly.chain_size; };
-
-    // --- super-voxel metadata -------------------------------------------
-    auto sv_of = [&](int m) {           // m-th super-voxel of this warp, -1 past the end
-        const int slot = cidx + m * Cw;
-        if (slot >= A.nsv) return -1;
-        return A.sv_order[A.backward ? A.nsv - 1 - slot : slot];
-    };
-    // visiting list of a super-voxel from its column offsets; returns count
-    auto build_list = [&](const uint32_t *sc, uint16_t *tl) {
-        int count = 0;
-        for (int k0 = 0; k0 < S2; k0 += 32) {
-            const int k = k0 + lane;
-            const int t = A.backward ? S2 - 1 - k : k;
-            const bool ne = k < S2 && sc[t + 1] != sc[t];
-            const unsigned m = __ballot_sync(FULL, ne);
-            if (ne) tl[count + __popc(m & lt_mask)] = (uint16_t)t;
-            count += __popc(m);
-        }
-        __syncwarp();
-        return count;
-    };
-    // issue TMA for column q of a super-voxel into ring position idx
-    auto issue = [&](uint32_t idx, const uint8_t *svcols, const uint32_t *sc, const uint16_t *tl, int q) {
-        const int t = tl[q];
-        const uint32_t stg = idx % kRing;
-        const uint32_t bytes = sc[t + 1] - sc[t];
-        mbar_expect_tx(&bars[stg], bytes);
-        tma_load_1d(ring + (size_t)stg * A.col_stride, svcols + sc[t], bytes, &bars[stg]);
-    };
-
-    int sv = sv_of(0);
-    if (sv < 0) return;
-    // first super-voxel: metadata with plain loads
-    {
-        const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv) * (S2 + 1);
-        for (int k = lane; k <= S2; k += 32) scoff2[k] = coff[k];
-        const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
-        for (int v = lane; v < Vg; v += 32) bdesc2[v] = bd[v];
-        __syncwarp();
-    }
-    int count = build_list(scoff2, tl2);
-    const uint8_t *svcols = A.cols + A.sv_base[(int64_t)g * A.nsv + sv];
-    uint32_t issued = 0, seq = 0;     // ring positions issued / consumed (per warp)
-    if (lane == 0)
-        for (int q = 0; q < min(count, kRing); ++q) issue(issued + q, svcols, scoff2, tl2, q);
-    issued += min(count, kRing);
-    int cur = 0;
-    int status_seen = 0;
-
-    for (int m = 0; sv >= 0; ++m) {
-        uint32_t *bdesc = bdesc2 + cur * A.max_views;
-        uint32_t *scoff = scoff2 + cur * (S2 + 1);
-        uint16_t *tl = tl2 + cur * S2;
-        uint32_t *bdesc_n = bdesc2 + (cur ^ 1) * A.max_views;
-        uint32_t *scoff_n = scoff2 + (cur ^ 1) * (S2 + 1);
-        uint16_t *tl_n = tl2 + (cur ^ 1) * S2;
-        const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
-
-        // --- band layout; band, X and consensus tiles of every chain --------
-        const int band_tot = load_band_layout(bdesc, Vg, bdesc, boff, bview, lane);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            float2 *beL = (float2 *)(ch + Ly.beL);
-            float *xt = (float *)(ch + Ly.xt);
-            double *wbs = (double *)(ch + Ly.wst);
-            float *ws = (float *)(ch + Ly.wst + (size_t)S2 * 8);
-            const float2 *eL = eLk(k);
-            for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[band_global(f, bdesc, boff, bview, A.D)]);
-            const float *Xg = Xk(k);
-            for (int q = lane; q < T2 * T2; q += 32) {
-                const int i = si * S + q / T2 - 1, j = sj * S + q % T2 - 1;
-                if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&xt[q], &Xg[(int64_t)i * A.nx + j]);
-                else xt[q] = 0.f;
-            }
-            if (!A.vexp) {
-                const double *wb = A.wbar + (int64_t)(grp * K + k) * n;
-                const float *wk = A.w + ((int64_t)(grp * K + k) * A.N + g) * n;
-                for (int q = lane; q < S2; q += 32) {
-                    const int i = si * S + q / S, j = sj * S + q % S;
-                    if (i < A.ny && j < A.nx) {
-                        cp_async8(&wbs[q], &wb[(int64_t)i * A.nx + j]);
-                        cp_async4(&ws[q], &wk[(int64_t)i * A.nx + j]);
-                    }
-                }
-            }
-        }
-        if (A.nb26) {
-            // X tiles of the neighbouring slices (volumes run one chain per warp)
-            const int z = grp * K;
-            for (int h = 0; h < 2; ++h) {
-                const int zz = z + (h ? 1 : -1);
-                float *ht = h ? halo_hi : halo_lo;
-                const float *Xz = (zz >= 0 && zz < A.B) ? A.X + ((int64_t)zz * A.N + g) * n : nullptr;
-                for (int q = lane; q < T2 * T2; q += 32) {
-                    const int i = si * S + q / T2 - 1, j = sj * S + q % T2 - 1;
-                    if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&ht[q], &Xz[(int64_t)i * A.nx + j]);
-                    else ht[q] = 0.f;
-                }
-            }
-        }
-        cp_async_commit();
-        // next super-voxel: claim its metadata while this one runs
-        const int sv_n = sv_of(m + 1);
-        const uint8_t *svcols_n = nullptr;
-        if (sv_n >= 0) {
-            svcols_n = A.cols + A.sv_base[(int64_t)g * A.nsv + sv_n];
-            const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv_n) * (S2 + 1);
-            for (int k = lane; k <= S2; k += 32) cp_async4(&scoff_n[k], &coff[k]);
-            const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv_n * Vg;
-            for (int v = lane; v < Vg; v += 32) cp_async4(&bdesc_n[v], &bd[v]);
-        }
-        cp_async_commit();
-        if (lane == 0) status_seen = *((volatile int *)A.status);
-        cp_async_wait_all();
-        __syncwarp();
-        status_seen = __shfl_sync(FULL, status_seen, 0);
-        int count_n = 0;
-        if (sv_n >= 0) count_n = build_list(scoff_n, tl_n);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            const float2 *beL = (const float2 *)(ch + Ly.beL);
-            float *bsnap = (float *)(ch + Ly.bsnap);
-            float *vt = (float *)(ch + Ly.vt);
-            const double *wbs = (const double *)(ch + Ly.wst);
-            const float *ws = (const float *)(ch + Ly.wst + (size_t)S2 * 8);
-            for (int f = lane; f < band_tot; f += 32) bsnap[f] = beL[f].x;
-            for (int q = lane; q < S2; q += 32) {
-                const int i = si * S + q / S, j = sj * S + q % S;
-                float vv = 0.f;
-                if (i < A.ny && j < A.nx) {
-                    const int64_t s = (int64_t)i * A.nx + j;
-                    vv = A.vexp ? A.vexp[((int64_t)(grp * K + k) * A.N + g) * n + s]
-                                : (float)(2.0 * wbs[q] - (double)ws[q]);
-                }
-                vt[q] = vv;
-            }
-        }
-        __syncwarp();
-        if (status_seen != 0) {
-            // another warp gave up: drain this warp's copies in flight and stop
-            for (uint32_t q2 = seq; q2 < issued; ++q2) {
-                uint32_t sp2 = 0;
-                while (!mbar_try_wait(&bars[q2 % kRing], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
-            }
-            return;
-        }
-
-        // --- visit the pixels ------------------------------------------------
-        int nq = 0;   // columns of the next super-voxel issued so far
-        for (int q = 0; q < count; ++q) {
-            const int t = tl[q];
-            const int ti = t / S, tj = t % S;
-            const int i = si * S + ti, j = sj * S + tj;
-            const int tc = (ti + 1) * T2 + (tj + 1);
-            // prior through the surrogate weights (lanes 0..7: the 8
-            // neighbours), from the X tile only: overlaps the column's arrival
-            float xs[K], pr1[K], pr2[K], prox[K];
-            const int zc = grp * K;   // slice of chain 0 (volumes)
-            const bool nb_in = lane < nlanes && i + pdi >= 0 && i + pdi < A.ny && j + pdj >= 0 && j + pdj < A.nx &&
-                               (pdz == 0 || (zc + pdz >= 0 && zc + pdz < A.B));
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float *xt = (const float *)(chain(k) + Ly.xt);
-                const float *vt = (const float *)(chain(k) + Ly.vt);
-                xs[k] = xt[tc];
-                pr1[k] = 0.f;
-                pr2[k] = 0.f;
-                if (nb_in) {
-                    const float *nt = pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi);
-                    const float d = xs[k] - nt[tc + pdi * T2 + pdj];
-                    pr2[k] = pb * prior_weight(A, d);
-                    pr1[k] = pr2[k] * d;
-                }
-                prox[k] = (xs[k] - vt[t]) * A.inv_s2;
-            }
-            const uint32_t stg = seq % kRing;
-            const uint32_t parity = (seq / kRing) & 1u;
-            uint32_t spins = 0;
-            while (!mbar_try_wait(&bars[stg], parity)) {
-                if (++spins > kSpinLimit) {
-                    // give up: flag the host, then wait (bounded) for this
-                    // warp's copies still in flight before leaving
-                    if (lane == 0) atomicExch(A.status, kStatusTimeout);
-                    for (uint32_t q2 = seq + 1; q2 < issued; ++q2) {
-                        uint32_t sp2 = 0;
-                        while (!mbar_try_wait(&bars[q2 % kRing], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
-                    }
-                    return;
-                }
-            }
-            const uint8_t *col = ring + (size_t)stg * A.col_stride;
-            const uint16_t *cidx = (const uint16_t *)col;
-            const int nnz = cidx[0];
-            const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
-
-            // data term of each chain: p1 = -sum A Lambda e, p2 = sum A^2 Lambda
-            float p1[K], p2[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) { p1[k] = pr1[k]; p2[k] = pr2[k]; }
-            constexpr int RC = MR > 0 ? MR : 1;
-            float ca[RC], ce[K][RC];
-            int cb[RC];
-            if (MR > 0) {
-#pragma unroll
-                for (int r = 0; r < RC; ++r) {
-                    const int e = r * 32 + lane;
-                    ca[r] = 0.f;
-                    cb[r] = 0;
-                    if (e < nnz) {
-                        cb[r] = cidx[1 + e];
-                        ca[r] = ld_val<T>(cval, e);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < RC; ++r) {
-                    if (r * 32 + lane < nnz) {
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const float2 el = ((const float2 *)(chain(k) + Ly.beL))[cb[r]];
-                            ce[k][r] = el.x;
-                            p1[k] = fmaf(-ca[r] * el.y, el.x, p1[k]);
-                            p2[k] = fmaf(ca[r] * ca[r], el.y, p2[k]);
-                        }
-                    }
-                }
-            } else {
-                const float2 *beL = (const float2 *)(chain(0) + Ly.beL);
-                for (int e = lane; e < nnz; e += 32) {
-                    const float a = ld_val<T>(cval, e);
-                    const float2 el = beL[cidx[1 + e]];
-                    p1[0] = fmaf(-a * el.y, el.x, p1[0]);
-                    p2[0] = fmaf(a * a, el.y, p2[0]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    p1[k] += __shfl_xor_sync(FULL, p1[k], o);
-                    p2[k] += __shfl_xor_sync(FULL, p2[k], o);
-                }
-            }
-            // the step's sign and zero set come from the numerator alone, so a
-            // fast division leaves the fixed point unchanged
-            float alpha[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) alpha[k] = -__fdividef(p1[k] + prox[k], p2[k] + A.inv_s2);
-            // update e: the entries of one column are distinct band positions
-            if (MR > 0) {
-#pragma unroll
-                for (int r = 0; r < RC; ++r)
-                    if (r * 32 + lane < nnz) {
-#pragma unroll
-                        for (int k = 0; k < K; ++k)
-                            ((float2 *)(chain(k) + Ly.beL))[cb[r]].x = fmaf(-ca[r], alpha[k], ce[k][r]);
-                    }
-            } else {
-                float2 *beL = (float2 *)(chain(0) + Ly.beL);
-                for (int e = lane; e < nnz; e += 32) {
-                    const int bb = cidx[1 + e];
-                    beL[bb].x = fmaf(-ld_val<T>(cval, e), alpha[0], beL[bb].x);
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) ((float *)(chain(k) + Ly.xt))[tc] = xs[k] + alpha[k];
-            }
-            ++seq;
-            __syncwarp();
-            // refill the ring slot just freed (the next column of this
-            // super-voxel, else of the next one).  Every read of the slot has
-            // completed: its values fed the reduction all lanes joined before
-            // the __syncwarp above, so the TMA write cannot overtake them.
-            if (q + kRing < count) {
-                if (lane == 0) issue(issued, svcols, scoff, tl, q + kRing);
-                ++issued;
-            } else if (nq < count_n) {
-                if (lane == 0) issue(issued, svcols_n, scoff_n, tl_n, nq);
-                ++issued;
-                ++nq;
-            }
-        }
-
-        // --- write back: X tiles and the change of e --------------------------
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            const float *xt = (const float *)(ch + Ly.xt);
-            float *Xg = Xk(k);
-            for (int q = lane; q < S2; q += 32) {
-                const int i = si * S + q / S, j = sj * S + q % S;
-                if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(q / S + 1) * T2 + (q % S + 1)];
-            }
-            const float2 *beL = (const float2 *)(ch + Ly.beL);
-            const float *bsnap = (const float *)(ch + Ly.bsnap);
-            float2 *eL = eLk(k);
-            for (int f = lane; f < band_tot; f += 32) {
-                const float de = beL[f].x - bsnap[f];
-                if (de != 0.f) atomicAdd(&eL[band_global(f, bdesc, boff, bview, A.D)].x, de);
-            }
-        }
-        __syncwarp();
-        // the next super-voxel's first columns: those not issued yet
-        if (sv_n >= 0) {
-            while (nq < min(count_n, kRing) && (int)(issued - seq) < kRing) {
-                if (lane == 0) issue(issued, svcols_n, scoff_n, tl_n, nq);
-                ++issued;
-                ++nq;
-            }
-        }
-        // hand the staged next-super-voxel state over
-        sv = sv_n;
-        svcols = svcols_n;
-        count = count_n;
-        cur ^= 1;
-        // now exactly min(count, kRing) columns of the new super-voxel are in
-        // flight, as the pixel loop's refill (column q + kRing) assumes
-    }
-}
 
 // --- consensus (G), Mann, residual ------------------------------------------
 __global__ void consensus_kernel(const float *__restrict__ w, int B, int N, int64_t n, double *__restrict__ wbar,
@@ -1222,15 +618,6 @@ __global__ void residual_kernel(const double *__restrict__ part, int nblk, int B
 }
 
 // --- error sinogram: e = y - A X ---------------------------------------------
-// Per-warp shared memory of the kernels that walk columns outside the sweep:
-// band descriptors, offsets, entry views and one float per band entry.
-__host__ __device__ inline size_t aux_warp_bytes(int max_band, int max_views)
-{
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    return r16((size_t)max_views * 4) + r16((size_t)max_views * 2) + r16((size_t)max_band * 2) +
-           r16((size_t)max_band * 4);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                                       const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
@@ -1271,9 +658,9 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
         const uint8_t *col = svcols + coff[t];
         const uint16_t *cidx = (const uint16_t *)col;
         const int nnz = cidx[0];
-        const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
+        const uint8_t *cval = col + col_idx_bytes(nnz);
         for (int k = lane; k < nnz; k += 32) {
-            const int bb = cidx[1 + k];
+            const int bb = cidx[2 + k];
             acc[bb] = fmaf(-ld_val<T>(cval, k), xs, acc[bb]);
         }
         __syncwarp();
@@ -1323,21 +710,17 @@ __global__ void check_weights_kernel(const float *__restrict__ y, const float *_
     if (!isfinite(a) || !isfinite(b) || b < 0.f) atomicOr(bad, 1);
 }
 
-__device__ __forceinline__ float ld_any(const uint8_t *p, int idx, int dtype)
+__global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
+                              const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
+                              const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
+                              int nsvx, int S, int nx, int ny, int D, int64_t ne, int dtype, int max_band,
+                              int max_views, float *__restrict__ theta2, double *__restrict__ total)
 {
-    if (dtype == MACE_F32) return ld_val<float>(p, idx);
-    if (dtype == MACE_BF16) return ld_val<__nv_bfloat16>(p, idx);
-    return ld_val<__half>(p, idx);
-}
-
-__global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
-                                  const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
-                                  const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
-                                  int S, int D, int64_t ne, int dtype, int max_band, int max_views,
-                                  double *__restrict__ out)
-{
-    // sum over reconstructions, agents and voxels of sum_{k in J_i} A^2 Lambda
-    // (FP64), for the normalised sigma; one warp per (b, agent, super-voxel)
+    // theta2[b][g][s] = sum_{k in J_g} A_ks^2 Lambda_k (the data term of the
+    // coordinate curvature in Algorithm 2, constant over the iterations),
+    // accumulated in FP64 and stored in FP32; zero for pixels without a
+    // column.  total += the FP64 sum over everything (for the normalised
+    // sigma).  One warp per (b, agent, super-voxel).
     extern __shared__ __align__(16) uint8_t smem[];
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
@@ -1349,25 +732,33 @@ __global__ void theta2_sum_kernel(const uint8_t *__restrict__ cols, const int64_
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
     const int b = pair / N, g = pair - b * N;
+    const int si = sv / nsvx, sj = sv % nsvx;
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint32_t *coff = col_off + gsv * (S2 + 1);
     const float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
+    float *t2g = theta2 + (int64_t)pair * nx * ny;
     load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
-    double acc = 0.0;
+    double sum = 0.0;
     for (int t = 0; t < S2; ++t) {
-        if (coff[t + 1] == coff[t]) continue;
-        const uint8_t *col = cols + sv_base[gsv] + coff[t];
-        const uint16_t *cidx = (const uint16_t *)col;
-        const int nnz = cidx[0];
-        const uint8_t *cval = col + ((2 + 2 * nnz + 15) & ~15);
-        for (int k = lane; k < nnz; k += 32) {
-            const float a = ld_any(cval, k, dtype);
-            acc += (double)a * a * eLg[band_global(cidx[1 + k], bdesc, boff, bview, D)].y;
+        const int i = si * S + t / S, j = sj * S + t % S;
+        if (i >= ny || j >= nx) continue;
+        double acc = 0.0;
+        if (coff[t + 1] != coff[t]) {
+            const uint8_t *col = cols + sv_base[gsv] + coff[t];
+            const uint16_t *cidx = (const uint16_t *)col;
+            const int nnz = cidx[0];
+            const uint8_t *cval = col + col_idx_bytes(nnz);
+            for (int k = lane; k < nnz; k += 32) {
+                const float a = ld_any(cval, k, dtype);
+                acc += (double)a * a * eLg[band_global(cidx[2 + k], bdesc, boff, bview, D)].y;
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         }
+        if (lane == 0) t2g[(int64_t)i * nx + j] = (float)acc;
+        sum += acc;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomicAdd(out, acc);
+    if (lane == 0) atomicAdd(total, sum);
 }
 
 // Bounded-wait self test: one warp arms an mbarrier for bytes that are never
@@ -1422,36 +813,14 @@ static int launch_forward(mace_state *st)
     return MACE_OK;
 }
 
-typedef void (*sweep_fn)(SweepArgs);
-
-template <typename T, int S>
-static sweep_fn sweep_kernel_ptr_s(const mace_sysmatrix *M, int K)
-{
-    // entries per column in rounds of 32 lanes
-    const int rounds = (M->max_nnz + 31) / 32;
-    if (rounds <= 3) return K == 4 ? icd_sweep_kernel<T, 3, S, 4> : K == 2 ? icd_sweep_kernel<T, 3, S, 2> : icd_sweep_kernel<T, 3, S, 1>;
-    if (rounds <= 4) return K == 4 ? icd_sweep_kernel<T, 4, S, 4> : K == 2 ? icd_sweep_kernel<T, 4, S, 2> : icd_sweep_kernel<T, 4, S, 1>;
-    if (rounds <= 5) return K == 4 ? icd_sweep_kernel<T, 5, S, 4> : K == 2 ? icd_sweep_kernel<T, 5, S, 2> : icd_sweep_kernel<T, 5, S, 1>;
-    return K == 1 ? icd_sweep_kernel<T, 0, S, 1> : nullptr;
-}
-
-template <typename T>
-static sweep_fn sweep_kernel_ptr_t(const mace_sysmatrix *M, int K)
-{
-    switch (M->S) {
-    case 4: return sweep_kernel_ptr_s<T, 4>(M, K);
-    case 8: return sweep_kernel_ptr_s<T, 8>(M, K);
-    case 16: return K == 1 ? sweep_kernel_ptr_s<T, 16>(M, 1) : nullptr;
-    default: return nullptr;
-    }
-}
-
 static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K)
 {
+    // entries per column in pairs of 32 lanes
+    const int pair_rounds = (M->max_nnz + 63) / 64;
     switch (M->dtype) {
-    case MACE_F32: return sweep_kernel_ptr_t<float>(M, K);
-    case MACE_BF16: return sweep_kernel_ptr_t<__nv_bfloat16>(M, K);
-    default: return sweep_kernel_ptr_t<__half>(M, K);
+    case MACE_F32: return mace_sweep_kernel_f32(pair_rounds, M->S, K);
+    case MACE_BF16: return mace_sweep_kernel_bf16(pair_rounds, M->S, K);
+    default: return mace_sweep_kernel_f16(pair_rounds, M->S, K);
     }
 }
 
@@ -1470,13 +839,12 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.w = st->d_w;
     A.wbar = st->d_wbar;
     A.vexp = vexp;
-    A.counter = st->d_counter;
+    A.theta2 = st->d_theta2;
     A.status = st->d_status;
     A.B = st->B;
     A.N = M->N;
     A.nsv = M->nsv;
     A.nsvx = M->nsvx;
-    A.S = M->S;
     A.nx = M->geo.nx;
     A.ny = M->geo.ny;
     A.D = M->geo.D;
@@ -1504,7 +872,9 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
-    sweep_kernel_ptr(M, st->chains)<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    sweep_fn fn = sweep_kernel_ptr(M, st->chains);
+    if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix");
+    fn<<<grid, block, st->sweep_smem, st->stream>>>(A);
     if (rec) {
         CUDA_TRY(cudaEventRecord(st->ev[st->ev_used + 1], st->stream));
         st->ev_used += 2;
@@ -1525,7 +895,7 @@ static int configure_sweep(mace_state *st)
     // chains per warp: reconstructions of the batch that share each column
     // load (a divisor of the batch; 1 when the columns are not cached)
     int K = 1;
-    if ((M->max_nnz + 31) / 32 <= 5 && M->S != 16 && st->P.neighbourhood != 26) {
+    if ((M->max_nnz + 63) / 64 <= 3 && M->S != 16 && st->P.neighbourhood != 26) {
         // one chain unless asked: sharing the column between chains saves
         // column traffic but costs registers and shared memory, and measured
         // slower on the 512^2 workload
@@ -1535,7 +905,8 @@ static int configure_sweep(mace_state *st)
     }
     sweep_fn fn = nullptr;
     for (;;) {
-        st->warp_smem = warp_smem_bytes(M->max_band, col_stride, M->S, M->max_views, K);
+        st->warp_smem = warp_smem_layout(M->max_band, col_stride, M->S, M->max_views, K,
+                                         st->P.neighbourhood == 26).total;
         fn = sweep_kernel_ptr(M, K);
         if (fn && st->warp_smem <= (size_t)max_smem) break;
         if (K == 1) break;
@@ -1629,7 +1000,7 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_wbar);
     cudaFree(st->d_part);
     cudaFree(st->d_resid);
-    cudaFree(st->d_counter);
+    cudaFree(st->d_theta2);
     cudaFree(st->d_status);
     cudaFree(st->d_sv_order);
     for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
@@ -1688,9 +1059,9 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
         cudaMalloc(&st->d_y, sizeof(float) * m) != cudaSuccess ||
         cudaMalloc(&st->d_w, sizeof(float) * NN) != cudaSuccess ||
         cudaMalloc(&st->d_X, sizeof(float) * NN) != cudaSuccess ||
+        cudaMalloc(&st->d_theta2, sizeof(float) * NN) != cudaSuccess ||
         cudaMalloc(&st->d_wbar, sizeof(double) * batch * st->n) != cudaSuccess ||
         cudaMalloc(&st->d_resid, sizeof(double) * 3 * batch) != cudaSuccess ||
-        cudaMalloc(&st->d_counter, sizeof(int) * batch * M->N) != cudaSuccess ||
         cudaMalloc(&st->d_status, sizeof(int)) != cudaSuccess)
         return bail(MACE_ENOMEM, "cudaMalloc failed for the reconstruction state");
     int dev = 0, nsm = 0;
@@ -1744,29 +1115,34 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     rc = set_X_from_w(st);
     if (rc == MACE_OK) rc = launch_forward(st);
     if (rc) { mace_free_state(st); return rc; }
-    // sigma in image units
-    if (params->sigma_mode == 1) {
+    // theta2 per (b, agent, pixel) and its mean; sigma in image units
+    {
         double *d_t2 = nullptr;
         double h_t2 = 0.0;
         ce = cudaMalloc(&d_t2, sizeof(double));
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_t2, 0, sizeof(double), s);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_theta2, 0, sizeof(float) * NN, s);
         if (ce == cudaSuccess) {
             int64_t items = (int64_t)batch * M->N * M->nsv;
             const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
-            cudaFuncSetAttribute(theta2_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            theta2_sum_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, sm, s>>>(
-                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->S,
-                M->geo.D, st->ne, (int)M->dtype, M->max_band, M->max_views, d_t2);
-            ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaFuncSetAttribute(theta2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            theta2_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, sm, s>>>(
+                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, batch, M->N, M->nsv,
+                M->nsvx, M->S, M->geo.nx, M->geo.ny, M->geo.D, st->ne, (int)M->dtype, M->max_band, M->max_views,
+                st->d_theta2, d_t2);
+            ce = cudaGetLastError();
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         cudaFree(d_t2);
         if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("theta2: ") + cudaGetErrorString(ce));
-        double mean_t2 = h_t2 / ((double)batch * M->N * (double)st->n);
-        if (!(mean_t2 > 0)) return bail(MACE_EINVAL, "all weights are zero");
-        st->sigma_abs = params->sigma / std::sqrt(mean_t2);
-    } else {
-        st->sigma_abs = params->sigma;
+        if (params->sigma_mode == 1) {
+            double mean_t2 = h_t2 / ((double)batch * M->N * (double)st->n);
+            if (!(mean_t2 > 0)) return bail(MACE_EINVAL, "all weights are zero");
+            st->sigma_abs = params->sigma / std::sqrt(mean_t2);
+        } else {
+            st->sigma_abs = params->sigma;
+        }
     }
     rc = configure_sweep(st);
     if (rc) { mace_free_state(st); return rc; }

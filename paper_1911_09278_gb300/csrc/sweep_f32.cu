@@ -1,0 +1,5 @@
+// ICD sweep kernels with float stored matrix values (one translation unit
+// per value type, so the library's device code compiles in parallel).
+#include "sweep.cuh"
+
+sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K) { return sweep_lookup<float>(pair_rounds, S, K); }

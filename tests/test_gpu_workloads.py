@@ -43,40 +43,45 @@ def test_bounded_wait_reports_timeout(gpu_lib):
 
 def test_full_size_512_parity(gpu_lib):
     """The 512^2 / 720-view / 725-channel / 16-agent Q-GGMRF workload at full
-    size, in the benchmark's launch configuration: the converged image matches
-    the oracle's reference MAP image (tests/golden, written by the oracle)
-    within relative RMSE 1e-4, and the oracle's KKT residual of the GPU image
-    is small."""
+    size, in the benchmark's launch configuration (its batch of two scans,
+    concurrency, sigma, tolerance): the first scan's image matches the
+    oracle's reference MAP image of the same scan (tests/golden, written by
+    the oracle) within relative RMSE 1e-4, the oracle's KKT residual of both
+    images is small, and every agent state equals the consensus."""
+    import types
+    import bench
     mace = gpu_lib
-    cfg = synth.CONFIGS["cfg2"]
-    c = synth.make_case(**cfg)
-    y, lam = c["y"][0], c["lam"][0]
-    sx = synth.prior_sigma_x(lam, 720, frac=1.0)
-    sm = mace.mace_build_sysmatrix(512, 512, 720, 725, 16, sv_size=8)
-    prm = mace.make_params(prior="qggmrf", sigma_x=sx, tol=1e-7, max_iter=4000, **PROD)
-    st = mace.mace_init(sm, y, lam, prm)
+    d = bench.DEFAULTS
+    args = types.SimpleNamespace(**d)
+    y, lam = bench.make_inputs(d["batch"], 0)
+    sx = synth.prior_sigma_x(lam[0], 720, frac=1.0)
+    sm = mace.mace_build_sysmatrix(512, 512, 720, 725, 16, sv_size=d["sv"], dtype=d["dtype"])
+    st = mace.mace_init(sm, y, lam, bench.solver_params(mace, sx, args), batch=d["batch"])
     x, iters, r, conv = st.reconstruct()
     w, X = st.get_state()
     st.close()
-    print("512^2: iters=%d residual=%.2e" % (iters, r))
-    P = oracle.Problem(512, 512, 720, 725, y, lam, n_agents=16, prior="qggmrf", sigma_x=sx)
-    g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
-    kkt = np.linalg.norm(P.gradient(x.ravel().astype(np.float64))) / g0
-    print("512^2: KKT %.2e" % kkt)
-    assert kkt < 1e-5
-    # equilibrium: every agent state equals the consensus (Theorem 1 proof)
-    wbar = w.astype(np.float64).mean(0)
-    for g in range(16):
-        assert nrmse(X[g], wbar) < 1e-3
+    print("512^2 batch %d: iters=%d residual=%.2e converged=%s" % (d["batch"], iters, r, conv))
+    assert conv
+    x = x.reshape(d["batch"], 512, 512)
+    w = w.reshape(d["batch"], 16, 512 * 512)
+    X = X.reshape(d["batch"], 16, 512 * 512)
+    for b in range(d["batch"]):
+        # the batch shares one prior (sigma_x of the first scan), as solved
+        P = oracle.Problem(512, 512, 720, 725, y[b], lam[b], n_agents=16, prior="qggmrf", sigma_x=sx)
+        g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
+        kkt = np.linalg.norm(P.gradient(x[b].ravel().astype(np.float64))) / g0
+        print("512^2 scan %d: KKT %.2e" % (b, kkt))
+        assert kkt < 1e-5
+        # equilibrium: every agent state equals the consensus (Theorem 1 proof)
+        wbar = w[b].astype(np.float64).mean(0)
+        for g in range(16):
+            assert nrmse(X[b, g], wbar) < 1e-3
     ref = os.path.join(GOLDEN, "cfg2_reference.npz")
-    if os.path.exists(ref):
-        d = np.load(ref)
-        if str(d["digest"]) == _digest(y, lam):
-            err = nrmse(x, d["x"])
-            print("512^2: NRMSE vs oracle %.2e (oracle KKT %.1e)" % (err, float(d["kkt"])))
-            assert err < 1e-4
-        else:
-            print("512^2: inputs differ from the stored reference's; NRMSE check skipped")
+    dref = np.load(ref)
+    assert str(dref["digest"]) == _digest(y[0], lam[0]), "stored oracle image is of other inputs"
+    err = nrmse(x[0], dref["x"].reshape(512, 512))
+    print("512^2: NRMSE vs oracle %.2e (oracle KKT %.1e, %d iterations)" % (err, float(dref["kkt"]), int(dref["iters"])))
+    assert err < 1e-4
 
 
 @pytest.mark.parametrize("batch,chains", [(3, 0), (4, 4), (4, 2)])
