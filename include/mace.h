@@ -99,7 +99,11 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   max_iter, tol: mace_reconstruct stops when the relative Mann residual
  *   ||w^(k+1) - w^(k)|| / ||w^(k+1)|| (FP64) falls below tol.
  *   concurrency: super-voxels of one agent updated at the same time (0 =
- *   every warp the GPU holds; 1 = one at a time, the serial ICD order).
+ *   every warp the GPU holds; 1 = one at a time, the serial ICD order;
+ *   -1 = one per row of super-voxels, so with sv_order 0 each warp sweeps
+ *   one row and the rows advance side by side -- on the 512^2 workload
+ *   this converges in the fewest iterations of the settings measured).
+ *   Always capped by the warps the GPU holds.
  *   sv_order: 0 visits super-voxels in raster order cut into `concurrency`
  *   bands that run side by side (plain raster when concurrency is 1);
  *   1 a stride permutation spreading consecutive super-voxels apart.

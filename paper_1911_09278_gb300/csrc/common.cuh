@@ -11,7 +11,12 @@
 #include "../../include/mace.h"
 
 static constexpr int kMaxViews = 4096;     // per geometry
-static constexpr int kRing = 8;            // column ring stages per warp (a power of two)
+// Column ring stages per warp (a power of two).  Four cover the copy latency
+// at the sweep's pixel rate and leave shared memory for more warps per SM.
+#ifndef MACE_RING
+#define MACE_RING 4
+#endif
+static constexpr int kRing = MACE_RING;
 static constexpr uint32_t kSpinLimit = 1u << 26;  // bounded device waits
 static constexpr int kStatusTimeout = 1;
 

@@ -813,14 +813,14 @@ static int launch_forward(mace_state *st)
     return MACE_OK;
 }
 
-static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K)
+static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26)
 {
     // entries per column in pairs of 32 lanes
     const int pair_rounds = (M->max_nnz + 63) / 64;
     switch (M->dtype) {
-    case MACE_F32: return mace_sweep_kernel_f32(pair_rounds, M->S, K);
-    case MACE_BF16: return mace_sweep_kernel_bf16(pair_rounds, M->S, K);
-    default: return mace_sweep_kernel_f16(pair_rounds, M->S, K);
+    case MACE_F32: return mace_sweep_kernel_f32(pair_rounds, M->S, K, nb26);
+    case MACE_BF16: return mace_sweep_kernel_bf16(pair_rounds, M->S, K, nb26);
+    default: return mace_sweep_kernel_f16(pair_rounds, M->S, K, nb26);
     }
 }
 
@@ -859,7 +859,7 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.inv_sx2 = (float)(1.0 / (st->P.sigma_x * st->P.sigma_x));
     A.inv_Tsx = (float)(1.0 / (st->P.T * st->P.sigma_x));
     A.qexp = (float)(st->P.p - st->P.q);
-    A.qq = (float)st->P.q;
+    A.half_q_inv_sx2 = (float)(0.5 * st->P.q / (st->P.sigma_x * st->P.sigma_x));
     double bsum = 4.0 + 4.0 / std::sqrt(2.0);
     A.b_edge = (float)(1.0 / bsum);
     A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
@@ -872,7 +872,7 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
-    sweep_fn fn = sweep_kernel_ptr(M, st->chains);
+    sweep_fn fn = sweep_kernel_ptr(M, st->chains, st->P.neighbourhood == 26);
     if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix");
     fn<<<grid, block, st->sweep_smem, st->stream>>>(A);
     if (rec) {
@@ -907,7 +907,7 @@ static int configure_sweep(mace_state *st)
     for (;;) {
         st->warp_smem = warp_smem_layout(M->max_band, col_stride, M->S, M->max_views, K,
                                          st->P.neighbourhood == 26).total;
-        fn = sweep_kernel_ptr(M, K);
+        fn = sweep_kernel_ptr(M, K, st->P.neighbourhood == 26);
         if (fn && st->warp_smem <= (size_t)max_smem) break;
         if (K == 1) break;
         K /= 2;
@@ -933,6 +933,7 @@ static int configure_sweep(mace_state *st)
     int64_t C = capacity / pairs;
     if (C < 1) C = 1;
     if (st->P.concurrency > 0) C = std::min<int64_t>(C, st->P.concurrency);
+    if (st->P.concurrency == -1) C = std::min<int64_t>(C, M->nsvy);   // one super-voxel row per warp
     C = std::min<int64_t>(C, M->nsv);
     int64_t warps = C * pairs;
     if (warps > capacity) return fail(MACE_EINVAL, "more (reconstruction, agent) pairs than resident warps; lower the batch");
@@ -982,7 +983,7 @@ static int check_params(const mace_params *P)
     if (P->recompute_every < 0) return fail(MACE_EINVAL, "recompute_every must be >= 0");
     if (P->max_iter < 0) return fail(MACE_EINVAL, "max_iter must be >= 0");
     if (!(P->tol >= 0)) return fail(MACE_EINVAL, "tol must be >= 0");
-    if (P->concurrency < 0) return fail(MACE_EINVAL, "concurrency must be >= 0");
+    if (P->concurrency < -1) return fail(MACE_EINVAL, "concurrency must be >= -1");
     if (P->sv_order != 0 && P->sv_order != 1) return fail(MACE_EINVAL, "sv_order must be 0 or 1");
     if (P->chains != 0 && P->chains != 1 && P->chains != 2 && P->chains != 4)
         return fail(MACE_EINVAL, "chains must be 0, 1, 2 or 4");

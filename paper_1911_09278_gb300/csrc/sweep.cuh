@@ -27,7 +27,7 @@ struct SweepArgs {
     int max_band, col_stride, max_views;   // per-warp shared-memory layout (S is a template parameter)
     float inv_s2, pscale;
     int prior;                  // 0 quadratic, 1 Q-GGMRF
-    float inv_sx2, inv_Tsx, qexp, qq;   // prior constants
+    float inv_sx2, inv_Tsx, qexp, half_q_inv_sx2;   // prior constants
     float b_edge, b_diag;       // 8-neighbourhood weights (face, diagonal)
     int nb26;                   // 1: the batch is the z-stack of one volume, 26-neighbourhood prior
     float b26[3];               // 26-neighbourhood weights by squared distance 1, 2, 3
@@ -43,18 +43,18 @@ typedef void (*sweep_fn)(SweepArgs);
 //   bdesc:  2 * max_views * 4             band descriptors (lo | len << 16), current and next super-voxel
 //   boff:   max_views * 2                 band offset of each view (u16)
 //   bview:  max_band * 2                  view of each band entry (u16)
-//   coff:   2 * (S^2 + 1) * 4             column byte offsets, current and next super-voxel
-//   tl:     2 * S^2 * 2                   non-empty pixels in visiting order, current and next
+//   coff:   (S^2 + 1) * 4                 column byte offsets of the next super-voxel (staging)
+//   pl:     2 * S^2 * 4                   per visited pixel: t | tile index << 8 | neighbour mask << 17
+//   cl:     2 * S^2 * 8                   per visited pixel: (column byte offset, bytes)
 //   halo:   2 * (S+2)^2 * 4               X tiles of the slices below and above (volumes only)
 // and per chain:
 //   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
 //   bsnap:  max_band * 4                  e of the band when the super-voxel began
 //   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
-//   vt:     S^2 * 4                       v tile
-//   t2t:    S^2 * 4                       theta2 tile (data term of the coordinate curvature)
+//   vt2:    S^2 * 8                       (v, theta2) per pixel of the tile
 struct WarpSmem {
-    size_t ring, bars, bdesc, boff, bview, coff, tl, halo, chain0, chain_size;
-    size_t beL, bsnap, xt, vt, t2t;
+    size_t ring, bars, bdesc, boff, bview, coff, pl, cl, halo, chain0, chain_size;
+    size_t beL, bsnap, xt, vt2;
     size_t total;
 };
 
@@ -63,6 +63,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_strid
 {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t S2 = (size_t)S * S, TA = (size_t)(S + 2) * (S + 2);
+    if (max_band < 1) max_band = 1;   // the gathers may read band entry 0
     WarpSmem L;
     size_t o = 0;
     L.ring = o;  o += r16((size_t)kRing * col_stride);
@@ -70,31 +71,53 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_strid
     L.bdesc = o; o += r16((size_t)2 * max_views * 4);
     L.boff = o;  o += r16((size_t)max_views * 2);
     L.bview = o; o += r16((size_t)max_band * 2);
-    L.coff = o;  o += r16((size_t)2 * (S2 + 1) * 4);
-    L.tl = o;    o += r16((size_t)2 * S2 * 2);
+    L.coff = o;  o += r16((S2 + 1) * 4);
+    L.pl = o;    o += r16(2 * S2 * 4);
+    L.cl = o;    o += r16(2 * S2 * 8);
     L.halo = o;  o += halo ? r16(2 * TA * 4) : 0;
     L.chain0 = o;
     size_t c = 0;
     L.beL = c;   c += r16((size_t)max_band * 8);
     L.bsnap = c; c += r16((size_t)max_band * 4);
     L.xt = c;    c += r16(TA * 4);
-    L.vt = c;    c += r16(S2 * 4);
-    L.t2t = c;   c += r16(S2 * 4);
+    L.vt2 = c;   c += r16(S2 * 8);
     L.chain_size = c;
     L.total = o + (size_t)K * c;
     return L;
 }
 
+// Approximate reciprocal, base-2 logarithm and exponential (single PTX
+// instructions, flush-to-zero).  They only enter step sizes and the prior's
+// surrogate weight; their relative error (a few ulp) moves the fixed point by
+// an amount of the order of FP32 rounding.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Surrogate weight rho'(D)/D of the prior potential (quadratic: 1/sigma_x^2;
-// Q-GGMRF with p = 2: (2 + q a) / (2 sigma_x^2 (1 + a)^2), a = |D/(T sigma_x)|^(p-q)).
-// It scales the prior's gradient, so its rounding moves the fixed point by
-// a relative amount of the order of FP32 rounding only.
+// Q-GGMRF with p = 2: (2 + q a) / (2 sigma_x^2 (1 + a)^2), a = |D/(T sigma_x)|^(p-q),
+// the power taken as 2^((p-q) log2 |D/(T sigma_x)|); a = 0 at D = 0).
 __device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
 {
     if (A.prior == 0) return A.inv_sx2;
-    const float a = __powf(fabsf(d * A.inv_Tsx), A.qexp);
-    const float opa = 1.f + a;
-    return __fdividef((2.f + A.qq * a) * 0.5f * A.inv_sx2, opa * opa);
+    const float a = ex2_approx(A.qexp * lg2_approx(fabsf(d * A.inv_Tsx)));
+    const float r = rcp_approx(1.f + a);
+    return fmaf(A.half_q_inv_sx2, a, A.inv_sx2) * r * r;
 }
 
 // One warp runs K chains (reconstructions b0 .. b0+K-1 of one batch group,
@@ -104,28 +127,38 @@ __device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
 // time.  Inside a super-voxel the pixels are visited in order; each pixel's
 // column (a flat list of (band position, value) pairs, lane k taking the
 // pairs k, k+32, ...) is streamed once by TMA for all K chains.  The next
-// super-voxel's metadata and first columns are fetched while the current one
-// is processed.  PR > 0: at most 64*PR entries per column, kept in registers
-// between the reduction and the update, and the ring slot is refilled once
-// they have been consumed; PR == 0: any count (K must be 1).
-template <typename T, int PR, int S, int K>
-__global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
+// super-voxel's metadata, visiting list and first columns are prepared while
+// the current one is processed.  PR > 0: at most 64*PR entries per column,
+// kept in registers between the reduction and the update, and the ring slot
+// is refilled once they have been consumed; PR == 0: any count (K must be 1).
+// NB26: the batch is the z-stack of one volume, 26-neighbourhood prior (K = 1).
+// Register cap of the one-chain sweep kernel: residency is limited by
+// registers and shared memory together, and at 96 registers (21 warps per SM)
+// the one-chain kernels do not spill; multi-chain kernels keep their registers.
+#ifndef MACE_SWEEP_MAXNREG
+#define MACE_SWEEP_MAXNREG 96
+#endif
+
+template <typename T, int PR, int S, int K, bool NB26>
+__global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int S2 = S * S, TS = S + 2, TA = TS * TS;
     static_assert(PR > 0 || K == 1, "uncached columns support one chain");
+    static_assert(!NB26 || K == 1, "volumes run one chain per warp");
     static_assert((kRing & (kRing - 1)) == 0, "ring size is a power of two");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views, K, A.nb26);
+    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views, K, NB26);
     uint8_t *base = smem + wib * Ly.total;
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
     uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
     uint16_t *boff = (uint16_t *)(base + Ly.boff);
     uint16_t *bview = (uint16_t *)(base + Ly.bview);
-    uint32_t *scoff2 = (uint32_t *)(base + Ly.coff);
-    uint16_t *tl2 = (uint16_t *)(base + Ly.tl);
+    uint32_t *scoff = (uint32_t *)(base + Ly.coff);
+    uint32_t *pl2 = (uint32_t *)(base + Ly.pl);
+    uint2 *cl2 = (uint2 *)(base + Ly.cl);
     uint8_t *chains = base + Ly.chain0;
     float *halo_lo = (float *)(base + Ly.halo);
     float *halo_hi = halo_lo + TA;
@@ -146,31 +179,42 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
     const int grp = pair / A.N, g = pair - grp * A.N;
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
     const int Cw = A.nwarps / (G * A.N);
+    auto chain = [&](int k) { return chains + (size_t)k * Ly.chain_size; };
+
     // this lane's prior neighbour: lanes 0..7 the in-plane 8-neighbourhood,
-    // or (volumes) lanes 0..25 the 26-neighbourhood
-    int pdz = 0, pdi, pdj;
-    float pb;
-    if (A.nb26) {
-        const int kk = lane < 13 ? lane : lane + 1;   // skip the centre of the 3x3x3
-        pdz = kk / 9 - 1;
-        pdi = (kk / 3) % 3 - 1;
-        pdj = kk % 3 - 1;
-        const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
-        pb = lane < 26 ? A.pscale * A.b26[d2 - 1] : 0.f;
-    } else {
+    // or (volumes) lanes 0..25 the 26-neighbourhood; other lanes read the
+    // pixel itself with weight 0.  mbit: the neighbour's bit in a pixel's
+    // 3x3 in-image mask.
+    int pdz = 0, pdi = 0, pdj = 0;
+    float pb = 0.f;
+    if (NB26) {
+        if (lane < 26) {
+            const int kk = lane < 13 ? lane : lane + 1;   // skip the centre of the 3x3x3
+            pdz = kk / 9 - 1;
+            pdi = (kk / 3) % 3 - 1;
+            pdj = kk % 3 - 1;
+            const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
+            const int zz = grp + pdz;
+            pb = (zz >= 0 && zz < A.B) ? A.pscale * A.b26[d2 - 1] : 0.f;
+        }
+    } else if (lane < 8) {
         const int kk = lane < 4 ? lane : lane + 1;
         pdi = kk / 3 - 1;
         pdj = kk % 3 - 1;
-        pb = lane < 8 ? A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge) : 0.f;
+        pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
     }
-    const int nlanes = A.nb26 ? 26 : 8;
-    const int zc = grp * K;   // slice of chain 0 (volumes run one chain per warp)
-    const bool z_in = pdz == 0 || (zc + pdz >= 0 && zc + pdz < A.B);
+    const int mbit = (pdi + 1) * 3 + (pdj + 1);
+    const int noff = pdi * TS + pdj;
+    const float *nbase[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float *xt = (const float *)(chain(k) + Ly.xt);
+        nbase[k] = (pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi)) + noff;
+    }
 
     // chain k: reconstruction grp*K + k
     auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
     auto Xk = [&](int k) { return A.X + ((int64_t)(grp * K + k) * A.N + g) * n; };
-    auto chain = [&](int k) { return chains + (size_t)k * Ly.chain_size; };
 
     // --- super-voxel metadata -------------------------------------------
     auto sv_of = [&](int m) {           // m-th super-voxel of this warp, -1 past the end
@@ -178,15 +222,30 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
         if (slot >= A.nsv) return -1;
         return A.sv_order[A.backward ? A.nsv - 1 - slot : slot];
     };
-    // visiting list of a super-voxel from its column offsets; returns count
-    auto build_list = [&](const uint32_t *sc, uint16_t *tl) {
+    // visiting list of super-voxel sv from its column offsets sc: per
+    // non-empty pixel in visiting order its pixel/tile indices and in-image
+    // neighbour mask, and its column's offset and size; returns the count
+    auto build_list = [&](int svb, const uint32_t *sc, uint32_t *pl, uint2 *cl) {
+        const int bi = (svb / A.nsvx) * S, bj = (svb % A.nsvx) * S;
         int count = 0;
         for (int k0 = 0; k0 < S2; k0 += 32) {
             const int k = k0 + lane;
             const int t = A.backward ? S2 - 1 - k : k;
             const bool ne = k < S2 && sc[t + 1] != sc[t];
             const unsigned m = __ballot_sync(FULL, ne);
-            if (ne) tl[count + __popc(m & lt_mask)] = (uint16_t)t;
+            if (ne) {
+                const int ti = t / S, tj = t % S, i = bi + ti, j = bj + tj;
+                uint32_t mask = 0;
+#pragma unroll
+                for (int di = -1; di <= 1; ++di)
+#pragma unroll
+                    for (int dj = -1; dj <= 1; ++dj)
+                        if (i + di >= 0 && i + di < A.ny && j + dj >= 0 && j + dj < A.nx)
+                            mask |= 1u << ((di + 1) * 3 + dj + 1);
+                const int pos = count + __popc(m & lt_mask);
+                pl[pos] = (uint32_t)t | (uint32_t)((ti + 1) * TS + tj + 1) << 8 | mask << 17;
+                cl[pos] = make_uint2(sc[t], sc[t + 1] - sc[t]);
+            }
             count += __popc(m);
         }
         __syncwarp();
@@ -204,30 +263,45 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
     // first super-voxel: metadata with plain loads
     {
         const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv) * (S2 + 1);
-        for (int k = lane; k <= S2; k += 32) scoff2[k] = coff[k];
+        for (int k = lane; k <= S2; k += 32) scoff[k] = coff[k];
         const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv * Vg;
         for (int v = lane; v < Vg; v += 32) bdesc2[v] = bd[v];
         __syncwarp();
     }
-    int count = build_list(scoff2, tl2);
+    int count = build_list(sv, scoff, pl2, cl2);
     const uint8_t *svcols = A.cols + A.sv_base[(int64_t)g * A.nsv + sv];
-    uint32_t issued = 0, seq = 0;     // ring positions issued / consumed (per warp)
-    if (lane == 0)
-        for (int q = 0; q < min(count, kRing); ++q) {
-            const int t = tl2[q];
-            issue(issued + q, svcols + scoff2[t], scoff2[t + 1] - scoff2[t]);
-        }
-    issued += min(count, kRing);
+    // The warp's columns form one sequence (its super-voxels' visiting lists
+    // one after the other).  seq: columns consumed; issued: columns whose
+    // copy has been started; seq0: sequence number of the current
+    // super-voxel's first column.  Columns of the current and of the next
+    // super-voxel (once its list is built) may be in flight, at most kRing.
+    uint32_t issued = 0, seq = 0, seq0 = 0;
+    int count_n = 0;
     int cur = 0;
+    const uint8_t *svcols_n = nullptr;
+    auto list_entry = [&](uint32_t x, const uint2 *cl, const uint2 *cl_n, const uint8_t **src) {
+        const bool in_cur = x < (uint32_t)count;
+        *src = in_cur ? svcols : svcols_n;
+        return in_cur ? cl[x] : cl_n[x - count];
+    };
+    auto fill_ring = [&](const uint2 *cl, const uint2 *cl_n) {
+        while (issued - seq < (uint32_t)kRing && issued - seq0 < (uint32_t)(count + count_n)) {
+            const uint8_t *src;
+            const uint2 c = list_entry(issued - seq0, cl, cl_n, &src);
+            if (lane == 0) issue(issued, src + c.x, c.y);
+            ++issued;
+        }
+    };
+    fill_ring(cl2, cl2 + S2);
     int status_seen = 0;
 
     for (int m = 0; sv >= 0; ++m) {
         uint32_t *bdesc = bdesc2 + cur * A.max_views;
-        uint32_t *scoff = scoff2 + cur * (S2 + 1);
-        uint16_t *tl = tl2 + cur * S2;
+        const uint32_t *pl = pl2 + cur * S2;
+        const uint2 *cl = cl2 + cur * S2;
         uint32_t *bdesc_n = bdesc2 + (cur ^ 1) * A.max_views;
-        uint32_t *scoff_n = scoff2 + (cur ^ 1) * (S2 + 1);
-        uint16_t *tl_n = tl2 + (cur ^ 1) * S2;
+        uint32_t *pl_n = pl2 + (cur ^ 1) * S2;
+        uint2 *cl_n = cl2 + (cur ^ 1) * S2;
         const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
 
         // --- band layout; band, X and theta2 tiles of every chain -----------
@@ -237,9 +311,11 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             uint8_t *ch = chain(k);
             float2 *beL = (float2 *)(ch + Ly.beL);
             float *xt = (float *)(ch + Ly.xt);
-            float *t2t = (float *)(ch + Ly.t2t);
+            float2 *vt2 = (float2 *)(ch + Ly.vt2);
             const float2 *eL = eLk(k);
             for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[band_global(f, bdesc, boff, bview, A.D)]);
+            // lanes past a column's end gather entry 0 with weight 0: keep it finite
+            if (band_tot == 0 && lane == 0) beL[0] = make_float2(0.f, 0.f);
             const float *Xg = Xk(k);
             for (int q = lane; q < TA; q += 32) {
                 const int i = si * S + q / TS - 1, j = sj * S + q % TS - 1;
@@ -249,13 +325,13 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             const float *t2g = A.theta2 + ((int64_t)(grp * K + k) * A.N + g) * n;
             for (int q = lane; q < S2; q += 32) {
                 const int i = si * S + q / S, j = sj * S + q % S;
-                if (i < A.ny && j < A.nx) cp_async4(&t2t[q], &t2g[(int64_t)i * A.nx + j]);
+                if (i < A.ny && j < A.nx) cp_async4(&vt2[q].y, &t2g[(int64_t)i * A.nx + j]);
             }
         }
-        if (A.nb26) {
+        if (NB26) {
             // X tiles of the neighbouring slices
             for (int h = 0; h < 2; ++h) {
-                const int zz = zc + (h ? 1 : -1);
+                const int zz = grp + (h ? 1 : -1);
                 float *ht = h ? halo_hi : halo_lo;
                 const float *Xz = (zz >= 0 && zz < A.B) ? A.X + ((int64_t)zz * A.N + g) * n : nullptr;
                 for (int q = lane; q < TA; q += 32) {
@@ -268,20 +344,20 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
         cp_async_commit();
         // next super-voxel: claim its metadata while this one runs
         const int sv_n = sv_of(m + 1);
-        const uint8_t *svcols_n = nullptr;
+        svcols_n = nullptr;
         if (sv_n >= 0) {
             svcols_n = A.cols + A.sv_base[(int64_t)g * A.nsv + sv_n];
             const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv_n) * (S2 + 1);
-            for (int k = lane; k <= S2; k += 32) cp_async4(&scoff_n[k], &coff[k]);
+            for (int k = lane; k <= S2; k += 32) cp_async4(&scoff[k], &coff[k]);
             const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv_n * Vg;
             for (int v = lane; v < Vg; v += 32) cp_async4(&bdesc_n[v], &bd[v]);
         }
         cp_async_commit();
-        // v tile (v = 2 wbar - w, FP64 consensus; or the caller's v) with
+        // v (= 2 wbar - w from the FP64 consensus, or the caller's v) with
         // plain loads while the copies above are in flight
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float *vt = (float *)(chain(k) + Ly.vt);
+            float2 *vt2 = (float2 *)(chain(k) + Ly.vt2);
             const int64_t rb = (int64_t)(grp * K + k);
             for (int q = lane; q < S2; q += 32) {
                 const int i = si * S + q / S, j = sj * S + q % S;
@@ -291,15 +367,17 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
                     vv = A.vexp ? A.vexp[(rb * A.N + g) * n + s]
                                 : (float)(2.0 * A.wbar[rb * n + s] - (double)A.w[(rb * A.N + g) * n + s]);
                 }
-                vt[q] = vv;
+                vt2[q].x = vv;
             }
         }
         if (lane == 0) status_seen = *((volatile int *)A.status);
         cp_async_wait_all();
         __syncwarp();
         status_seen = __shfl_sync(FULL, status_seen, 0);
-        int count_n = 0;
-        if (sv_n >= 0) count_n = build_list(scoff_n, tl_n);
+        count_n = 0;
+        if (sv_n >= 0) count_n = build_list(sv_n, scoff, pl_n, cl_n);
+        // a short super-voxel may leave ring slots free: start the next one's columns
+        fill_ring(cl, cl_n);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             uint8_t *ch = chain(k);
@@ -318,57 +396,40 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
         }
 
         // --- visit the pixels ------------------------------------------------
-        int nq = 0;   // columns of the next super-voxel issued so far
         for (int q = 0; q < count; ++q) {
-            const int t = tl[q];
-            const int ti = t / S, tj = t % S;
-            const int i = si * S + ti, j = sj * S + tj;
-            const int tc = (ti + 1) * TS + (tj + 1);
-            // the column that refills the slot this pixel frees: column
-            // q + kRing of this super-voxel, else the next one of the next
-            // super-voxel (offsets read now, off the critical path)
-            const bool rf_cur = q + kRing < count;
-            const bool rf_any = rf_cur || nq < count_n;
-            const uint8_t *rf_src = nullptr;
-            uint32_t rf_bytes = 0;
-            if (rf_any) {
-                const int rt = rf_cur ? tl[q + kRing] : tl_n[nq];
-                const uint32_t *rsc = rf_cur ? scoff : scoff_n;
-                const uint32_t lo = rsc[rt];
-                rf_bytes = rsc[rt + 1] - lo;
-                rf_src = (rf_cur ? svcols : svcols_n) + lo;
-            }
+            const uint32_t pq = pl[q];
+            const int t = (int)(pq & 0xFFu);
+            const int tc = (int)((pq >> 8) & 0x1FFu);
+            // the column that refills the slot this pixel frees (the ring
+            // always has room for one once a column is consumed): the next
+            // of the sequence, if its list is known; read now, off the
+            // critical path
+            const bool rf_any = issued - seq0 < (uint32_t)(count + count_n);
+            const uint8_t *rf_base = svcols;
+            uint2 rf = make_uint2(0u, 0u);
+            if (rf_any) rf = list_entry(issued - seq0, cl, cl_n, &rf_base);
             // prior through the surrogate weights (lane l: neighbour l), from
             // the X tiles only; its curvature is reduced here, before the
-            // column is needed
+            // column is needed.  No branch: out-of-image neighbours and idle
+            // lanes get weight 0.
+            const float pbv = ((pq >> (17 + mbit)) & 1u) ? pb : 0.f;
             float xs[K], pr1[K], pr2[K], prox[K], t2[K];
-            const bool nb_in = lane < nlanes && z_in && i + pdi >= 0 && i + pdi < A.ny && j + pdj >= 0 &&
-                               j + pdj < A.nx;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const float *xt = (const float *)(chain(k) + Ly.xt);
+                const float2 vq = ((const float2 *)(chain(k) + Ly.vt2))[t];
                 xs[k] = xt[tc];
-                pr1[k] = 0.f;
-                pr2[k] = 0.f;
-                if (nb_in) {
-                    const float *nt = pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi);
-                    const float d = xs[k] - nt[tc + pdi * TS + pdj];
-                    pr2[k] = pb * prior_weight(A, d);
-                    pr1[k] = pr2[k] * d;
-                }
-                prox[k] = (xs[k] - ((const float *)(chain(k) + Ly.vt))[t]) * A.inv_s2;
-                t2[k] = ((const float *)(chain(k) + Ly.t2t))[t];
+                const float d = xs[k] - nbase[k][tc];
+                pr2[k] = pbv * prior_weight(A, d);
+                pr1[k] = pr2[k] * d;
+                prox[k] = (xs[k] - vq.x) * A.inv_s2;
+                t2[k] = vq.y;
             }
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
+            for (int o = 1; o < (NB26 ? 32 : 8); o <<= 1)
 #pragma unroll
                 for (int k = 0; k < K; ++k) pr2[k] += __shfl_xor_sync(FULL, pr2[k], o);
-            if (A.nb26) {
-#pragma unroll
-                for (int o = 8; o < 32; o <<= 1)
-#pragma unroll
-                    for (int k = 0; k < K; ++k) pr2[k] += __shfl_xor_sync(FULL, pr2[k], o);
-            } else {
+            if (!NB26) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) pr2[k] = __shfl_sync(FULL, pr2[k], 0);
             }
@@ -376,7 +437,7 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             const uint32_t stg = seq & (kRing - 1);
             const uint32_t parity = (seq / kRing) & 1u;
             uint32_t spins = 0;
-            while (!mbar_try_wait(&bars[stg], parity)) {
+            while (!__all_sync(FULL, mbar_try_wait(&bars[stg], parity))) {
                 if (++spins > kSpinLimit) {
                     // give up: flag the host, then wait (bounded) for this
                     // warp's copies still in flight before leaving
@@ -393,28 +454,33 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             const uint32_t *cidx2 = (const uint32_t *)(col + 4);
             const uint8_t *cval = col + col_idx_bytes(nnz);
 
-            // data term of each chain: p1 = -sum A Lambda e (+ the prior's
-            // gradient in lanes 0..7 / 0..25); theta2 = sum A^2 Lambda is stored
-            float p1[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) p1[k] = pr1[k];
+            // data term of each chain: -sum A Lambda e in two interleaved
+            // accumulators, plus the prior's gradient (lanes 0..7 / 0..25);
+            // theta2 = sum A^2 Lambda is stored
             float alpha[K];
             if constexpr (PR > 0) {
+                // pair loads without branches: lanes past the column's end
+                // read its last pair (or pair 0 of an empty column, inside
+                // the slot) and take (0, 0)
+                const int npairs = (nnz + 1) >> 1;
+                const int lastp = max(npairs - 1, 0);
                 uint32_t ib[PR];
                 float2 av[PR];
 #pragma unroll
                 for (int r = 0; r < PR; ++r) {
                     const int pe = r * 32 + lane;
-                    ib[r] = 0u;
-                    av[r] = make_float2(0.f, 0.f);
-                    if (2 * pe < nnz) {
-                        ib[r] = cidx2[pe];
-                        av[r] = ld_pair<T>(cval, pe);
-                    }
+                    const int pc = min(pe, lastp);
+                    const uint32_t i0 = cidx2[pc];
+                    const float2 a0 = ld_pair<T>(cval, pc);
+                    const bool ok = pe < npairs;
+                    ib[r] = ok ? i0 : 0u;
+                    av[r] = ok ? a0 : make_float2(0.f, 0.f);
                 }
-                float ex[K][PR][2];
-                // no branch per round: pairs past the column's end are (0, 0)
-                // and add nothing, and every gather is issued back to back
+                // pairs past the column's end are (0, 0) and add nothing;
+                // every gather is issued back to back
+                float ex[K][PR][2], pa[K], pc[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) { pa[k] = 0.f; pc[k] = 0.f; }
 #pragma unroll
                 for (int r = 0; r < PR; ++r) {
                     const int b0 = (int)(ib[r] & 0xFFFFu), b1 = (int)(ib[r] >> 16);
@@ -424,10 +490,13 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
                         const float2 e0 = beL[b0], e1 = beL[b1];
                         ex[k][r][0] = e0.x;
                         ex[k][r][1] = e1.x;
-                        p1[k] = fmaf(-av[r].x * e0.y, e0.x, p1[k]);
-                        p1[k] = fmaf(-av[r].y * e1.y, e1.x, p1[k]);
+                        pa[k] = fmaf(-av[r].x * e0.y, e0.x, pa[k]);
+                        pc[k] = fmaf(-av[r].y * e1.y, e1.x, pc[k]);
                     }
                 }
+                float p1[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) p1[k] = (pa[k] + pc[k]) + pr1[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -440,14 +509,13 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
                 // flight.
                 ++seq;
                 if (rf_any) {
-                    if (lane == 0) issue(issued, rf_src, rf_bytes);
+                    if (lane == 0) issue(issued, rf_base + rf.x, rf.y);
                     ++issued;
-                    if (!rf_cur) ++nq;
                 }
-                // the step's sign and zero set come from the numerator alone, so a
-                // fast division leaves the fixed point unchanged
+                // the step's sign and zero set come from the numerator alone, so an
+                // approximate reciprocal leaves the fixed point unchanged
 #pragma unroll
-                for (int k = 0; k < K; ++k) alpha[k] = -__fdividef(p1[k] + prox[k], t2[k] + pr2[k] + A.inv_s2);
+                for (int k = 0; k < K; ++k) alpha[k] = -(p1[k] + prox[k]) * rcp_approx(t2[k] + pr2[k] + A.inv_s2);
                 // update e: the entries of one column are distinct band positions
 #pragma unroll
                 for (int r = 0; r < PR; ++r) {
@@ -456,22 +524,24 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         float2 *beL = (float2 *)(chain(k) + Ly.beL);
-                        if (2 * pe < nnz) beL[b0].x = fmaf(-av[r].x, alpha[k], ex[k][r][0]);
+                        if (pe < npairs) beL[b0].x = fmaf(-av[r].x, alpha[k], ex[k][r][0]);
                         if (2 * pe + 1 < nnz) beL[b1].x = fmaf(-av[r].y, alpha[k], ex[k][r][1]);
                     }
                 }
             } else {
                 float2 *beL = (float2 *)(chain(0) + Ly.beL);
+                float pa = 0.f, pc = 0.f;
                 for (int pe = lane; 2 * pe < nnz; pe += 32) {
                     const uint32_t ib = cidx2[pe];
                     const float2 av = ld_pair<T>(cval, pe);
                     const float2 e0 = beL[ib & 0xFFFFu], e1 = beL[ib >> 16];
-                    p1[0] = fmaf(-av.x * e0.y, e0.x, p1[0]);
-                    p1[0] = fmaf(-av.y * e1.y, e1.x, p1[0]);
+                    pa = fmaf(-av.x * e0.y, e0.x, pa);
+                    pc = fmaf(-av.y * e1.y, e1.x, pc);
                 }
+                float p1 = (pa + pc) + pr1[0];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) p1[0] += __shfl_xor_sync(FULL, p1[0], o);
-                alpha[0] = -__fdividef(p1[0] + prox[0], t2[0] + pr2[0] + A.inv_s2);
+                for (int o = 16; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
+                alpha[0] = -(p1 + prox[0]) * rcp_approx(t2[0] + pr2[0] + A.inv_s2);
                 for (int pe = lane; 2 * pe < nnz; pe += 32) {
                     const uint32_t ib = cidx2[pe];
                     const float2 av = ld_pair<T>(cval, pe);
@@ -480,18 +550,16 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
                     if (2 * pe + 1 < nnz) beL[b1].x = fmaf(-av.y, alpha[0], beL[b1].x);
                 }
             }
-            if (lane == 0) {
+            // X update: every lane holds alpha and stores the same value
 #pragma unroll
-                for (int k = 0; k < K; ++k) ((float *)(chain(k) + Ly.xt))[tc] = xs[k] + alpha[k];
-            }
+            for (int k = 0; k < K; ++k) ((float *)(chain(k) + Ly.xt))[tc] = xs[k] + alpha[k];
             __syncwarp();
             if constexpr (PR == 0) {
                 // the slot was read until the update above
                 ++seq;
                 if (rf_any) {
-                    if (lane == 0) issue(issued, rf_src, rf_bytes);
+                    if (lane == 0) issue(issued, rf_base + rf.x, rf.y);
                     ++issued;
-                    if (!rf_cur) ++nq;
                 }
             }
         }
@@ -515,51 +583,49 @@ __global__ void __launch_bounds__(256, 1) icd_sweep_kernel(SweepArgs A)
             }
         }
         __syncwarp();
-        // the next super-voxel's first columns: those not issued yet
-        if (sv_n >= 0) {
-            while (nq < min(count_n, kRing) && (int)(issued - seq) < kRing) {
-                if (lane == 0) {
-                    const int t = tl_n[nq];
-                    issue(issued, svcols_n + scoff_n[t], scoff_n[t + 1] - scoff_n[t]);
-                }
-                ++issued;
-                ++nq;
-            }
-        }
-        // hand the staged next-super-voxel state over
+        // hand the staged next-super-voxel state over; its successor's list
+        // is built when it starts
         sv = sv_n;
         svcols = svcols_n;
+        seq0 += count;
         count = count_n;
+        count_n = 0;
         cur ^= 1;
-        // now exactly min(count, kRing) columns of the new super-voxel are in
-        // flight, as the pixel loop's refill (column q + kRing) assumes
     }
 }
 
 template <typename T, int S>
-static sweep_fn sweep_lookup_s(int pair_rounds, int K)
+static sweep_fn sweep_lookup_s(int pair_rounds, int K, bool nb26)
 {
+    if (nb26) {
+        if (K != 1) return nullptr;
+        if (pair_rounds <= 2) return icd_sweep_kernel<T, 2, S, 1, true>;
+        if (pair_rounds <= 3) return icd_sweep_kernel<T, 3, S, 1, true>;
+        return icd_sweep_kernel<T, 0, S, 1, true>;
+    }
     if (pair_rounds <= 2)
-        return K == 4 ? icd_sweep_kernel<T, 2, S, 4> : K == 2 ? icd_sweep_kernel<T, 2, S, 2> : icd_sweep_kernel<T, 2, S, 1>;
+        return K == 4 ? icd_sweep_kernel<T, 2, S, 4, false> : K == 2 ? icd_sweep_kernel<T, 2, S, 2, false>
+                                                                     : icd_sweep_kernel<T, 2, S, 1, false>;
     if (pair_rounds <= 3)
-        return K == 4 ? icd_sweep_kernel<T, 3, S, 4> : K == 2 ? icd_sweep_kernel<T, 3, S, 2> : icd_sweep_kernel<T, 3, S, 1>;
-    return K == 1 ? icd_sweep_kernel<T, 0, S, 1> : nullptr;
+        return K == 4 ? icd_sweep_kernel<T, 3, S, 4, false> : K == 2 ? icd_sweep_kernel<T, 3, S, 2, false>
+                                                                     : icd_sweep_kernel<T, 3, S, 1, false>;
+    return K == 1 ? icd_sweep_kernel<T, 0, S, 1, false> : nullptr;
 }
 
 // The sweep kernel for columns of at most 64 * pair_rounds entries (any
-// count when pair_rounds > 3, one chain), super-voxel size S and K chains;
-// nullptr if that combination is not built.
+// count when pair_rounds > 3, one chain), super-voxel size S, K chains and
+// the 8- or 26-neighbourhood; nullptr if that combination is not built.
 template <typename T>
-static sweep_fn sweep_lookup(int pair_rounds, int S, int K)
+static sweep_fn sweep_lookup(int pair_rounds, int S, int K, bool nb26)
 {
     switch (S) {
-    case 4: return sweep_lookup_s<T, 4>(pair_rounds, K);
-    case 8: return sweep_lookup_s<T, 8>(pair_rounds, K);
-    case 16: return K == 1 ? sweep_lookup_s<T, 16>(pair_rounds, 1) : nullptr;
+    case 4: return sweep_lookup_s<T, 4>(pair_rounds, K, nb26);
+    case 8: return sweep_lookup_s<T, 8>(pair_rounds, K, nb26);
+    case 16: return K == 1 ? sweep_lookup_s<T, 16>(pair_rounds, 1, nb26) : nullptr;
     default: return nullptr;
     }
 }
 
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int pair_rounds, int S, int K);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int pair_rounds, int S, int K);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int pair_rounds, int S, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int pair_rounds, int S, int K, bool nb26);

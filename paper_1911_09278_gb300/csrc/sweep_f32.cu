@@ -2,4 +2,7 @@
 // per value type, so the library's device code compiles in parallel).
 #include "sweep.cuh"
 
-sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K) { return sweep_lookup<float>(pair_rounds, S, K); }
+sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K, bool nb26)
+{
+    return sweep_lookup<float>(pair_rounds, S, K, nb26);
+}
