@@ -67,6 +67,11 @@ def lib():
         L.or_mace.argtypes = [P, dbl, dbl, i32, i32, dbl, i32, dbl, vp, i32,
                               vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_mace.restype = i32
+        L.or_prior_prox.argtypes = [P, dbl, vp, vp, i32, dbl]
+        L.or_prior_prox.restype = i32
+        L.or_pnp_mace.argtypes = [P, dbl, dbl, i32, i32, i32, dbl, vp, i32, dbl,
+                                  vp, vp, vp, vp, vp, i32]
+        L.or_pnp_mace.restype = i32
         _lib = L
     return _lib
 
@@ -212,6 +217,32 @@ class Problem:
             raise ValueError("or_mace failed: %d" % it)
         return dict(x=xbar, w=w, X=X, iters=int(it), resid=float(r[0]), hist=hist[:it].copy(),
                     nrmse_hist=nh[:it].copy() if xref is not None else None)
+
+
+    def prior_prox(self, v, sigma, tol=1e-14, max_pass=100000):
+        """H(v) = argmin_z beta h(z) + ||z - v||^2 / (2 sigma^2) (Gauss-Seidel to tol)."""
+        v = _f64(v).ravel()
+        x = np.empty_like(v)
+        lib().or_prior_prox(self.ref, float(sigma), _ptr(v), _ptr(x), int(max_pass), float(tol))
+        return x
+
+    def pnp_mace(self, sigma, rho=0.8, sweeps=1, max_iter=1000, tol=1e-10, w0=None, X0=None,
+                 order=None, n_threads=0, symmetric=False, h_tol=1e-14):
+        """Algorithm 3 (partial-update MACE with the prior's proximal map as
+        the plug-and-play denoiser).  Returns dict(x, w, X, iters, resid, hist)."""
+        N, n = self.n_agents, self.n
+        w = np.zeros((N, n)) if w0 is None else _f64(w0).reshape(N, n).copy()
+        X = np.zeros((N, n)) if X0 is None else _f64(X0).reshape(N, n).copy()
+        xs = np.empty(n)
+        hist = np.zeros(max(int(max_iter), 1))
+        r = np.zeros(1)
+        o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+        it = lib().or_pnp_mace(self.ref, float(sigma), float(rho), int(sweeps), int(bool(symmetric)),
+                               int(max_iter), float(tol), _ptr(o), 1 if X0 is None else 0, float(h_tol),
+                               _ptr(w), _ptr(X), _ptr(xs), _ptr(hist), _ptr(r), int(n_threads))
+        if it < 0:
+            raise ValueError("or_pnp_mace failed: %d" % it)
+        return dict(x=xs, w=w, X=X, iters=int(it), resid=float(r[0]), hist=hist[:it].copy())
 
 
 def mean_theta2(problem):

@@ -17,6 +17,11 @@
  *   - Partial-update MACE (Algorithm 1): v = (2G - I) w; X = F~(v; X);
  *     w <- rho (2X - v) + (1 - rho) w; solution x* = mean_i w_i.
  *   - Centralised MAP by plain ICD (the single-node method of Sec. IV-A).
+ *   - Partial-update MACE with a plug-and-play denoiser (Sec. III,
+ *     Algorithm 3): agents hold the data terms only and use proximal
+ *     parameter sqrt(N) sigma; the consensus operator is
+ *     G_H(w) = H(mean_i w_i) for every agent; the solution is H(mean_i w_i).
+ *     H here is the proximal map of beta h at sigma, computed to convergence.
  *
  * Readings of things the paper leaves open (the paper cites but does not
  * define the projector, the Q-GGMRF prior and the stopping rule):
@@ -62,7 +67,7 @@ typedef struct {
     double beta, sigma_x, p, q, T;
 } or_problem;
 
-int or_version(void) { return 3; }
+int or_version(void) { return 4; }
 
 /* ---------------------------------------------------------------------- */
 /* View angles theta_m = m pi / N_theta (Sec. IV: views uniform over 180 deg) */
@@ -511,5 +516,132 @@ int32_t or_mace(const or_problem *P, double sigma, double rho, int32_t sweeps,
     if (resid_out) *resid_out = r;
     for (int32_t g = 0; g < N; ++g) free(e[g]);
     free(e); free(v); free(wbar); free(nv);
+    return k;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Proximal map of the prior: x = argmin_z beta h(z) + ||z - v||^2 / (2 sigma^2),
+ * by exact coordinate minimisation (Gauss-Seidel in raster order) repeated
+ * until ||dx|| <= tol ||x||, from x = v.  For the quadratic prior each step is
+ * the exact 1-D minimiser; for Q-GGMRF the surrogate step, which is zero
+ * exactly where the coordinate derivative is (so the limit is the prox).
+ * Returns the number of passes. */
+int32_t or_prior_prox(const or_problem *P, double sigma, const double *v, double *x, int32_t max_pass,
+                      double tol)
+{
+    int64_t plane = (int64_t)P->nx * P->ny, n = plane * P->nz;
+    nbr_t nb[26];
+    int nnb = make_nbrs(P->neighbourhood, nb);
+    double inv_s2 = 1.0 / (sigma * sigma);
+    memcpy(x, v, sizeof(double) * (size_t)n);
+    int32_t pass = 0;
+    while (pass < max_pass) {
+        double da2 = 0.0, xx = 0.0;
+        for (int64_t s = 0; s < n; ++s) {
+            int32_t z = (int32_t)(s / plane);
+            int32_t i = (int32_t)((s % plane) / P->nx);
+            int32_t j = (int32_t)(s % P->nx);
+            double gp = 0.0, hp = 0.0;
+            for (int k = 0; k < nnb; ++k) {
+                int32_t zz = z + nb[k].dz, ii = i + nb[k].di, jj = j + nb[k].dj;
+                if (zz < 0 || zz >= P->nz || ii < 0 || ii >= P->ny || jj < 0 || jj >= P->nx)
+                    continue;
+                double d = x[s] - x[zz * plane + (int64_t)ii * P->nx + jj];
+                double wgt = nb[k].b * prior_weight(P, d);
+                gp += wgt * d;
+                hp += wgt;
+            }
+            double num = P->beta * gp + (x[s] - v[s]) * inv_s2;
+            double den = P->beta * hp + inv_s2;
+            double alpha = -num / den;
+            x[s] += alpha;
+            da2 += alpha * alpha;
+        }
+        for (int64_t s = 0; s < n; ++s) xx += x[s] * x[s];
+        ++pass;
+        if (da2 <= tol * tol * (xx > 0.0 ? xx : 1.0)) break;
+    }
+    return pass;
+}
+
+/* Partial-update MACE with a plug-and-play prior, Algorithm 3:
+ *   v = (2 G_H - I) w, G_H(w) = H(mean_i w_i) for every agent;
+ *   X = F~(v; sqrt(N) sigma, X): `sweeps` ICD passes of each agent's data
+ *       term only (beta = 0), symmetric as in or_mace;
+ *   w <- rho (2X - v) + (1 - rho) w;
+ *   solution x* = H(mean_i w_i).
+ * H is or_prior_prox(sigma) solved to h_tol.  Arguments as in or_mace;
+ * init_X != 0 forms X^(0) = G_H(w^(0)). */
+int32_t or_pnp_mace(const or_problem *P, double sigma, double rho, int32_t sweeps, int32_t symmetric,
+                    int32_t max_iter, double tol, const int64_t *order, int32_t init_X, double h_tol,
+                    double *w, double *X, double *xstar, double *resid_hist, double *resid_out,
+                    int32_t n_threads)
+{
+    int32_t N = P->n_agents;
+    int64_t n = (int64_t)P->nx * P->ny * P->nz;
+    if (N < 1 || n < 1 || sigma <= 0.0 || rho <= 0.0 || rho >= 1.0) return OR_EINVAL;
+    int32_t *nv = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    for (int32_t m = 0; m < P->n_views; ++m) {
+        if (P->view_agent[m] < 0 || P->view_agent[m] >= N) { free(nv); return OR_EINVAL; }
+        nv[P->view_agent[m]]++;
+    }
+    double **e = (double **)calloc((size_t)N, sizeof(double *));
+    double *v = (double *)malloc(sizeof(double) * (size_t)(N * n));
+    double *wbar = (double *)malloc(sizeof(double) * (size_t)n);
+    double *hx = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int32_t g = 0; g < N; ++g)
+        e[g] = (double *)malloc(sizeof(double) * (size_t)((int64_t)P->nz * nv[g] * P->n_channels) + 8);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const double sigma_f = sqrt((double)N) * sigma;
+    /* G_H(w): mean over agents, then the denoiser */
+    #define PNP_GH()                                                           \
+        do {                                                                   \
+            for (int64_t s = 0; s < n; ++s) {                                  \
+                double acc = 0.0;                                              \
+                for (int32_t g = 0; g < N; ++g) acc += w[g * n + s];           \
+                wbar[s] = acc / (double)N;                                     \
+            }                                                                  \
+            or_prior_prox(P, sigma, wbar, hx, 100000, h_tol);                  \
+        } while (0)
+    if (init_X) {
+        PNP_GH();
+        for (int32_t g = 0; g < N; ++g) memcpy(X + g * n, hx, sizeof(double) * (size_t)n);
+    }
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t g = 0; g < N; ++g) or_error_sinogram(P, g, X + g * n, e[g]);
+
+    double r = INFINITY;
+    int32_t k = 0;
+    while (k < max_iter) {
+        PNP_GH();
+        for (int32_t g = 0; g < N; ++g)
+            for (int64_t s = 0; s < n; ++s) v[g * n + s] = 2.0 * hx[s] - w[g * n + s];
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t g = 0; g < N; ++g)
+            for (int32_t sw = 0; sw < sweeps; ++sw)
+                icd_sweep_dir(P, g, 1, sigma_f, 0.0, order, symmetric && (sw & 1), v + g * n, X + g * n, e[g]);
+        double dw2 = 0.0, ww2 = 0.0;
+        for (int64_t t = 0; t < N * n; ++t) {
+            double wn = rho * (2.0 * X[t] - v[t]) + (1.0 - rho) * w[t];
+            double d = wn - w[t];
+            dw2 += d * d;
+            ww2 += wn * wn;
+            w[t] = wn;
+        }
+        r = ww2 > 0.0 ? sqrt(dw2 / ww2) : sqrt(dw2);
+        if (resid_hist) resid_hist[k] = r;
+        ++k;
+        if (r < tol) break;
+    }
+    PNP_GH();
+    memcpy(xstar, hx, sizeof(double) * (size_t)n);
+    #undef PNP_GH
+    if (resid_out) *resid_out = r;
+    for (int32_t g = 0; g < N; ++g) free(e[g]);
+    free(e); free(v); free(wbar); free(hx); free(nv);
     return k;
 }
