@@ -127,7 +127,7 @@ def make_inputs(batch, rank):
     return y, lam
 
 
-def oracle_match(x, y, lam):
+def oracle_match(x, y, lam, dtype="f32"):
     """Relative RMSE of the first reconstruction of the batch against the
     oracle's stored MAP image of the same scan (written by
     tests/golden/make_reference.py from the oracle alone), when the stored
@@ -144,7 +144,7 @@ def oracle_match(x, y, lam):
         return {"nrmse_vs_oracle": None, "why": "stored oracle image is of other inputs"}
     ref = d["x"].reshape(x.shape)
     err = float(np.sqrt(np.mean((x.astype(np.float64) - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
-    return {"nrmse_vs_oracle": err, "bound": 1e-4, "oracle_kkt": float(d["kkt"]),
+    return {"nrmse_vs_oracle": err, "bound": 1e-4 if dtype == "f32" else 1e-3, "oracle_kkt": float(d["kkt"]),
             "oracle_iters": int(d["iters"])}
 
 
@@ -237,7 +237,7 @@ def run_mace(args, rank, world):
     el, clocks = timed(True, True, args.warmup)
     iters_main = [it for it, _, _ in iters_seen[-args.steps:]]
     conv_main = all(c for _, _, c in iters_seen[-args.steps:])
-    accuracy = oracle_match(d_x[0].cpu().numpy(), y[0], lam[0])
+    accuracy = oracle_match(d_x[0].cpu().numpy(), y[0], lam[0], args.dtype)
     el_e2e, _ = timed(False, False, 1)
     recons = B * args.steps * world
     value = recons / el
@@ -428,6 +428,58 @@ def run_serve(args):
     }
 
 
+def run_volume(args):
+    """A 3D stack: args.slices slices of 512^2 sharing one 2D matrix (960
+    views over 180 deg, 725 channels), 32 agents with uneven view subsets
+    (16-40 views each, spread over the half circle), 26-neighbourhood
+    Q-GGMRF coupling the slices; all slices and agents in one sweep launch.
+    Times Mann iterations (the iteration count to tolerance is not measured
+    at this size): value = Mann iterations per second of the whole volume."""
+    import torch
+    import synth
+    import paper_1911_09278_gb300 as mace
+    from paper_1911_09278_gb300 import build as gbuild
+
+    gbuild.build()
+    torch.cuda.set_device(0)
+    n, nz, V, D, N = 512, args.slices, 960, 725, 32
+    c = synth.make_volume(n=n, nz=nz, n_views=V, n_channels=D, I0=2e4, mu_max=0.02 * 64 / n, seed=4,
+                          noise_seed=104)
+    va = synth.uneven_partition(204, V, N, 16, 40)
+    sx = synth.prior_sigma_x(c["lam"], V, frac=1.0)
+    stream = torch.cuda.Stream()
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=args.sv, dtype=args.dtype, stream=stream)
+    info = sm.info()
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho,
+                           sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter, tol=0.0,
+                           concurrency=args.concurrency, neighbourhood=26)
+    st = mace.mace_init(sm, c["y"], c["lam"], prm, stream=stream, batch=nz)
+    st.iterate(args.warmup)
+    st.set_timing(True, max_launches=2 * args.steps + 8)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st.launch(args.steps)
+    ev1.record(stream)
+    stream.synchronize()
+    el = ev0.elapsed_time(ev1) / 1000.0
+    ms, nl = st.get_timing()
+    stats = st.stats()
+    st.close()
+    updates = nz * n * n * N
+    return {
+        "metric": "Mann iterations / s of a 3D stack (all slices and agents)", "value": args.steps / el,
+        "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "dtype": args.dtype,
+        "data": "synthetic (seeded ellipsoid phantom, analytic sinograms, Poisson counts)",
+        "sweep_ms": ms / max(1, nl), "voxel_updates_per_s": updates / (ms / max(1, nl) / 1000.0),
+        "concurrency_per_agent": stats["concurrency"],
+        "config": {"workload": "3D %dx%dx%d, 960 views, 725 channels, 32 agents with 16-40 views, "
+                               "26-neighbour Q-GGMRF" % (n, n, nz),
+                   "matrix_gb": info["bytes_columns"] / 1e9, "sigma_normalised": args.sigma, "rho": args.rho},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,7 +507,13 @@ def main():
     ap.add_argument("--max-active", dest="max_active", type=int, default=8)
     ap.add_argument("--serve-concurrency", dest="serve_concurrency", type=int, default=-1)
     ap.add_argument("--serve-dtype", dest="serve_dtype", default="bf16", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--volume", action="store_true",
+                    help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
+    ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()
+    if args.volume:
+        print(json.dumps(run_volume(args)))
+        return
     if args.serve:
         print(json.dumps(run_serve(args)))
         return

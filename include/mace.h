@@ -110,7 +110,16 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   Pixels inside a super-voxel are visited in raster order.
  *   chains: reconstructions of a batch one warp updates together, sharing
  *   every column load (0 or 1: one; 2 or 4: that many when they divide the
- *   batch).  Results do not depend on it. */
+ *   batch).  Results do not depend on it.
+ *   pnp: 0 = Algorithm 1 (the prior inside every agent, weight beta/N);
+ *   1 = Algorithm 3 (Sec. III, MACE with a plug-and-play prior): the agents
+ *   hold the data terms only and use proximal parameter sqrt(N) sigma; the
+ *   consensus operator is G_H(w) = H(mean_i w_i) for every agent, and the
+ *   solution is H(mean_i w_i).  H is the proximal map of the prior beta h at
+ *   sigma, H(v) = (I + sigma^2 beta B)^-1 v for the quadratic prior (the only
+ *   one accepted with pnp = 1, 8-neighbourhood), solved in FP64 by Jacobi
+ *   iterations to round-off.  H is firmly non-expansive, so by Theorem 3 and
+ *   Lemma 2 the fixed point is the MAP image of the whole cost. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -126,6 +135,7 @@ typedef struct {
     int32_t concurrency;
     int32_t sv_order;
     int32_t chains;
+    int32_t pnp;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */

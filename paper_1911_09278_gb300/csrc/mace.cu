@@ -474,7 +474,7 @@ extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t
     const uint8_t *vals_p = col.data() + col_idx_bytes((int)nz);
     std::vector<int> boff(Vg + 1, 0);
     for (int v = 0; v < Vg; ++v) boff[v + 1] = boff[v] + (int)(bd[v] >> 16);
-    for (int k = 0; k < nz; ++k) {
+    for (int k = 0; k < (int)nz; ++k) {
         uint16_t b;
         memcpy(&b, col.data() + 4 + 2 * k, 2);
         int v = (int)(std::upper_bound(boff.begin(), boff.end(), (int)b) - boff.begin()) - 1;
@@ -517,6 +517,9 @@ struct mace_state {
     float *d_X = nullptr;      // [B][N][n]
     float *d_vexp = nullptr;   // [B][N][n] explicit v (prox-pass entry point)
     float *d_theta2 = nullptr; // [B][N][n] sum_{k in J_g} A_ks^2 Lambda_k
+    double *d_hbuf = nullptr;  // pnp: [2][B][n] the denoiser's input and its second iterate
+    int h_iters = 0;           // pnp: Jacobi iterations of H (even)
+    double h_c = 0.0;          // pnp: sigma^2 beta / sigma_x^2
     double *d_wbar = nullptr;  // [B][n]
     double *d_part = nullptr;  // [B][nblk_mann][2] residual partials
     double *d_resid = nullptr; // [B][3]: dw2, ww2, r
@@ -761,6 +764,40 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
     if (lane == 0) atomicAdd(total, sum);
 }
 
+// One Jacobi iteration of the plug-and-play denoiser H (Algorithm 3): the
+// proximal map of the quadratic prior, x = (I + c B)^-1 v with
+// (B x)_s = sum_r b_sr (x_s - x_r) (8-neighbourhood, b_sr ~ 1/distance summing
+// to 1, out-of-image neighbours dropped, c = sigma^2 beta / sigma_x^2):
+// x_s <- (v_s + c sum_r b_sr x_r) / (1 + c sum_r b_sr).  FP64.
+__global__ void prior_prox_jacobi_kernel(const double *__restrict__ v, const double *__restrict__ xin,
+                                         double *__restrict__ xout, int B, int nx, int ny, double c,
+                                         double b_edge, double b_diag)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)nx * ny;
+    if (k >= (int64_t)B * n) return;
+    const int64_t b = k / n, s = k - b * n;
+    const int i = (int)(s / nx), j = (int)(s % nx);
+    const double *xb = xin + b * n;
+    double acc = 0.0, bs = 0.0;
+    for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj) {
+            if (!di && !dj) continue;
+            const int ii = i + di, jj = j + dj;
+            if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+            const double w = (di && dj) ? b_diag : b_edge;
+            acc += w * xb[(int64_t)ii * nx + jj];
+            bs += w;
+        }
+    xout[k] = (v[k] + c * acc) / (1.0 + c * bs);
+}
+
+__global__ void to_float_kernel(const double *__restrict__ x, float *__restrict__ out, int64_t m)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) out[k] = (float)x[k];
+}
+
 // Bounded-wait self test: one warp arms an mbarrier for bytes that are never
 // sent and waits on it with the sweep's bounded spin (limit given); on expiry
 // it records MACE_ETIMEOUT in the status word and returns, as the sweep does.
@@ -854,7 +891,9 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.col_stride = (M->max_col_bytes + 15) & ~15;
     A.max_views = M->max_views;
     A.inv_s2 = (float)(1.0 / (st->sigma_abs * st->sigma_abs));
-    A.pscale = (float)(st->P.beta / (double)M->N);
+    A.pscale = st->P.pnp ? 0.f : (float)(st->P.beta / (double)M->N);
+    if (st->P.pnp)   // data-only agents with proximal parameter sqrt(N) sigma (Algorithm 3)
+        A.inv_s2 = (float)(1.0 / ((double)M->N * st->sigma_abs * st->sigma_abs));
     A.prior = st->P.prior;
     A.inv_sx2 = (float)(1.0 / (st->P.sigma_x * st->P.sigma_x));
     A.inv_Tsx = (float)(1.0 / (st->P.T * st->P.sigma_x));
@@ -892,6 +931,8 @@ static int configure_sweep(mace_state *st)
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int col_stride = (M->max_col_bytes + 15) & ~15;
+    // the sweep addresses columns in 16-byte units with 32 bits
+    if (M->bytes_cols >= ((int64_t)1 << 36)) return fail(MACE_EINVAL, "stored matrix larger than 64 GiB");
     // chains per warp: reconstructions of the batch that share each column
     // load (a divisor of the batch; 1 when the columns are not cached)
     int K = 1;
@@ -987,6 +1028,9 @@ static int check_params(const mace_params *P)
     if (P->sv_order != 0 && P->sv_order != 1) return fail(MACE_EINVAL, "sv_order must be 0 or 1");
     if (P->chains != 0 && P->chains != 1 && P->chains != 2 && P->chains != 4)
         return fail(MACE_EINVAL, "chains must be 0, 1, 2 or 4");
+    if (P->pnp != 0 && P->pnp != 1) return fail(MACE_EINVAL, "pnp must be 0 or 1");
+    if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
+        return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
 }
 
@@ -1002,6 +1046,7 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_part);
     cudaFree(st->d_resid);
     cudaFree(st->d_theta2);
+    cudaFree(st->d_hbuf);
     cudaFree(st->d_status);
     cudaFree(st->d_sv_order);
     for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
@@ -1022,12 +1067,38 @@ static int copy_out(void *dst, const void *src, size_t bytes, int is_dev, cudaSt
     return MACE_OK;
 }
 
-// X^(0) = G(w^(0)) (Algorithm 1 initialisation)
+// The consensus operator into d_wbar (FP64): G (Algorithm 1) = mean_i w_i, or
+// G_H (Algorithm 3) = H(mean_i w_i) with H by h_iters Jacobi iterations from
+// the mean; x_out (device, optional) receives it in FP32.
+static int apply_consensus(mace_state *st, float *x_out)
+{
+    const mace_sysmatrix *M = st->M;
+    const int64_t Bn = (int64_t)st->B * st->n;
+    const unsigned blocks = (unsigned)((Bn + 255) / 256);
+    consensus_kernel<<<blocks, 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, st->d_wbar,
+                                                     st->P.pnp ? nullptr : x_out);
+    if (st->P.pnp) {
+        double *v = st->d_hbuf, *x2 = st->d_hbuf + Bn;
+        CUDA_TRY(cudaMemcpyAsync(v, st->d_wbar, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, st->stream));
+        const double bsum = 4.0 + 4.0 / std::sqrt(2.0);
+        for (int k = 0; k < st->h_iters; ++k)
+            prior_prox_jacobi_kernel<<<blocks, 256, 0, st->stream>>>(v, (k & 1) ? x2 : st->d_wbar,
+                                                                     (k & 1) ? st->d_wbar : x2, st->B, M->geo.nx,
+                                                                     M->geo.ny, st->h_c, 1.0 / bsum,
+                                                                     (1.0 / std::sqrt(2.0)) / bsum);
+        if (x_out) to_float_kernel<<<blocks, 256, 0, st->stream>>>(st->d_wbar, x_out, Bn);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MACE_OK;
+}
+
+// X^(0) = G(w^(0)) (Algorithm 1) or G_H(w^(0)) (Algorithm 3)
 static int set_X_from_w(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
     const int64_t Bn = (int64_t)st->B * st->n;
-    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, st->d_wbar, nullptr);
+    int rc = apply_consensus(st, nullptr);
+    if (rc) return rc;
     broadcast_kernel<<<(unsigned)((Bn * M->N + 255) / 256), 256, 0, st->stream>>>(st->d_wbar, st->d_X, st->B, M->N, st->n);
     CUDA_TRY(cudaGetLastError());
     return MACE_OK;
@@ -1106,16 +1177,6 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("input packing: ") + cudaGetErrorString(ce));
     if (bad) return bail(MACE_EINVAL, "y and weights must be finite and weights >= 0");
     if (cudaMemsetAsync(st->d_status, 0, sizeof(int), s) != cudaSuccess) return bail(MACE_ECUDA, "memset status");
-    // w^(0), X^(0) = G(w^(0)), e = y - A X
-    if (w0) {
-        rc = copy_in(st->d_w, w0, sizeof(float) * NN, ptr_is_device, s);
-        if (rc) { mace_free_state(st); return rc; }
-    } else if (cudaMemsetAsync(st->d_w, 0, sizeof(float) * NN, s) != cudaSuccess) {
-        return bail(MACE_ECUDA, "memset w");
-    }
-    rc = set_X_from_w(st);
-    if (rc == MACE_OK) rc = launch_forward(st);
-    if (rc) { mace_free_state(st); return rc; }
     // theta2 per (b, agent, pixel) and its mean; sigma in image units
     {
         double *d_t2 = nullptr;
@@ -1145,6 +1206,27 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
             st->sigma_abs = params->sigma;
         }
     }
+    if (params->pnp) {
+        // H: Jacobi for (I + c B) x = v contracts by c / (1 + c) per iteration
+        // (sum_r b_sr <= 1); iterate to FP64 round-off, an even count
+        st->h_c = st->sigma_abs * st->sigma_abs * params->beta / (params->sigma_x * params->sigma_x);
+        const double q = st->h_c / (1.0 + st->h_c);
+        int k = q > 0.0 ? (int)std::ceil(std::log(1e-15) / std::log(q)) : 1;
+        k = std::max(2, std::min(1000, k + (k & 1)));
+        st->h_iters = k;
+        if (cudaMalloc(&st->d_hbuf, sizeof(double) * 2 * batch * st->n) != cudaSuccess)
+            return bail(MACE_ENOMEM, "cudaMalloc failed for the denoiser buffers");
+    }
+    // w^(0), X^(0) = G(w^(0)), e = y - A X
+    if (w0) {
+        rc = copy_in(st->d_w, w0, sizeof(float) * NN, ptr_is_device, s);
+        if (rc) { mace_free_state(st); return rc; }
+    } else if (cudaMemsetAsync(st->d_w, 0, sizeof(float) * NN, s) != cudaSuccess) {
+        return bail(MACE_ECUDA, "memset w");
+    }
+    rc = set_X_from_w(st);
+    if (rc == MACE_OK) rc = launch_forward(st);
+    if (rc) { mace_free_state(st); return rc; }
     rc = configure_sweep(st);
     if (rc) { mace_free_state(st); return rc; }
     ce = cudaStreamSynchronize(s);
@@ -1156,9 +1238,8 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
 static int run_iteration(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
-    const int64_t Bn = (int64_t)st->B * st->n;
-    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, st->d_wbar, nullptr);
-    CUDA_TRY(cudaGetLastError());
+    int rc0 = apply_consensus(st, nullptr);
+    if (rc0) return rc0;
     for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
         int rc = launch_sweep(st, st->P.symmetric ? (k & 1) : 0, nullptr);
         if (rc) return rc;
@@ -1259,17 +1340,17 @@ extern "C" int mace_get_timing(mace_state *st, double *sweep_ms, int32_t *launch
 extern "C" int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device)
 {
     if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
-    const mace_sysmatrix *M = st->M;
     const int64_t Bn = (int64_t)st->B * st->n;
     float *d_x = ptr_is_device ? x_out : nullptr;
     if (!d_x && cudaMalloc(&d_x, sizeof(float) * Bn) != cudaSuccess) return fail(MACE_ENOMEM, "cudaMalloc x");
-    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, nullptr, d_x);
-    cudaError_t ce = cudaGetLastError();
-    if (ce == cudaSuccess && !ptr_is_device) {
+    const int rc = apply_consensus(st, d_x);
+    cudaError_t ce = cudaSuccess;
+    if (rc == MACE_OK && !ptr_is_device) {
         ce = cudaMemcpyAsync(x_out, d_x, sizeof(float) * Bn, cudaMemcpyDeviceToHost, st->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st->stream);
     }
     if (!ptr_is_device) cudaFree(d_x);
+    if (rc) return rc;
     if (ce != cudaSuccess) return fail(MACE_ECUDA, std::string("consensus: ") + cudaGetErrorString(ce));
     return MACE_OK;
 }
@@ -1291,7 +1372,6 @@ static float *g_noalloc_addr[256] = {nullptr};
 extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_is_device)
 {
     if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
-    const mace_sysmatrix *M = st->M;
     const int64_t Bn = (int64_t)st->B * st->n;
     float *d_x = x_out;
     if (!ptr_is_device) {
@@ -1310,8 +1390,8 @@ extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_
         }
         d_x = g_noalloc_addr[dev];
     }
-    consensus_kernel<<<(unsigned)((Bn + 255) / 256), 256, 0, st->stream>>>(st->d_w, st->B, M->N, st->n, nullptr, d_x);
-    CUDA_TRY(cudaGetLastError());
+    const int rc = apply_consensus(st, d_x);
+    if (rc) return rc;
     if (!ptr_is_device) {
         CUDA_TRY(cudaMemcpyAsync(x_out, d_x, sizeof(float) * Bn, cudaMemcpyDeviceToHost, st->stream));
         CUDA_TRY(cudaStreamSynchronize(st->stream));

@@ -44,14 +44,16 @@ typedef void (*sweep_fn)(SweepArgs);
 //   boff:   max_views * 2                 band offset of each view (u16)
 //   bview:  max_band * 2                  view of each band entry (u16)
 //   coff:   (S^2 + 1) * 4                 column byte offsets of the next super-voxel (staging)
-//   pl:     2 * S^2 * 4                   per visited pixel: t | tile index << 8 | neighbour mask << 17
-//   cl:     2 * S^2 * 8                   per visited pixel: (column byte offset, bytes)
+//   pl:     2 * S^2 * 4                   per visited pixel: tile index | neighbour mask << 9
+//   cl:     2 * S^2 * 8                   per visited pixel: (column offset from the matrix start
+//                                         in 16-byte units, bytes)
 //   halo:   2 * (S+2)^2 * 4               X tiles of the slices below and above (volumes only)
 // and per chain:
-//   beL:    max_band * 8                  (e, Lambda) of the band, e kept current
+//   beL:    (max_band + 1) * 8            (e, Lambda) of the band, e kept current; the last
+//                                         entry takes the stores of lanes past a column's end
 //   bsnap:  max_band * 4                  e of the band when the super-voxel began
 //   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
-//   vt2:    S^2 * 8                       (v, theta2) per pixel of the tile
+//   vt2:    S^2 * 8                       per visited pixel (v / sigma^2, theta2 + 1 / sigma^2)
 struct WarpSmem {
     size_t ring, bars, bdesc, boff, bview, coff, pl, cl, halo, chain0, chain_size;
     size_t beL, bsnap, xt, vt2;
@@ -77,7 +79,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_strid
     L.halo = o;  o += halo ? r16(2 * TA * 4) : 0;
     L.chain0 = o;
     size_t c = 0;
-    L.beL = c;   c += r16((size_t)max_band * 8);
+    L.beL = c;   c += r16((size_t)(max_band + 1) * 8);   // + a sink entry for masked-off stores
     L.bsnap = c; c += r16((size_t)max_band * 4);
     L.xt = c;    c += r16(TA * 4);
     L.vt2 = c;   c += r16(S2 * 8);
@@ -216,6 +218,12 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
     auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
     auto Xk = [&](int k) { return A.X + ((int64_t)(grp * K + k) * A.N + g) * n; };
 
+    // pixel t = ti * S + tj of a visiting-list word (tile index (ti+1)*TS + tj+1)
+    auto tile_pixel = [&](uint32_t word) {
+        const int tc = (int)(word & 0x1FFu);
+        return (tc / TS - 1) * S + (tc % TS - 1);
+    };
+
     // --- super-voxel metadata -------------------------------------------
     auto sv_of = [&](int m) {           // m-th super-voxel of this warp, -1 past the end
         const int slot = cidx + m * Cw;
@@ -227,6 +235,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
     // neighbour mask, and its column's offset and size; returns the count
     auto build_list = [&](int svb, const uint32_t *sc, uint32_t *pl, uint2 *cl) {
         const int bi = (svb / A.nsvx) * S, bj = (svb % A.nsvx) * S;
+        const int64_t svoff = A.sv_base[(int64_t)g * A.nsv + svb];
         int count = 0;
         for (int k0 = 0; k0 < S2; k0 += 32) {
             const int k = k0 + lane;
@@ -243,8 +252,8 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                         if (i + di >= 0 && i + di < A.ny && j + dj >= 0 && j + dj < A.nx)
                             mask |= 1u << ((di + 1) * 3 + dj + 1);
                 const int pos = count + __popc(m & lt_mask);
-                pl[pos] = (uint32_t)t | (uint32_t)((ti + 1) * TS + tj + 1) << 8 | mask << 17;
-                cl[pos] = make_uint2(sc[t], sc[t + 1] - sc[t]);
+                pl[pos] = (uint32_t)((ti + 1) * TS + tj + 1) | mask << 9;
+                cl[pos] = make_uint2((uint32_t)((svoff + sc[t]) >> 4), sc[t + 1] - sc[t]);
             }
             count += __popc(m);
         }
@@ -269,7 +278,6 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         __syncwarp();
     }
     int count = build_list(sv, scoff, pl2, cl2);
-    const uint8_t *svcols = A.cols + A.sv_base[(int64_t)g * A.nsv + sv];
     // The warp's columns form one sequence (its super-voxels' visiting lists
     // one after the other).  seq: columns consumed; issued: columns whose
     // copy has been started; seq0: sequence number of the current
@@ -278,17 +286,14 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
     uint32_t issued = 0, seq = 0, seq0 = 0;
     int count_n = 0;
     int cur = 0;
-    const uint8_t *svcols_n = nullptr;
-    auto list_entry = [&](uint32_t x, const uint2 *cl, const uint2 *cl_n, const uint8_t **src) {
-        const bool in_cur = x < (uint32_t)count;
-        *src = in_cur ? svcols : svcols_n;
-        return in_cur ? cl[x] : cl_n[x - count];
+    auto list_entry = [&](uint32_t x, const uint2 *cl, const uint2 *cl_n) {
+        return x < (uint32_t)count ? cl[x] : cl_n[x - count];
     };
+    auto col_src = [&](uint2 c) { return A.cols + ((uint64_t)c.x << 4); };
     auto fill_ring = [&](const uint2 *cl, const uint2 *cl_n) {
         while (issued - seq < (uint32_t)kRing && issued - seq0 < (uint32_t)(count + count_n)) {
-            const uint8_t *src;
-            const uint2 c = list_entry(issued - seq0, cl, cl_n, &src);
-            if (lane == 0) issue(issued, src + c.x, c.y);
+            const uint2 c = list_entry(issued - seq0, cl, cl_n);
+            if (lane == 0) issue(issued, col_src(c), c.y);
             ++issued;
         }
     };
@@ -323,9 +328,9 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                 else xt[q] = 0.f;
             }
             const float *t2g = A.theta2 + ((int64_t)(grp * K + k) * A.N + g) * n;
-            for (int q = lane; q < S2; q += 32) {
-                const int i = si * S + q / S, j = sj * S + q % S;
-                if (i < A.ny && j < A.nx) cp_async4(&vt2[q].y, &t2g[(int64_t)i * A.nx + j]);
+            for (int q = lane; q < count; q += 32) {
+                const int t = tile_pixel(pl[q]);
+                cp_async4(&vt2[q].y, &t2g[(int64_t)(si * S + t / S) * A.nx + sj * S + t % S]);
             }
         }
         if (NB26) {
@@ -344,9 +349,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         cp_async_commit();
         // next super-voxel: claim its metadata while this one runs
         const int sv_n = sv_of(m + 1);
-        svcols_n = nullptr;
         if (sv_n >= 0) {
-            svcols_n = A.cols + A.sv_base[(int64_t)g * A.nsv + sv_n];
             const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv_n) * (S2 + 1);
             for (int k = lane; k <= S2; k += 32) cp_async4(&scoff[k], &coff[k]);
             const uint32_t *bd = A.band + (int64_t)A.nsv * v0 + (int64_t)sv_n * Vg;
@@ -359,15 +362,12 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         for (int k = 0; k < K; ++k) {
             float2 *vt2 = (float2 *)(chain(k) + Ly.vt2);
             const int64_t rb = (int64_t)(grp * K + k);
-            for (int q = lane; q < S2; q += 32) {
-                const int i = si * S + q / S, j = sj * S + q % S;
-                float vv = 0.f;
-                if (i < A.ny && j < A.nx) {
-                    const int64_t s = (int64_t)i * A.nx + j;
-                    vv = A.vexp ? A.vexp[(rb * A.N + g) * n + s]
-                                : (float)(2.0 * A.wbar[rb * n + s] - (double)A.w[(rb * A.N + g) * n + s]);
-                }
-                vt2[q].x = vv;
+            for (int q = lane; q < count; q += 32) {
+                const int t = tile_pixel(pl[q]);
+                const int64_t s = (int64_t)(si * S + t / S) * A.nx + sj * S + t % S;
+                const float vv = A.vexp ? A.vexp[(rb * A.N + g) * n + s]
+                                        : (float)(2.0 * A.wbar[rb * n + s] - (double)A.w[(rb * A.N + g) * n + s]);
+                vt2[q].x = vv * A.inv_s2;
             }
         }
         if (lane == 0) status_seen = *((volatile int *)A.status);
@@ -384,6 +384,8 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
             const float2 *beL = (const float2 *)(ch + Ly.beL);
             float *bsnap = (float *)(ch + Ly.bsnap);
             for (int f = lane; f < band_tot; f += 32) bsnap[f] = beL[f].x;
+            float2 *vt2 = (float2 *)(ch + Ly.vt2);
+            for (int q = lane; q < count; q += 32) vt2[q].y += A.inv_s2;
         }
         __syncwarp();
         if (status_seen != 0) {
@@ -396,34 +398,33 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         }
 
         // --- visit the pixels ------------------------------------------------
+#pragma unroll 2
         for (int q = 0; q < count; ++q) {
             const uint32_t pq = pl[q];
-            const int t = (int)(pq & 0xFFu);
-            const int tc = (int)((pq >> 8) & 0x1FFu);
+            const int tc = (int)(pq & 0x1FFu);
             // the column that refills the slot this pixel frees (the ring
             // always has room for one once a column is consumed): the next
             // of the sequence, if its list is known; read now, off the
             // critical path
             const bool rf_any = issued - seq0 < (uint32_t)(count + count_n);
-            const uint8_t *rf_base = svcols;
             uint2 rf = make_uint2(0u, 0u);
-            if (rf_any) rf = list_entry(issued - seq0, cl, cl_n, &rf_base);
+            if (rf_any) rf = list_entry(issued - seq0, cl, cl_n);
             // prior through the surrogate weights (lane l: neighbour l), from
             // the X tiles only; its curvature is reduced here, before the
             // column is needed.  No branch: out-of-image neighbours and idle
             // lanes get weight 0.
-            const float pbv = ((pq >> (17 + mbit)) & 1u) ? pb : 0.f;
+            const float pbv = ((pq >> (9 + mbit)) & 1u) ? pb : 0.f;
             float xs[K], pr1[K], pr2[K], prox[K], t2[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const float *xt = (const float *)(chain(k) + Ly.xt);
-                const float2 vq = ((const float2 *)(chain(k) + Ly.vt2))[t];
+                const float2 vq = ((const float2 *)(chain(k) + Ly.vt2))[q];
                 xs[k] = xt[tc];
                 const float d = xs[k] - nbase[k][tc];
                 pr2[k] = pbv * prior_weight(A, d);
                 pr1[k] = pr2[k] * d;
-                prox[k] = (xs[k] - vq.x) * A.inv_s2;
-                t2[k] = vq.y;
+                prox[k] = fmaf(xs[k], A.inv_s2, -vq.x);   // (x - v) / sigma^2
+                t2[k] = vq.y;                             // theta2 + 1 / sigma^2
             }
 #pragma unroll
             for (int o = 1; o < (NB26 ? 32 : 8); o <<= 1)
@@ -509,23 +510,26 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                 // flight.
                 ++seq;
                 if (rf_any) {
-                    if (lane == 0) issue(issued, rf_base + rf.x, rf.y);
+                    if (lane == 0) issue(issued, col_src(rf), rf.y);
                     ++issued;
                 }
                 // the step's sign and zero set come from the numerator alone, so an
                 // approximate reciprocal leaves the fixed point unchanged
 #pragma unroll
-                for (int k = 0; k < K; ++k) alpha[k] = -(p1[k] + prox[k]) * rcp_approx(t2[k] + pr2[k] + A.inv_s2);
-                // update e: the entries of one column are distinct band positions
+                for (int k = 0; k < K; ++k) alpha[k] = -(p1[k] + prox[k]) * rcp_approx(t2[k] + pr2[k]);
+                // update e: the entries of one column are distinct band positions;
+                // stores past the column's end go to the sink entry (no branch)
+                const int sink = A.max_band;
 #pragma unroll
                 for (int r = 0; r < PR; ++r) {
                     const int pe = r * 32 + lane;
-                    const int b0 = (int)(ib[r] & 0xFFFFu), b1 = (int)(ib[r] >> 16);
+                    const int d0 = pe < npairs ? (int)(ib[r] & 0xFFFFu) : sink;
+                    const int d1 = 2 * pe + 1 < nnz ? (int)(ib[r] >> 16) : sink;
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         float2 *beL = (float2 *)(chain(k) + Ly.beL);
-                        if (pe < npairs) beL[b0].x = fmaf(-av[r].x, alpha[k], ex[k][r][0]);
-                        if (2 * pe + 1 < nnz) beL[b1].x = fmaf(-av[r].y, alpha[k], ex[k][r][1]);
+                        beL[d0].x = fmaf(-av[r].x, alpha[k], ex[k][r][0]);
+                        beL[d1].x = fmaf(-av[r].y, alpha[k], ex[k][r][1]);
                     }
                 }
             } else {
@@ -541,7 +545,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                 float p1 = (pa + pc) + pr1[0];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
-                alpha[0] = -(p1 + prox[0]) * rcp_approx(t2[0] + pr2[0] + A.inv_s2);
+                alpha[0] = -(p1 + prox[0]) * rcp_approx(t2[0] + pr2[0]);
                 for (int pe = lane; 2 * pe < nnz; pe += 32) {
                     const uint32_t ib = cidx2[pe];
                     const float2 av = ld_pair<T>(cval, pe);
@@ -558,7 +562,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                 // the slot was read until the update above
                 ++seq;
                 if (rf_any) {
-                    if (lane == 0) issue(issued, rf_base + rf.x, rf.y);
+                    if (lane == 0) issue(issued, col_src(rf), rf.y);
                     ++issued;
                 }
             }
@@ -586,7 +590,6 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         // hand the staged next-super-voxel state over; its successor's list
         // is built when it starts
         sv = sv_n;
-        svcols = svcols_n;
         seq0 += count;
         count = count_n;
         count_n = 0;
