@@ -1,0 +1,116 @@
+"""Edge cases of the CUDA path against the oracle: a ragged, non-square
+image with an uneven view partition; a single agent; a detector offset so
+that pixels near the centre have empty columns; zero weights (dead
+channels and a dropped view); the size limits of the geometry."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import nrmse
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def edge_case(name):
+    if name == "ragged":        # 45 x 38 pixels: neither side a multiple of 8
+        nx, ny, V, D, N, prior, off = 45, 38, 40, 61, 3, "qggmrf", 0.0
+        va = synth.uneven_partition(7, V, N, 10, 16)
+    elif name == "one_agent":
+        nx, ny, V, D, N, prior, off = 40, 40, 36, 57, 1, "quadratic", 0.0
+        va = None
+    elif name == "offset":      # detector covers t in [2, 22]: central pixels miss every view
+        nx, ny, V, D, N, prior, off = 32, 32, 30, 20, 2, "quadratic", 12.0
+        va = None
+    else:                       # "dead": zero weights on a channel band and on one view
+        nx, ny, V, D, N, prior, off = 48, 48, 40, 69, 4, "qggmrf", 0.0
+        va = None
+    m = min(nx, ny)
+    E = synth.ellipses(31, m, 0.02 * 64 / m)
+    p = synth.sinogram(E, V, D, channel_offset=off)
+    y, lam = synth.measurements(p, 2e4, synth.CounterRNG(131))
+    if name == "dead":
+        lam[:, 30:36] = 0.0
+        lam[7, :] = 0.0
+    sx = synth.prior_sigma_x(lam, V, frac=1.0)
+    P = oracle.Problem(nx, ny, V, D, y, lam, n_agents=N, view_agent=va, prior=prior, sigma_x=sx,
+                       channel_offset=off)
+    xs, it, r = P.central_icd(max_sweeps=40000, tol=1e-13)
+    g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
+    assert np.linalg.norm(P.gradient(xs)) / g0 < 1e-9
+    return dict(nx=nx, ny=ny, V=V, D=D, N=N, prior=prior, off=off, va=va, y=y, lam=lam, sx=sx, P=P, xs=xs)
+
+
+def _sysmatrix(mace, c):
+    return mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], c["N"], view_agent=c["va"],
+                                     channel_offset=c["off"], sv_size=8)
+
+
+@pytest.mark.parametrize("name", ["ragged", "one_agent", "offset", "dead"])
+def test_edge_converges_to_map(gpu_lib, name):
+    mace = gpu_lib
+    c = edge_case(name)
+    sm = _sysmatrix(mace, c)
+    prm = mace.make_params(prior=c["prior"], sigma_x=c["sx"], sigma=0.5, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
+                           symmetric=True, recompute_every=10, tol=2e-8, max_iter=8000, concurrency=1)
+    st = mace.mace_init(sm, c["y"], c["lam"], prm)
+    x, iters, r, conv = st.reconstruct()
+    st.close()
+    sm.close()
+    err = nrmse(x, c["xs"])
+    print("%s: iters=%d r=%.2e nrmse=%.2e" % (name, iters, r, err))
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("name", ["ragged", "offset"])
+def test_edge_one_pass_matches_algorithm2(gpu_lib, name):
+    mace = gpu_lib
+    c = edge_case(name)
+    P, N, n = c["P"], c["N"], c["nx"] * c["ny"]
+    sm = _sysmatrix(mace, c)
+    rng = np.random.default_rng(2)
+    xs = c["xs"]
+    X0 = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
+    v = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
+    prm = mace.make_params(prior=c["prior"], sigma_x=c["sx"], sigma=0.5, sigma_mode=1, concurrency=1)
+    st = mace.mace_init(sm, c["y"], c["lam"], prm)
+    st.set_state(X0.copy(), X0)
+    st.prox_pass(v)
+    _, Xg = st.get_state()
+    sigma = st.stats()["sigma_abs"]
+    order = st.visit_order()
+    st.close()
+    sm.close()
+    for g in range(N):
+        x = X0[g].astype(np.float64)
+        e = P.error_sinogram(g, x)
+        P.icd_sweep(g, x, e, v=v[g].astype(np.float64), sigma=sigma, order=order)
+        assert nrmse(Xg.reshape(N, n)[g], x) < 2e-5, g
+
+
+def test_offset_detector_has_empty_columns(gpu_lib):
+    """The central pixel misses every view: its stored column is empty."""
+    mace = gpu_lib
+    c = edge_case("offset")
+    sm = _sysmatrix(mace, c)
+    for g in range(c["N"]):
+        c0, ln, vals = sm.column(g, 16, 16)
+        assert int(np.sum(ln)) == 0
+        assert sum(len(c["P"].footprint(int(m), 16, 16)[1]) for m in c["P"].agent_views(g)) == 0
+    sm.close()
+
+
+def test_geometry_limits(gpu_lib):
+    mace = gpu_lib
+    with pytest.raises(mace.MaceError) as ei:
+        mace.mace_build_sysmatrix(16, 16, 4097, 23, 1)
+    assert ei.value.code == mace.MACE_EINVAL
+    with pytest.raises(mace.MaceError) as ei:
+        mace.mace_build_sysmatrix(16, 16, 8, 65536, 1)
+    assert ei.value.code == mace.MACE_EINVAL
+    with pytest.raises(mace.MaceError) as ei:
+        mace.mace_build_sysmatrix(16, 16, 0, 23, 1)
+    assert ei.value.code == mace.MACE_EINVAL
