@@ -527,6 +527,11 @@ struct mace_state {
     std::vector<int32_t> sv_order;   // super-voxel visiting order of a forward pass
     int32_t *d_sv_order = nullptr;
     // optional CUDA-event timing of the sweep launches
+    // iterations captured once as a CUDA graph and replayed (explicit streams,
+    // timing off); graph_failed: capture was refused, launch eagerly
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_iters = 0;
+    bool graph_failed = false;
     bool timing = false;
     std::vector<cudaEvent_t> ev;     // pairs (start, stop)
     int ev_used = 0;
@@ -1050,6 +1055,7 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_status);
     cudaFree(st->d_sv_order);
     for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
+    if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
     delete st;
 }
 
@@ -1274,13 +1280,64 @@ static int read_status(mace_state *st, double *r)
     return MACE_OK;
 }
 
+// One chunk of graph_iters iterations (a whole recompute period, starting
+// right after a recompute) from the captured graph; the graph is captured
+// on first use.  Returns 1 when capture is not possible (the caller then
+// launches eagerly), else a MACE code.
+static int graph_chunk(mace_state *st)
+{
+    if (!st->graph_exec) {
+        const int saved = st->iters;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            st->graph_failed = true;
+            return 1;
+        }
+        int rc = MACE_OK;
+        for (int k = 0; k < st->graph_iters && rc == MACE_OK; ++k) rc = run_iteration(st);
+        cudaError_t ce = cudaStreamEndCapture(st->stream, &g);
+        st->iters = saved;
+        if (rc != MACE_OK || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            st->graph_failed = true;
+            return 1;
+        }
+        ce = cudaGraphInstantiate(&st->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            st->graph_exec = nullptr;
+            cudaGetLastError();
+            st->graph_failed = true;
+            return 1;
+        }
+    }
+    CUDA_TRY(cudaGraphLaunch(st->graph_exec, st->stream));
+    st->iters += st->graph_iters;
+    return MACE_OK;
+}
+
 extern "C" int mace_launch(mace_state *st, int32_t n_iters)
 {
     if (!st) return fail(MACE_EINVAL, "state is NULL");
     if (n_iters < 0) return fail(MACE_EINVAL, "n_iters must be >= 0");
-    for (int k = 0; k < n_iters; ++k) {
-        int rc = run_iteration(st);
+    st->graph_iters = st->P.recompute_every > 0 ? st->P.recompute_every : 10;
+    int k = 0;
+    while (k < n_iters) {
+        const bool use_graph = st->stream != nullptr && !st->timing && !st->graph_failed &&
+                               st->iters % st->graph_iters == 0 && n_iters - k >= st->graph_iters;
+        if (use_graph) {
+            const int rc = graph_chunk(st);
+            if (rc == MACE_OK) {
+                k += st->graph_iters;
+                continue;
+            }
+            if (rc != 1) return rc;
+        }
+        const int rc = run_iteration(st);
         if (rc) return rc;
+        ++k;
     }
     return MACE_OK;
 }
