@@ -186,7 +186,9 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
     // this lane's prior neighbour: lanes 0..7 the in-plane 8-neighbourhood,
     // or (volumes) lanes 0..25 the 26-neighbourhood; other lanes read the
     // pixel itself with weight 0.  mbit: the neighbour's bit in a pixel's
-    // 3x3 in-image mask.
+    // 3x3 in-image mask.  With two chains the warp works as two 16-lane
+    // halves (half h: chain h), each with its own lanes 0..7.
+    const int plane_lane = K == 2 ? (lane & 15) : lane;
     int pdz = 0, pdi = 0, pdj = 0;
     float pb = 0.f;
     if (NB26) {
@@ -199,8 +201,8 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
             const int zz = grp + pdz;
             pb = (zz >= 0 && zz < A.B) ? A.pscale * A.b26[d2 - 1] : 0.f;
         }
-    } else if (lane < 8) {
-        const int kk = lane < 4 ? lane : lane + 1;
+    } else if (plane_lane < 8) {
+        const int kk = plane_lane < 4 ? plane_lane : plane_lane + 1;
         pdi = kk / 3 - 1;
         pdj = kk % 3 - 1;
         pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
@@ -213,6 +215,8 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
         const float *xt = (const float *)(chain(k) + Ly.xt);
         nbase[k] = (pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi)) + noff;
     }
+    // two chains: this lane's half's neighbour pointer
+    const float *nb_half = (const float *)(chain(K == 2 ? (lane >> 4) : 0) + Ly.xt) + noff;
 
     // chain k: reconstruction grp*K + k
     auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
@@ -299,6 +303,24 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
     };
     fill_ring(cl2, cl2 + S2);
     int status_seen = 0;
+    // wait for column seq; false when the bounded wait gave up (the host is
+    // flagged and this warp's copies in flight are drained first)
+    auto wait_column = [&]() {
+        const uint32_t stg = seq & (kRing - 1);
+        const uint32_t parity = (seq / kRing) & 1u;
+        uint32_t spins = 0;
+        while (!__all_sync(FULL, mbar_try_wait(&bars[stg], parity))) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicExch(A.status, kStatusTimeout);
+                for (uint32_t q2 = seq + 1; q2 < issued; ++q2) {
+                    uint32_t sp2 = 0;
+                    while (!mbar_try_wait(&bars[q2 & (kRing - 1)], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
+                }
+                return false;
+            }
+        }
+        return true;
+    };
 
     for (int m = 0; sv >= 0; ++m) {
         uint32_t *bdesc = bdesc2 + cur * A.max_views;
@@ -409,6 +431,76 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
             const bool rf_any = issued - seq0 < (uint32_t)(count + count_n);
             uint2 rf = make_uint2(0u, 0u);
             if (rf_any) rf = list_entry(issued - seq0, cl, cl_n);
+            if constexpr (K == 2) {
+                // Two chains: half h (lanes 16h .. 16h+15) updates chain h
+                // over the shared column, covering all its pairs; the control
+                // flow, the column wait and refill and the reductions serve
+                // both pixel updates.
+                const int h = lane >> 4, hl = lane & 15;
+                uint8_t *chh = chain(h);
+                float *xth = (float *)(chh + Ly.xt);
+                const float2 vq = ((const float2 *)(chh + Ly.vt2))[q];
+                const float xs = xth[tc];
+                const float d = xs - nb_half[tc];
+                const float pbv = ((pq >> (9 + mbit)) & 1u) ? pb : 0.f;
+                float pr2 = pbv * prior_weight(A, d);
+                const float pr1 = pr2 * d;
+                const float prox = fmaf(xs, A.inv_s2, -vq.x);   // (x - v) / sigma^2
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+                pr2 = __shfl_sync(FULL, pr2, lane & 16);
+                if (!wait_column()) return;
+                const uint8_t *col = ring + (size_t)(seq & (kRing - 1)) * A.col_stride;
+                const int nnz = *(const uint16_t *)col;
+                const uint32_t *cidx2 = (const uint32_t *)(col + 4);
+                const uint8_t *cval = col + col_idx_bytes(nnz);
+                const int npairs = (nnz + 1) >> 1;
+                const int lastp = max(npairs - 1, 0);
+                constexpr int R2 = 2 * PR;
+                uint32_t ib[R2];
+                float2 av[R2];
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const int pe = r * 16 + hl;
+                    const int pcl = min(pe, lastp);
+                    const uint32_t i0 = cidx2[pcl];
+                    const float2 a0 = ld_pair<T>(cval, pcl);
+                    const bool ok = pe < npairs;
+                    ib[r] = ok ? i0 : 0u;
+                    av[r] = ok ? a0 : make_float2(0.f, 0.f);
+                }
+                float2 *beL = (float2 *)(chh + Ly.beL);
+                float ex[R2][2], pa = 0.f, pc = 0.f;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const float2 e0 = beL[ib[r] & 0xFFFFu], e1 = beL[ib[r] >> 16];
+                    ex[r][0] = e0.x;
+                    ex[r][1] = e1.x;
+                    pa = fmaf(-av[r].x * e0.y, e0.x, pa);
+                    pc = fmaf(-av[r].y * e1.y, e1.x, pc);
+                }
+                float p1 = (pa + pc) + pr1;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
+                // both halves have consumed the column: refill its slot
+                ++seq;
+                if (rf_any) {
+                    if (lane == 0) issue(issued, col_src(rf), rf.y);
+                    ++issued;
+                }
+                const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
+                const int sink = A.max_band;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const int pe = r * 16 + hl;
+                    const int d0 = pe < npairs ? (int)(ib[r] & 0xFFFFu) : sink;
+                    const int d1 = 2 * pe + 1 < nnz ? (int)(ib[r] >> 16) : sink;
+                    beL[d0].x = fmaf(-av[r].x, alpha, ex[r][0]);
+                    beL[d1].x = fmaf(-av[r].y, alpha, ex[r][1]);
+                }
+                xth[tc] = xs + alpha;
+                __syncwarp();
+            } else {
             // prior through the surrogate weights (lane l: neighbour l), from
             // the X tiles only; its curvature is reduced here, before the
             // column is needed.  No branch: out-of-image neighbours and idle
@@ -435,22 +527,8 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                 for (int k = 0; k < K; ++k) pr2[k] = __shfl_sync(FULL, pr2[k], 0);
             }
 
-            const uint32_t stg = seq & (kRing - 1);
-            const uint32_t parity = (seq / kRing) & 1u;
-            uint32_t spins = 0;
-            while (!__all_sync(FULL, mbar_try_wait(&bars[stg], parity))) {
-                if (++spins > kSpinLimit) {
-                    // give up: flag the host, then wait (bounded) for this
-                    // warp's copies still in flight before leaving
-                    if (lane == 0) atomicExch(A.status, kStatusTimeout);
-                    for (uint32_t q2 = seq + 1; q2 < issued; ++q2) {
-                        uint32_t sp2 = 0;
-                        while (!mbar_try_wait(&bars[q2 & (kRing - 1)], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
-                    }
-                    return;
-                }
-            }
-            const uint8_t *col = ring + (size_t)stg * A.col_stride;
+            if (!wait_column()) return;
+            const uint8_t *col = ring + (size_t)(seq & (kRing - 1)) * A.col_stride;
             const int nnz = *(const uint16_t *)col;
             const uint32_t *cidx2 = (const uint32_t *)(col + 4);
             const uint8_t *cval = col + col_idx_bytes(nnz);
@@ -565,6 +643,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(
                     if (lane == 0) issue(issued, col_src(rf), rf.y);
                     ++issued;
                 }
+            }
             }
         }
 

@@ -57,7 +57,7 @@ def test_visit_order_is_permutation(gpu_lib, sv_order, conc):
 
 @pytest.mark.parametrize("prior", ["quadratic", "qggmrf"])
 @pytest.mark.parametrize("backward", [False, True])
-@pytest.mark.parametrize("batch", [1, 4])
+@pytest.mark.parametrize("batch", [1, 2, 4])
 def test_one_pass_matches_algorithm2(gpu_lib, prior, backward, batch):
     """With one super-voxel per agent in flight, a GPU pass is Algorithm 2 in
     the library's visiting order: compare X after one pass from a random state."""
