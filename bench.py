@@ -29,10 +29,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # the timed launch configuration (the full-size parity test runs the same)
-# concurrency -1: one super-voxel row per warp (64 concurrent super-voxels per
-# agent at 512^2 with 8x8 super-voxels); sigma (normalised) and rho from the
-# convergence study recorded with the design notes
-DEFAULTS = dict(batch=2, concurrency=-1, sigma=0.13, rho=0.95, tol=6.5e-7, max_iter=4000, sv=8, dtype="f32")
+# 4x4 super-voxels, concurrency -1: one super-voxel row per warp (128
+# concurrent super-voxels per agent at 512^2); chains 2: each warp updates
+# both scans of the batch in two 16-lane halves over one column load; sigma
+# (normalised) and rho from the convergence study recorded with the design
+# notes
+DEFAULTS = dict(batch=2, concurrency=-1, sigma=0.13, rho=0.95, tol=6.5e-7, max_iter=4000, sv=4, dtype="f32",
+                chains=2)
 
 WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
                      "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
@@ -151,7 +154,7 @@ def oracle_match(x, y, lam, dtype="f32"):
 def solver_params(mace, sigma_x, args):
     return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=args.rho,
                             sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
-                            tol=args.tol, concurrency=args.concurrency, sv_order=0)
+                            tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains)
 
 
 def run_mace(args, rank, world):
@@ -259,7 +262,8 @@ def run_mace(args, rank, world):
         try:
             with open(tf) as f:
                 tt = json.load(f)
-            if tt.get("batch") == B and tt.get("sv") == args.sv and tt.get("dtype") == args.dtype:
+            if (tt.get("batch") == B and tt.get("sv") == args.sv and tt.get("dtype") == args.dtype
+                    and tt.get("chains") == args.chains):
                 traffic = tt.get("bytes_per_launch")
         except Exception:
             pass
@@ -276,7 +280,7 @@ def run_mace(args, rank, world):
         "vs_baseline": None,
         "dtype": "f32" if args.dtype == "f32" else args.dtype + "-A/f32",
         "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Poisson counts)",
-        "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv,
+        "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv, "chains": args.chains,
                    "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma, "rho": args.rho,
                    "tol": args.tol, "iterations": iters_main, "converged": conv_main,
                    "accuracy": accuracy,
@@ -493,8 +497,10 @@ def main():
     ap.add_argument("--tol", type=float, default=DEFAULTS["tol"])
     ap.add_argument("--max-iter", dest="max_iter", type=int, default=DEFAULTS["max_iter"])
     ap.add_argument("--sv", type=int, default=DEFAULTS["sv"])
+    ap.add_argument("--chains", type=int, default=DEFAULTS["chains"],
+                    help="reconstructions of the batch one warp updates together (1, 2 or 4)")
     ap.add_argument("--dtype", default=DEFAULTS["dtype"], choices=["f32", "bf16", "f16"])
-    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=1150,
+    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=1050,
                     help="Mann iterations to tolerance the reference arm scales its sample to (the GPU path's count at the default settings)")
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
@@ -504,7 +510,7 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="continuous batching vs one-at-a-time service on a request stream (its own JSON line)")
     ap.add_argument("--requests", type=int, default=24)
-    ap.add_argument("--max-active", dest="max_active", type=int, default=8)
+    ap.add_argument("--max-active", dest="max_active", type=int, default=16)
     ap.add_argument("--serve-concurrency", dest="serve_concurrency", type=int, default=-1)
     ap.add_argument("--serve-dtype", dest="serve_dtype", default="bf16", choices=["f32", "bf16", "f16"])
     ap.add_argument("--volume", action="store_true",

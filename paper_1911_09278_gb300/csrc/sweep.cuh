@@ -142,7 +142,7 @@ __device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
 #endif
 
 template <typename T, int PR, int S, int K, bool NB26>
-__global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : 224) icd_sweep_kernel(SweepArgs A)
+__global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int S2 = S * S, TS = S + 2, TA = TS * TS;
