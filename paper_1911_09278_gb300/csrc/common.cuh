@@ -153,6 +153,36 @@ __device__ __forceinline__ int load_band_layout(const uint32_t *bd, int Vg, uint
     return run;
 }
 
+// The same bookkeeping with, per band entry, its index in the agent block
+// ([Vg][D]) instead of its view, so loading and flushing the band need one
+// shared-memory read per entry.  Returns the band size.  Warp-cooperative.
+__device__ __forceinline__ int load_band_index(const uint32_t *bd, int Vg, int D, uint32_t *bdesc,
+                                               uint32_t *bglob, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    int run = 0;
+    for (int r = 0; r * 32 < Vg; ++r) {
+        const int v = r * 32 + lane;
+        const uint32_t d = v < Vg ? bd[v] : 0u;
+        const int len = (int)(d >> 16);
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (v < Vg) {
+            const int b0 = run + incl - len;
+            bdesc[v] = d;
+            const uint32_t g0 = (uint32_t)v * (uint32_t)D + (d & 0xFFFFu);
+            for (int k = 0; k < len; ++k) bglob[b0 + k] = g0 + (uint32_t)k;
+        }
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    return run;
+}
+
 // global index (row of the agent block, [Vg][D]) of band entry f
 __device__ __forceinline__ int64_t band_global(int f, const uint32_t *bdesc, const uint16_t *boff,
                                                const uint16_t *bview, int D)

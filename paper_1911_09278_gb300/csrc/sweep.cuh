@@ -41,8 +41,7 @@ typedef void (*sweep_fn)(SweepArgs);
 //   ring:   kRing * col_stride            column staging (TMA destination)
 //   bars:   kRing * 8                     mbarriers
 //   bdesc:  2 * max_views * 4             band descriptors (lo | len << 16), current and next super-voxel
-//   boff:   max_views * 2                 band offset of each view (u16)
-//   bview:  max_band * 2                  view of each band entry (u16)
+//   bglob:  max_band * 4                  index of each band entry in the agent block [Vg][D]
 //   coff:   (S^2 + 1) * 4                 column byte offsets of the next super-voxel (staging)
 //   pl:     2 * S^2 * 4                   per visited pixel: tile index | neighbour mask << 9
 //   cl:     2 * S^2 * 8                   per visited pixel: (column offset from the matrix start
@@ -55,7 +54,7 @@ typedef void (*sweep_fn)(SweepArgs);
 //   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
 //   vt2:    S^2 * 8                       per visited pixel (v / sigma^2, theta2 + 1 / sigma^2)
 struct WarpSmem {
-    size_t ring, bars, bdesc, boff, bview, coff, pl, cl, halo, chain0, chain_size;
+    size_t ring, bars, bdesc, bglob, coff, pl, cl, halo, chain0, chain_size;
     size_t beL, bsnap, xt, vt2;
     size_t total;
 };
@@ -71,8 +70,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_strid
     L.ring = o;  o += r16((size_t)kRing * col_stride);
     L.bars = o;  o += r16(kRing * 8);
     L.bdesc = o; o += r16((size_t)2 * max_views * 4);
-    L.boff = o;  o += r16((size_t)max_views * 2);
-    L.bview = o; o += r16((size_t)max_band * 2);
+    L.bglob = o; o += r16((size_t)max_band * 4);
     L.coff = o;  o += r16((S2 + 1) * 4);
     L.pl = o;    o += r16(2 * S2 * 4);
     L.cl = o;    o += r16(2 * S2 * 8);
@@ -156,8 +154,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
     uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
-    uint16_t *boff = (uint16_t *)(base + Ly.boff);
-    uint16_t *bview = (uint16_t *)(base + Ly.bview);
+    uint32_t *bglob = (uint32_t *)(base + Ly.bglob);
     uint32_t *scoff = (uint32_t *)(base + Ly.coff);
     uint32_t *pl2 = (uint32_t *)(base + Ly.pl);
     uint2 *cl2 = (uint2 *)(base + Ly.cl);
@@ -332,7 +329,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
         const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
 
         // --- band layout; band, X and theta2 tiles of every chain -----------
-        const int band_tot = load_band_layout(bdesc, Vg, bdesc, boff, bview, lane);
+        const int band_tot = load_band_index(bdesc, Vg, A.D, bdesc, bglob, lane);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             uint8_t *ch = chain(k);
@@ -340,7 +337,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
             float *xt = (float *)(ch + Ly.xt);
             float2 *vt2 = (float2 *)(ch + Ly.vt2);
             const float2 *eL = eLk(k);
-            for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[band_global(f, bdesc, boff, bview, A.D)]);
+            for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[bglob[f]]);
             // lanes past a column's end gather entry 0 with weight 0: keep it finite
             if (band_tot == 0 && lane == 0) beL[0] = make_float2(0.f, 0.f);
             const float *Xg = Xk(k);
@@ -662,7 +659,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
             float2 *eL = eLk(k);
             for (int f = lane; f < band_tot; f += 32) {
                 const float de = beL[f].x - bsnap[f];
-                if (de != 0.f) atomicAdd(&eL[band_global(f, bdesc, boff, bview, A.D)].x, de);
+                if (de != 0.f) atomicAdd(&eL[bglob[f]].x, de);
             }
         }
         __syncwarp();
