@@ -857,12 +857,10 @@ static int launch_forward(mace_state *st)
 
 static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26)
 {
-    // entries per column in pairs of 32 lanes
-    const int pair_rounds = (M->max_nnz + 63) / 64;
     switch (M->dtype) {
-    case MACE_F32: return mace_sweep_kernel_f32(pair_rounds, M->S, K, nb26);
-    case MACE_BF16: return mace_sweep_kernel_bf16(pair_rounds, M->S, K, nb26);
-    default: return mace_sweep_kernel_f16(pair_rounds, M->S, K, nb26);
+    case MACE_F32: return mace_sweep_kernel_f32(M->max_nnz, M->S, K, nb26);
+    case MACE_BF16: return mace_sweep_kernel_bf16(M->max_nnz, M->S, K, nb26);
+    default: return mace_sweep_kernel_f16(M->max_nnz, M->S, K, nb26);
     }
 }
 

@@ -453,7 +453,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
                 const uint8_t *cval = col + col_idx_bytes(nnz);
                 const int npairs = (nnz + 1) >> 1;
                 const int lastp = max(npairs - 1, 0);
-                constexpr int R2 = 2 * PR;
+                constexpr int R2 = PR;   // rounds of 16 lanes
                 uint32_t ib[R2];
                 float2 av[R2];
 #pragma unroll
@@ -673,38 +673,52 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
     }
 }
 
-template <typename T, int S>
-static sweep_fn sweep_lookup_s(int pair_rounds, int K, bool nb26)
+// Entries per column in rounds: one or four chains take pairs over 32 lanes
+// (PR = ceil(max_nnz / 64) in {2, 3}; 0: any count, one chain); two chains
+// take pairs over one 16-lane half (PR = ceil(max_nnz / 32) in {4, 5, 6}).
+template <typename T, int S, bool CHAINS>
+static sweep_fn sweep_lookup_s(int max_nnz, int K, bool nb26)
 {
+    const int r32 = (max_nnz + 63) / 64, r16 = (max_nnz + 31) / 32;
     if (nb26) {
         if (K != 1) return nullptr;
-        if (pair_rounds <= 2) return icd_sweep_kernel<T, 2, S, 1, true>;
-        if (pair_rounds <= 3) return icd_sweep_kernel<T, 3, S, 1, true>;
+        if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 1, true>;
+        if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 1, true>;
         return icd_sweep_kernel<T, 0, S, 1, true>;
     }
-    if (pair_rounds <= 2)
-        return K == 4 ? icd_sweep_kernel<T, 2, S, 4, false> : K == 2 ? icd_sweep_kernel<T, 2, S, 2, false>
-                                                                     : icd_sweep_kernel<T, 2, S, 1, false>;
-    if (pair_rounds <= 3)
-        return K == 4 ? icd_sweep_kernel<T, 3, S, 4, false> : K == 2 ? icd_sweep_kernel<T, 3, S, 2, false>
-                                                                     : icd_sweep_kernel<T, 3, S, 1, false>;
-    return K == 1 ? icd_sweep_kernel<T, 0, S, 1, false> : nullptr;
+    if constexpr (CHAINS) {
+        if (K == 2) {
+            if (r16 <= 4) return icd_sweep_kernel<T, 4, S, 2, false>;
+            if (r16 <= 5) return icd_sweep_kernel<T, 5, S, 2, false>;
+            if (r16 <= 6) return icd_sweep_kernel<T, 6, S, 2, false>;
+            return nullptr;
+        }
+        if (K == 4) {
+            if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 4, false>;
+            if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 4, false>;
+            return nullptr;
+        }
+    }
+    if (K != 1) return nullptr;
+    if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 1, false>;
+    if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 1, false>;
+    return icd_sweep_kernel<T, 0, S, 1, false>;
 }
 
-// The sweep kernel for columns of at most 64 * pair_rounds entries (any
-// count when pair_rounds > 3, one chain), super-voxel size S, K chains and
-// the 8- or 26-neighbourhood; nullptr if that combination is not built.
+// The sweep kernel for columns of at most max_nnz entries, super-voxel size
+// S, K chains and the 8- or 26-neighbourhood; nullptr if that combination is
+// not built.
 template <typename T>
-static sweep_fn sweep_lookup(int pair_rounds, int S, int K, bool nb26)
+static sweep_fn sweep_lookup(int max_nnz, int S, int K, bool nb26)
 {
     switch (S) {
-    case 4: return sweep_lookup_s<T, 4>(pair_rounds, K, nb26);
-    case 8: return sweep_lookup_s<T, 8>(pair_rounds, K, nb26);
-    case 16: return K == 1 ? sweep_lookup_s<T, 16>(pair_rounds, 1, nb26) : nullptr;
+    case 4: return sweep_lookup_s<T, 4, true>(max_nnz, K, nb26);
+    case 8: return sweep_lookup_s<T, 8, true>(max_nnz, K, nb26);
+    case 16: return sweep_lookup_s<T, 16, false>(max_nnz, K, nb26);
     default: return nullptr;
     }
 }
 
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int pair_rounds, int S, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int pair_rounds, int S, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int pair_rounds, int S, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_nnz, int S, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_nnz, int S, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_nnz, int S, int K, bool nb26);
