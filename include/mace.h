@@ -110,7 +110,8 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   Pixels inside a super-voxel are visited in raster order.
  *   chains: reconstructions of a batch one warp updates together, sharing
  *   every column load (0 or 1: one; 2 or 4: that many when they divide the
- *   batch).  Results do not depend on it.
+ *   batch; with 2 the warp works as two 16-lane halves, one per
+ *   reconstruction).  Results do not depend on it.
  *   pnp: 0 = Algorithm 1 (the prior inside every agent, weight beta/N);
  *   1 = Algorithm 3 (Sec. III, MACE with a plug-and-play prior): the agents
  *   hold the data terms only and use proximal parameter sqrt(N) sigma; the
