@@ -394,8 +394,8 @@ def run_serve(args):
                             noise_seed=3000 + k)
         sx = synth.prior_sigma_x(c["lam"][0], V, frac=1.0)
         reqs.append(serve.Request(k, 0.0, n, n, V, D, N, c["y"][0], c["lam"][0], sx, None))
-    params = dict(prior="qggmrf", sigma=args.sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2, symmetric=True,
-                  recompute_every=10, tol=args.tol, concurrency=args.serve_concurrency)
+    params = dict(prior="qggmrf", sigma=args.serve_sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
+                  symmetric=True, recompute_every=10, tol=args.serve_tol, concurrency=args.serve_concurrency)
     srv = serve.Server(params, dtype=args.serve_dtype, sv_size=8, max_active=args.max_active,
                        max_iter=args.max_iter)
     for r in reqs:                      # matrices resident before any timing
@@ -428,7 +428,7 @@ def run_serve(args):
         "config": {"workload": "stream of %d 2D requests, sizes %s, agents %s, Poisson arrivals at %.2f/s "
                                "(2x one-at-a-time capacity)" % (len(reqs), SERVE_SIZES, SERVE_AGENTS, rate),
                    "max_active": args.max_active, "concurrency_per_agent": args.serve_concurrency,
-                   "sigma_normalised": args.sigma, "tol": args.tol},
+                   "sv_size": 8, "sigma_normalised": args.serve_sigma, "tol": args.serve_tol},
     }
 
 
@@ -456,7 +456,7 @@ def run_volume(args):
     # amortises the per-super-voxel work better (measured)
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=8, dtype=args.dtype, stream=stream)
     info = sm.info()
-    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho,
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.serve_sigma, sigma_mode=1, rho=args.rho,
                            sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter, tol=0.0,
                            concurrency=args.concurrency, neighbourhood=26)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, stream=stream, batch=nz)
@@ -482,7 +482,7 @@ def run_volume(args):
         "concurrency_per_agent": stats["concurrency"],
         "config": {"workload": "3D %dx%dx%d, 960 views, 725 channels, 32 agents with 16-40 views, "
                                "26-neighbour Q-GGMRF" % (n, n, nz),
-                   "matrix_gb": info["bytes_columns"] / 1e9, "sigma_normalised": args.sigma, "rho": args.rho},
+                   "matrix_gb": info["bytes_columns"] / 1e9, "sigma_normalised": args.serve_sigma, "rho": args.rho},
     }
 
 
@@ -515,6 +515,9 @@ def main():
     ap.add_argument("--max-active", dest="max_active", type=int, default=16)
     ap.add_argument("--serve-concurrency", dest="serve_concurrency", type=int, default=-1)
     ap.add_argument("--serve-dtype", dest="serve_dtype", default="bf16", choices=["f32", "bf16", "f16"])
+    # serving and the 3D stack run 8x8 super-voxels, stable up to sigma about 0.14
+    ap.add_argument("--serve-sigma", dest="serve_sigma", type=float, default=0.13)
+    ap.add_argument("--serve-tol", dest="serve_tol", type=float, default=6.5e-7)
     ap.add_argument("--volume", action="store_true",
                     help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
     ap.add_argument("--slices", type=int, default=64)
