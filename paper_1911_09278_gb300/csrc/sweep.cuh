@@ -120,25 +120,29 @@ __device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
     return fmaf(A.half_q_inv_sx2, a, A.inv_sx2) * r * r;
 }
 
+// Register cap of the one-chain sweep kernel: residency is limited by
+// registers and shared memory together, and at 96 registers (21 warps per SM)
+// the one-chain kernels do not spill; two-chain kernels are capped at 128
+// (16 warps per SM), four-chain kernels keep their registers.
+#ifndef MACE_SWEEP_MAXNREG
+#define MACE_SWEEP_MAXNREG 96
+#endif
+
 // One warp runs K chains (reconstructions b0 .. b0+K-1 of one batch group,
 // all on agent g) over a fixed sequence of super-voxels: slots c, c+C, c+2C,
 // ... of the visiting order, where C warps serve the same (group, agent) -- so
 // about C super-voxels of one agent of one reconstruction are in flight at a
 // time.  Inside a super-voxel the pixels are visited in order; each pixel's
-// column (a flat list of (band position, value) pairs, lane k taking the
-// pairs k, k+32, ...) is streamed once by TMA for all K chains.  The next
-// super-voxel's metadata, visiting list and first columns are prepared while
-// the current one is processed.  PR > 0: at most 64*PR entries per column,
-// kept in registers between the reduction and the update, and the ring slot
-// is refilled once they have been consumed; PR == 0: any count (K must be 1).
+// column (a flat list of (band position, value) pairs) is streamed once by
+// TMA for all K chains.  With one or four chains lane k takes the pairs k,
+// k+32, ... for every chain (PR rounds: at most 64*PR entries; PR == 0: any
+// count, one chain); with two chains the warp works as two 16-lane halves,
+// half h updating chain h and taking the pairs hl, hl+16, ... (PR rounds of
+// 16 lanes: at most 32*PR entries).  Pairs stay in registers between the
+// reduction and the update, and the ring slot is refilled once they have been
+// consumed.  The next super-voxel's metadata, visiting list and first columns
+// are prepared while the current one is processed.
 // NB26: the batch is the z-stack of one volume, 26-neighbourhood prior (K = 1).
-// Register cap of the one-chain sweep kernel: residency is limited by
-// registers and shared memory together, and at 96 registers (21 warps per SM)
-// the one-chain kernels do not spill; multi-chain kernels keep their registers.
-#ifndef MACE_SWEEP_MAXNREG
-#define MACE_SWEEP_MAXNREG 96
-#endif
-
 template <typename T, int PR, int S, int K, bool NB26>
 __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) icd_sweep_kernel(SweepArgs A)
 {
