@@ -200,6 +200,19 @@ int mace_iterate(mace_state *st, int32_t n_iters, double *residual_out,
 int mace_launch(mace_state *st, int32_t n_iters);
 int mace_poll(mace_state *st, double *residual_out, int32_t *converged_out);
 
+/* Non-blocking status.  mace_poll_async enqueues on the state's stream,
+ * after the iterations launched so far, a copy of the batch's Mann
+ * residuals and the device status word into host memory the state owns,
+ * and records an event; it returns at once.  mace_poll_ready never waits:
+ * *ready_out = 0 while that copy is in flight; once it has landed,
+ * *ready_out = 1 and residual_out / converged_out are set as by mace_poll
+ * (a caller may launch further iterations meanwhile: the status is the one
+ * at the point mace_poll_async was called).  Without a pending
+ * mace_poll_async, *ready_out = 1 with the last known residual.
+ * Errors: as mace_poll (MACE_ENUMERIC, MACE_ETIMEOUT, MACE_ECUDA). */
+int mace_poll_async(mace_state *st);
+int mace_poll_ready(mace_state *st, double *residual_out, int32_t *converged_out, int32_t *ready_out);
+
 /* Iterate until the residual is below params.tol or params.max_iter
  * iterations have run (checking every 10 iterations), then write the
  * consensus images x* = mean_i w_i (Algorithm 1 output) to x_out

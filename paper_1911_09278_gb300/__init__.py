@@ -31,7 +31,8 @@ DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
 EXPORTS = [
     "mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
     "mace_get_visit_order",
-    "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
+    "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_poll_async", "mace_poll_ready",
+    "mace_reconstruct", "mace_consensus",
     "mace_set_timing", "mace_get_timing", "mace_wait_selftest", "mace_consensus_noalloc",
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
@@ -97,6 +98,8 @@ def load(path=LIB_PATH):
     L.mace_iterate.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_launch.argtypes = [vp, i32]
     L.mace_poll.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.mace_poll_async.argtypes = [vp]
+    L.mace_poll_ready.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.mace_set_timing.argtypes = [vp, i32, i32]
     L.mace_wait_selftest.argtypes = [ctypes.c_uint32, vp]
     L.mace_consensus_noalloc.argtypes = [vp, vp, i32]
@@ -119,7 +122,8 @@ def load(path=LIB_PATH):
     L.mace_last_error.restype = ctypes.c_char_p
     for name in ("mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
                  "mace_get_visit_order",
-                 "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_reconstruct", "mace_consensus",
+                 "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_poll_async", "mace_poll_ready",
+    "mace_reconstruct", "mace_consensus",
     "mace_set_timing", "mace_get_timing",
                  "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
                  "mace_recompute_error", "mace_get_stats"):
@@ -257,6 +261,18 @@ class State:
         c = ctypes.c_int32()
         _check(load().mace_poll(self.handle, ctypes.byref(r), ctypes.byref(c)))
         return r.value, bool(c.value)
+
+    def poll_async(self):
+        """Enqueue a copy of the current status (returns at once)."""
+        _check(load().mace_poll_async(self.handle))
+
+    def poll_ready(self):
+        """(ready, residual, converged) of the last poll_async, without waiting."""
+        r = ctypes.c_double()
+        c = ctypes.c_int32()
+        ok = ctypes.c_int32()
+        _check(load().mace_poll_ready(self.handle, ctypes.byref(r), ctypes.byref(c), ctypes.byref(ok)))
+        return bool(ok.value), r.value, bool(c.value)
 
     def set_timing(self, enable=True, max_launches=4096):
         _check(load().mace_set_timing(self.handle, int(bool(enable)), max_launches))

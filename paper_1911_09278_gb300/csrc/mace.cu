@@ -530,6 +530,11 @@ struct mace_state {
     // iterations captured once as a CUDA graph and replayed (explicit streams,
     // timing off); graph_failed: capture was refused, launch eagerly
     cudaGraphExec_t graph_exec = nullptr;
+    // non-blocking status: pinned copy of d_resid (3 B doubles) and the
+    // status word, and the event that marks its arrival
+    double *h_poll = nullptr;
+    cudaEvent_t poll_ev = nullptr;
+    bool poll_pending = false;
     int graph_iters = 0;
     bool graph_failed = false;
     bool timing = false;
@@ -1054,6 +1059,8 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_sv_order);
     for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
     if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
+    if (st->poll_ev) cudaEventDestroy(st->poll_ev);
+    if (st->h_poll) cudaFreeHost(st->h_poll);
     delete st;
 }
 
@@ -1257,14 +1264,10 @@ static int run_iteration(mace_state *st)
     return MACE_OK;
 }
 
-// largest relative Mann residual over the batch
-static int read_status(mace_state *st, double *r)
+// largest relative Mann residual over the batch from a host copy of d_resid
+// ([B][3]) and the status word
+static int parse_status(mace_state *st, const double *h, int status, double *r)
 {
-    std::vector<double> h(3 * st->B);
-    int status = 0;
-    CUDA_TRY(cudaMemcpyAsync(h.data(), st->d_resid, sizeof(double) * 3 * st->B, cudaMemcpyDeviceToHost, st->stream));
-    CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
-    CUDA_TRY(cudaStreamSynchronize(st->stream));
     if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
     double worst = 0.0;
     for (int b = 0; b < st->B; ++b) {
@@ -1276,6 +1279,16 @@ static int read_status(mace_state *st, double *r)
     st->last_resid = worst;
     if (!std::isfinite(worst)) return fail(MACE_ENUMERIC, "non-finite Mann residual (divergence)");
     return MACE_OK;
+}
+
+static int read_status(mace_state *st, double *r)
+{
+    std::vector<double> h(3 * st->B);
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(h.data(), st->d_resid, sizeof(double) * 3 * st->B, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return parse_status(st, h.data(), status, r);
 }
 
 // One chunk of graph_iters iterations (a whole recompute period, starting
@@ -1347,6 +1360,50 @@ extern "C" int mace_poll(mace_state *st, double *residual_out, int32_t *converge
     if (st->iters > 0) {
         int rc = read_status(st, &r);
         if (rc) return rc;
+    }
+    if (residual_out) *residual_out = r;
+    if (converged_out) *converged_out = r < st->P.tol ? 1 : 0;
+    return MACE_OK;
+}
+
+extern "C" int mace_poll_async(mace_state *st)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    if (!st->h_poll) {
+        // 3 B residual doubles, then one double's room for the status word
+        if (cudaMallocHost(&st->h_poll, sizeof(double) * (3 * st->B + 1)) != cudaSuccess) {
+            st->h_poll = nullptr;
+            return fail(MACE_ENOMEM, "cudaMallocHost failed for the status copy");
+        }
+        CUDA_TRY(cudaEventCreateWithFlags(&st->poll_ev, cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaMemcpyAsync(st->h_poll, st->d_resid, sizeof(double) * 3 * st->B, cudaMemcpyDeviceToHost,
+                             st->stream));
+    CUDA_TRY(cudaMemcpyAsync(st->h_poll + 3 * st->B, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaEventRecord(st->poll_ev, st->stream));
+    st->poll_pending = true;
+    return MACE_OK;
+}
+
+extern "C" int mace_poll_ready(mace_state *st, double *residual_out, int32_t *converged_out, int32_t *ready_out)
+{
+    if (!st || !ready_out) return fail(MACE_EINVAL, "NULL argument");
+    double r = st->last_resid;
+    *ready_out = 1;
+    if (st->poll_pending) {
+        const cudaError_t q = cudaEventQuery(st->poll_ev);
+        if (q == cudaErrorNotReady) {
+            *ready_out = 0;
+            return MACE_OK;
+        }
+        if (q != cudaSuccess) return fail(MACE_ECUDA, std::string("status copy: ") + cudaGetErrorString(q));
+        st->poll_pending = false;
+        int status = 0;
+        memcpy(&status, st->h_poll + 3 * st->B, sizeof(int));
+        if (st->iters > 0) {
+            const int rc = parse_status(st, st->h_poll, status, &r);
+            if (rc) return rc;
+        }
     }
     if (residual_out) *residual_out = r;
     if (converged_out) *converged_out = r < st->P.tol ? 1 : 0;

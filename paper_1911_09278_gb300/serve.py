@@ -3,11 +3,15 @@
 Requests (a scan: geometry, partition, y, Lambda) arrive over time.  Each
 admitted request gets its own reconstruction state on its own CUDA stream;
 the server enqueues its Mann iterations in short chunks (mace_launch), so the
-iterations of every active request run on the GPU at the same time, polls
-them (mace_poll), retires converged requests (consensus image copied to the
-host) and admits waiting ones as slots and device memory free up.  Stored
-system matrices are shared by every request with the same geometry and
-partition and stay resident.
+iterations of every active request run on the GPU at the same time.  Each
+request keeps two chunks queued: after one chunk a status copy is enqueued
+(mace_poll_async) and the server checks it without waiting
+(mace_poll_ready); when it lands, the next chunk is queued behind the one
+still running, so no stream waits on the host.  Converged requests are
+retired (consensus image copied to the host; they ran one chunk past the
+point where convergence was seen) and waiting ones admitted as slots and
+device memory free up.  Stored system matrices are shared by every request
+with the same geometry and partition and stay resident.
 
 Admission is by device-memory footprint: the request's state plus, for a new
 geometry, its system matrix must fit the budget next to what is resident.
@@ -105,28 +109,44 @@ class Server:
                 stream = torch.cuda.Stream()
                 prm = make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
                 st = mace_init(sm, r.y, r.lam, prm, stream=stream)
-                active.append(dict(req=r, st=st, stream=stream, start=now() - t0,
+                # first chunk, its status copy, and the next chunk behind it
+                st.launch(self.chunk)
+                st.poll_async()
+                seen = self.chunk
+                if seen < self.max_iter:
+                    st.launch(self.chunk)
+                active.append(dict(req=r, st=st, stream=stream, start=now() - t0, seen=seen,
                                    bytes=state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)))
             if not active:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (now() - t0))))
                 continue
-            for a in active:
-                a["st"].launch(self.chunk)
             still = []
+            progressed = False
             for a in active:
-                r_, conv = a["st"].poll()
-                it = a["st"].stats()["iters"]
-                if conv or it >= self.max_iter:
-                    x = a["st"].consensus()
+                st = a["st"]
+                ready, r_, conv = st.poll_ready()
+                if not ready:
+                    still.append(a)
+                    continue
+                progressed = True
+                if conv or a["seen"] >= self.max_iter:
+                    x = st.consensus()
                     fin = now() - t0
-                    done[a["req"].rid] = dict(x=x, iters=it, residual=r_, converged=conv,
+                    done[a["req"].rid] = dict(x=x, iters=st.stats()["iters"], residual=r_, converged=conv,
                                               latency=fin - a["req"].arrival, finish=fin,
                                               start=a["start"])
-                    a["st"].close()
-                else:
-                    still.append(a)
+                    st.close()
+                    continue
+                # status of the chunk queued behind, then one more chunk
+                st.poll_async()
+                a["seen"] = st.stats()["iters"]
+                if a["seen"] < self.max_iter:
+                    st.launch(self.chunk)
+                still.append(a)
             active = still
+            if not progressed:
+                time.sleep(0.0002)
         makespan = max(d["finish"] for d in done.values()) if done else 0.0
         lat = np.array([d["latency"] for d in done.values()])
         first = min(r.arrival for r in requests) if requests else 0.0
