@@ -46,3 +46,20 @@ def test_pnp_fixed_point_is_map_and_equilibrium():
     # and the denoiser's residual alpha = -sum u_i satisfies H(x* + alpha) = x*
     alpha = -sum((x - w[g]) / N for g in range(N))
     assert np.linalg.norm(P.prior_prox(x + alpha, sigma) - x) / np.linalg.norm(x) < 1e-9
+
+
+def test_qggmrf_prior_prox_is_stationary():
+    """The oracle's prior proximal map for the Q-GGMRF prior (a nonlinear
+    map, by coordinate steps to convergence): beta grad h(x) + (x - v) /
+    sigma^2 = 0, with grad h from the cost's gradient on a problem without
+    data (all weights zero)."""
+    n, V, D = 10, 8, 15
+    zero = np.zeros((V, D))
+    sx = 0.01
+    P = oracle.Problem(n, n, V, D, zero, zero, n_agents=1, prior="qggmrf", sigma_x=sx)
+    rng = np.random.default_rng(4)
+    v = 0.02 + 0.01 * rng.standard_normal(P.n)
+    for sigma in (0.3 * sx, 3.0 * sx):
+        x = P.prior_prox(v, sigma)
+        g = P.gradient(x) + (x - v) / sigma ** 2
+        assert np.linalg.norm(g) < 1e-10 * np.linalg.norm((v - v.mean()) / sigma ** 2)
