@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 # (normalised) and rho from the convergence study recorded with the design
 # notes
 DEFAULTS = dict(batch=2, concurrency=-1, sigma=0.17, rho=0.95, tol=8e-7, max_iter=4000, sv=4, dtype="f32",
-                chains=2)
+                chains=2, recompute_every=10)
 
 WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
                      "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
@@ -153,8 +153,8 @@ def oracle_match(x, y, lam, dtype="f32"):
 
 def solver_params(mace, sigma_x, args):
     return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=args.rho,
-                            sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
-                            tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains)
+                            sweeps_per_iter=2, symmetric=True, recompute_every=args.recompute_every,
+                            max_iter=args.max_iter, tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains)
 
 
 def run_mace(args, rank, world):
@@ -282,7 +282,7 @@ def run_mace(args, rank, world):
         "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Poisson counts)",
         "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv, "chains": args.chains,
                    "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma, "rho": args.rho,
-                   "tol": args.tol, "iterations": iters_main, "converged": conv_main,
+                   "tol": args.tol, "recompute_every": args.recompute_every, "iterations": iters_main, "converged": conv_main,
                    "accuracy": accuracy,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (stored matrix %.2f GB)" % (info["bytes_columns"] / 1e9)},
@@ -297,9 +297,9 @@ def run_mace(args, rank, world):
     }
     # kernel launches inside one timed step: init (check, pack, consensus,
     # broadcast, reset, forward, theta2) + per iteration (consensus, 2 sweeps,
-    # mann, residual) + recompute every 10 iterations (reset, forward) + output
+    # mann, residual) + recompute every few iterations (reset, forward) + output
     its = sum(iters_main)
-    out["gpu_launches"] = int(args.steps * 7 + its * 5 + 2 * (its // 10) + args.steps)
+    out["gpu_launches"] = int(args.steps * 7 + its * 5 + 2 * (its // args.recompute_every) + args.steps)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, int(np.mean(iters_main)),
                                            seconds=args.cpu_seconds)
@@ -504,6 +504,8 @@ def main():
     ap.add_argument("--chains", type=int, default=DEFAULTS["chains"],
                     help="reconstructions of the batch one warp updates together (1, 2 or 4)")
     ap.add_argument("--dtype", default=DEFAULTS["dtype"], choices=["f32", "bf16", "f16"])
+    ap.add_argument("--recompute-every", dest="recompute_every", type=int, default=DEFAULTS["recompute_every"],
+                    help="Mann iterations between recomputations of e = y - A x")
     ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=700,
                     help="Mann iterations to tolerance the reference arm scales its sample to (the GPU path's count at the default settings)")
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
