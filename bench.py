@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 # (normalised) and rho from the convergence study recorded with the design
 # notes
 DEFAULTS = dict(batch=2, concurrency=-1, sigma=0.17, rho=0.95, tol=8e-7, max_iter=4000, sv=4, dtype="f32",
-                chains=2, recompute_every=10)
+                chains=2, recompute_every=10, forward="auto")
 
 WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
                      "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
@@ -151,10 +151,17 @@ def oracle_match(x, y, lam, dtype="f32"):
             "oracle_iters": int(d["iters"])}
 
 
+def forward_geometry(args):
+    """The e recompute evaluates A from the geometry when the stored values
+    are rounded (auto), or as asked."""
+    return args.forward == "geometry" or (args.forward == "auto" and args.dtype != "f32")
+
+
 def solver_params(mace, sigma_x, args):
     return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=args.rho,
                             sweeps_per_iter=2, symmetric=True, recompute_every=args.recompute_every,
-                            max_iter=args.max_iter, tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains)
+                            max_iter=args.max_iter, tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains,
+                            forward_geometry=forward_geometry(args))
 
 
 def run_mace(args, rank, world):
@@ -282,7 +289,8 @@ def run_mace(args, rank, world):
         "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Poisson counts)",
         "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv, "chains": args.chains,
                    "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma, "rho": args.rho,
-                   "tol": args.tol, "recompute_every": args.recompute_every, "iterations": iters_main, "converged": conv_main,
+                   "tol": args.tol, "recompute_every": args.recompute_every,
+                   "e_recompute": "geometry" if forward_geometry(args) else "stored values", "iterations": iters_main, "converged": conv_main,
                    "accuracy": accuracy,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (stored matrix %.2f GB)" % (info["bytes_columns"] / 1e9)},
@@ -504,6 +512,9 @@ def main():
     ap.add_argument("--chains", type=int, default=DEFAULTS["chains"],
                     help="reconstructions of the batch one warp updates together (1, 2 or 4)")
     ap.add_argument("--dtype", default=DEFAULTS["dtype"], choices=["f32", "bf16", "f16"])
+    ap.add_argument("--forward", default=DEFAULTS["forward"], choices=["auto", "stored", "geometry"],
+                    help="A for the e recompute: stored values or evaluated from the geometry (auto: geometry "
+                         "when the stored values are BF16/FP16)")
     ap.add_argument("--recompute-every", dest="recompute_every", type=int, default=DEFAULTS["recompute_every"],
                     help="Mann iterations between recomputations of e = y - A x")
     ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=700,

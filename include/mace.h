@@ -120,7 +120,14 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   sigma, H(v) = (I + sigma^2 beta B)^-1 v for the quadratic prior (the only
  *   one accepted with pnp = 1, 8-neighbourhood), solved in FP64 by Jacobi
  *   iterations to round-off.  H is firmly non-expansive, so by Theorem 3 and
- *   Lemma 2 the fixed point is the MAP image of the whole cost. */
+ *   Lemma 2 the fixed point is the MAP image of the whole cost.
+ *   forward_geometry: 0 = the periodic recompute e_i = y_i - A_i X_i (and
+ *   the initial one) reads A_i from the stored columns; 1 = it evaluates
+ *   A_i's strip-integral footprints from the geometry (the super-voxel's
+ *   projection in FP64, the rest in FP32), so with BF16/FP16 stored values
+ *   the recompute still sees the exact projector.  The ICD updates keep
+ *   using the stored values; the fixed point then matches the exact MAP
+ *   image more closely than that of the rounded matrix. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -137,6 +144,7 @@ typedef struct {
     int32_t sv_order;
     int32_t chains;
     int32_t pnp;
+    int32_t forward_geometry;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */

@@ -66,7 +66,8 @@ class Params(ctypes.Structure):
                 ("symmetric", ctypes.c_int32), ("recompute_every", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32),
-                ("chains", ctypes.c_int32), ("pnp", ctypes.c_int32)]
+                ("chains", ctypes.c_int32), ("pnp", ctypes.c_int32),
+                ("forward_geometry", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -226,10 +227,11 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
-                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0, pnp=False):
+                max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0, pnp=False,
+                forward_geometry=False):
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
-                  max_iter, tol, concurrency, sv_order, chains, int(bool(pnp)))
+                  max_iter, tol, concurrency, sv_order, chains, int(bool(pnp)), int(bool(forward_geometry)))
 
 
 class State:

@@ -116,6 +116,19 @@ __device__ __forceinline__ int footprint_dev(const GeoParams &G, double ct, doub
     return L;
 }
 
+// What the footprint of a pixel in one view needs, tabulated on the host in
+// FP64 (the divisions stay off the GPU's FP64 units): the channel coordinate
+// of pixel (i, j)'s centre is q00 + j cq - i sq, and the footprint is the
+// trapezoid of the FP64 routine above with these breakpoints.
+struct ViewGeo {
+    double q00, cq, sq;
+    float u1, u2;    // (w2 - w1) / 2, (w2 + w1) / 2
+    float h, k2;     // plateau height 1 / w2; ramp factor h / (2 w1), 0 when w1 = 0
+    float w1;        // the shorter of a = dx |cos| / dd and b = dx |sin| / dd
+    float half;      // half the footprint width, (a + b) / 2
+    float scale;     // dx^2 / dd
+};
+
 // ---------------------------------------------------------------------------
 // system matrix
 // ---------------------------------------------------------------------------
@@ -133,6 +146,7 @@ struct mace_sysmatrix {
     std::vector<double> cosv, sinv;
     // device
     double2 *d_cs = nullptr;          // (cos, sin) per view in agent order
+    ViewGeo *d_vgeo = nullptr;        // footprint constants per view in agent order
     int *d_view_off = nullptr;        // [N+1]
     uint32_t *d_band = nullptr;       // [nsv * V]: agent g block at nsv*view_off[g], (lo | len << 16)
     uint32_t *d_band_tot = nullptr;   // [N * nsv]
@@ -326,7 +340,26 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
     cudaStream_t s = M->stream;
     const int64_t nband = (int64_t)M->nsv * M->V;
     const int64_t ncol = (int64_t)M->N * M->nsv * M->S2;
-    if (cudaMalloc(&M->d_cs, sizeof(double2) * M->V) != cudaSuccess ||
+    std::vector<ViewGeo> vg(M->V);
+    for (int k = 0; k < M->V; ++k) {
+        const GeoParams &G = M->geo;
+        const double ct = cs[k].x, st = cs[k].y;
+        const double a = G.dx * fabs(ct) / G.dd, b = G.dx * fabs(st) / G.dd;
+        const double w1 = std::min(a, b), w2 = std::max(a, b);
+        const double xc = (0.0 - 0.5 * (double)(G.nx - 1)) * G.dx, yc = 0.5 * (double)(G.ny - 1) * G.dx;
+        vg[k].q00 = (xc * ct + yc * st - G.off) / G.dd + 0.5 * (double)G.D;
+        vg[k].cq = G.dx * ct / G.dd;
+        vg[k].sq = G.dx * st / G.dd;
+        vg[k].u1 = (float)(0.5 * (w2 - w1));
+        vg[k].u2 = (float)(0.5 * (w2 + w1));
+        vg[k].h = (float)(1.0 / w2);
+        vg[k].k2 = w1 > 0.0 ? (float)(1.0 / (w2 * 2.0 * w1)) : 0.f;
+        vg[k].w1 = (float)w1;
+        vg[k].half = (float)(0.5 * (a + b));
+        vg[k].scale = (float)(G.dx * G.dx / G.dd);
+    }
+    if (cudaMalloc(&M->d_vgeo, sizeof(ViewGeo) * M->V) != cudaSuccess ||
+        cudaMalloc(&M->d_cs, sizeof(double2) * M->V) != cudaSuccess ||
         cudaMalloc(&M->d_view_off, sizeof(int) * (M->N + 1)) != cudaSuccess ||
         cudaMalloc(&M->d_band, sizeof(uint32_t) * nband) != cudaSuccess ||
         cudaMalloc(&M->d_band_tot, sizeof(uint32_t) * M->N * M->nsv) != cudaSuccess ||
@@ -334,6 +367,7 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
         cudaMalloc(&M->d_col_off, sizeof(uint32_t) * M->N * M->nsv * (M->S2 + 1)) != cudaSuccess)
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for system-matrix metadata");
     if (cudaMemcpyAsync(M->d_cs, cs.data(), sizeof(double2) * M->V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(M->d_vgeo, vg.data(), sizeof(ViewGeo) * M->V, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(M->d_view_off, M->view_off.data(), sizeof(int) * (M->N + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return cleanup(MACE_ECUDA, "copy of view tables failed");
 
@@ -491,6 +525,7 @@ extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
 {
     if (!M) return;
     cudaFree(M->d_cs);
+    cudaFree(M->d_vgeo);
     cudaFree(M->d_view_off);
     cudaFree(M->d_band);
     cudaFree(M->d_band_tot);
@@ -684,6 +719,90 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
     }
 }
 
+// The same product with A evaluated from the geometry instead of read from
+// the stored columns: the periodic recompute that removes drift (Sec. II-C)
+// then sees the exact projector even when the stored values are BF16/FP16.
+// One warp per (reconstruction, agent, super-voxel); lane l takes views
+// l, l + 32, ... of the agent, so the lanes write disjoint runs of the band.
+// The projection of the super-voxel's first pixel is formed in FP64, the
+// offsets inside the super-voxel and the trapezoid in FP32 (position error
+// ~1e-6 channel).  Channels outside the stored band (values at round-off
+// level on a footprint's edge) are dropped.
+__device__ __forceinline__ float trap_cdf_f(float u, const ViewGeo &G)
+{
+    if (u <= -G.u2) return 0.f;
+    if (u < -G.u1) {
+        const float d = u + G.u2;
+        return G.k2 * d * d;
+    }
+    if (u <= G.u1) return G.h * (0.5f * G.w1 + (u + G.u1));
+    if (u < G.u2) {
+        const float d = G.u2 - u;
+        return 1.f - G.k2 * d * d;
+    }
+    return 1.f;
+}
+
+__global__ void __launch_bounds__(256) forward_geometry_kernel(const ViewGeo *__restrict__ vgeo,
+                                                               const uint32_t *__restrict__ band,
+                                                               const int *__restrict__ view_off, float2 *__restrict__ eL,
+                                                               const float *__restrict__ X, int B, int N, int nsv, int nsvx,
+                                                               int S, int nx, int ny, int D, int64_t ne, int max_band,
+                                                               int max_views)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    const int lane = threadIdx.x & 31;
+    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
+    uint32_t *bdesc = (uint32_t *)base;
+    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
+    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
+    float *acc = (float *)((uint8_t *)bview + r16((size_t)max_band * 2));
+    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (item >= (int64_t)B * N * nsv) return;
+    const int pair = (int)(item / nsv), sv = (int)(item % nsv);
+    const int b = pair / N, g = pair - b * N;
+    const int i0 = (sv / nsvx) * S, j0 = (sv % nsvx) * S, S2 = S * S;
+    const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
+    float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
+    const float *Xg = X + (int64_t)pair * nx * ny;
+    const int band_tot = load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
+    for (int f = lane; f < band_tot; f += 32) acc[f] = 0.f;
+    __syncwarp();
+    for (int v = lane; v < Vg; v += 32) {
+        const int lo_v = (int)(bdesc[v] & 0xFFFFu), len_v = (int)(bdesc[v] >> 16);
+        if (len_v == 0) continue;
+        const ViewGeo G = vgeo[v0 + v];
+        const double q0 = fma((double)j0, G.cq, fma(-(double)i0, G.sq, G.q00));
+        const double qb = floor(q0);
+        const int qi = (int)qb;
+        const float qf = (float)(q0 - qb), cqf = (float)G.cq, sqf = (float)G.sq;
+        const int bo = (int)boff[v] - lo_v;
+        for (int t = 0; t < S2; ++t) {
+            const int ti = t / S, tj = t - ti * S;
+            if (i0 + ti >= ny || j0 + tj >= nx) continue;
+            const float xs = Xg[(int64_t)(i0 + ti) * nx + j0 + tj];
+            if (xs == 0.f) continue;
+            const float q = qf + fmaf((float)tj, cqf, -(float)ti * sqf);
+            const int cf = (int)floorf(q - G.half);
+            float prev = trap_cdf_f((float)cf - q, G);
+            for (int k = 0; k < 4; ++k) {
+                const int c = cf + k;
+                if ((float)c >= q + G.half) break;
+                const float next = trap_cdf_f((float)(c + 1) - q, G);
+                const int ch = qi + c;
+                if (ch >= lo_v && ch < lo_v + len_v) acc[bo + ch] = fmaf(-G.scale * (next - prev), xs, acc[bo + ch]);
+                prev = next;
+            }
+        }
+    }
+    __syncwarp();
+    for (int f = lane; f < band_tot; f += 32) {
+        const float a = acc[f];
+        if (a != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, D)].x, a);
+    }
+}
+
 __global__ void pack_kernel(const float *__restrict__ y, const float *__restrict__ lam, const int *__restrict__ agent_view,
                             int B, int V, int D, float2 *__restrict__ eL, float *__restrict__ yg)
 {
@@ -851,6 +970,15 @@ static int launch_forward(mace_state *st)
     unsigned blocks = (unsigned)((items * 32 + 255) / 256);
     int64_t tot = (int64_t)st->B * st->ne;
     reset_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, tot);
+    if (st->P.forward_geometry) {
+        const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
+        cudaFuncSetAttribute(forward_geometry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        forward_geometry_kernel<<<blocks, 256, sm, st->stream>>>(M->d_vgeo, M->d_band, M->d_view_off, st->d_eL, st->d_X,
+                                                                 st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                                 M->geo.ny, M->geo.D, st->ne, M->max_band, M->max_views);
+        CUDA_TRY(cudaGetLastError());
+        return MACE_OK;
+    }
     switch (M->dtype) {
     case MACE_F32: launch_forward_t<float>(st, blocks); break;
     case MACE_BF16: launch_forward_t<__nv_bfloat16>(st, blocks); break;
@@ -1037,6 +1165,8 @@ static int check_params(const mace_params *P)
     if (P->chains != 0 && P->chains != 1 && P->chains != 2 && P->chains != 4)
         return fail(MACE_EINVAL, "chains must be 0, 1, 2 or 4");
     if (P->pnp != 0 && P->pnp != 1) return fail(MACE_EINVAL, "pnp must be 0 or 1");
+    if (P->forward_geometry != 0 && P->forward_geometry != 1)
+        return fail(MACE_EINVAL, "forward_geometry must be 0 or 1");
     if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
         return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
