@@ -496,6 +496,36 @@ def run_volume(args):
     }
 
 
+def run_autotune(args):
+    """The sweep-configuration autotuner on the benchmark's scans: for each
+    (super-voxel size, chains) a short probe of Mann iterations, timed, and
+    the iterations to tolerance extrapolated from the residual's rate."""
+    import torch
+    import synth
+    import paper_1911_09278_gb300 as mace
+    from paper_1911_09278_gb300 import autotune
+    from paper_1911_09278_gb300 import build as gbuild
+
+    gbuild.build()
+    torch.cuda.set_device(0)
+    y, lam = make_inputs(args.batch, 0)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    params = dict(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
+                  symmetric=True, recompute_every=args.recompute_every, max_iter=args.max_iter, tol=args.tol,
+                  concurrency=args.concurrency, sv_order=0, forward_geometry=forward_geometry(args))
+    best, table = autotune.tune(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"],
+                                WORKLOAD["n_agents"], y, lam, params, batch=args.batch, dtype=args.dtype,
+                                probe_iters=args.probe_iters)
+    for row in table:
+        row.pop("trajectory", None)
+        for k, v in row.items():
+            if isinstance(v, float) and not math.isfinite(v):
+                row[k] = None     # did not contract within the probe
+    pick = None if best is None else {"sv_size": best["sv_size"], "chains": best["chains"]}
+    return {"mode": "autotune", "workload": WORKLOAD["name"], "batch": args.batch, "sigma_normalised": args.sigma,
+            "rho": args.rho, "tol": args.tol, "probe_iters": args.probe_iters, "best": pick, "candidates": table}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -538,7 +568,14 @@ def main():
     ap.add_argument("--volume", action="store_true",
                     help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
     ap.add_argument("--slices", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true",
+                    help="rank super-voxel sizes and chains on the workload by estimated time to tolerance "
+                         "(its own JSON line)")
+    ap.add_argument("--probe-iters", dest="probe_iters", type=int, default=100)
     args = ap.parse_args()
+    if args.autotune:
+        print(json.dumps(run_autotune(args)))
+        return
     if args.volume:
         print(json.dumps(run_volume(args)))
         return
