@@ -1,7 +1,9 @@
 """Pins of the oracle's ICD and MACE against closed forms from the paper:
 Eq. ICDUpdate1 (one ICD pass is a Gauss-Seidel step), Eq. prox_exact,
 Lemma B.1, Theorem 1 (MACE fixed point = MAP), Theorem 2 (spectral radius),
-and the Q-GGMRF gradient against finite differences of the cost."""
+the Q-GGMRF gradient against finite differences of the cost, and the
+Q-GGMRF potential through its q = p special case (half the quadratic prior)
+and its growth exponents (p near zero, q far from it)."""
 import math
 
 import numpy as np
@@ -211,3 +213,43 @@ def test_qggmrf_central_icd_kkt():
     x, it, r = P.central_icd(max_sweeps=20000, tol=1e-14)
     g0 = np.linalg.norm(P.gradient(np.zeros(P.n)))
     assert np.linalg.norm(P.gradient(x)) / g0 < 1e-10
+
+
+def _prior_only(nx, ny, prior, q=1.2, T=1.0, sx=0.7):
+    """A problem whose weights are all zero: its cost is beta h(x) alone."""
+    V, D = 4, 9
+    z = np.zeros((V, D))
+    return oracle.Problem(nx, ny, V, D, z, z, n_agents=1, prior=prior, sigma_x=sx, q=q, T=T)
+
+
+def test_qggmrf_with_q_equal_p_is_half_the_quadratic_prior():
+    """With q = p = 2 the Q-GGMRF's edge factor is constant (1/2), so its
+    cost and gradient are half those of the quadratic prior (pinned above
+    against the dense B), over every neighbour pair of a ragged image."""
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(6 * 5)
+    Pq = _prior_only(6, 5, "qggmrf", q=2.0, T=0.5)
+    Pquad = _prior_only(6, 5, "quadratic")
+    assert Pquad.cost(x) > 0
+    assert Pq.cost(x) == pytest.approx(0.5 * Pquad.cost(x), rel=1e-13)
+    np.testing.assert_allclose(Pq.gradient(x), 0.5 * Pquad.gradient(x), rtol=1e-12, atol=1e-15)
+
+
+def test_qggmrf_potential_growth_exponents():
+    """The Q-GGMRF potential of one neighbour pair grows like |D|^p (p = 2,
+    low-contrast detail kept by a quadratic) for |D| << T sigma_x and like
+    |D|^q (q = 1.2, edges penalised less) for |D| >> T sigma_x; it is even,
+    zero at zero and increasing in |D|."""
+    sx, T, q = 0.7, 1.0, 1.2
+    P = _prior_only(2, 1, "qggmrf", q=q, T=T, sx=sx)
+
+    def h(d):
+        return P.cost(np.array([d, 0.0]))
+    assert h(0.0) == 0.0
+    assert h(-0.3) == pytest.approx(h(0.3), rel=1e-15)
+    small, large = 1e-6 * T * sx, 1e6 * T * sx
+    assert h(2 * small) / h(small) == pytest.approx(4.0, rel=1e-3)
+    assert h(2 * large) / h(large) == pytest.approx(2.0 ** q, rel=1e-3)
+    ds = np.geomspace(1e-3, 1e3, 61) * T * sx
+    vals = [h(d) for d in ds]
+    assert all(b > a for a, b in zip(vals, vals[1:]))
