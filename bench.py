@@ -547,7 +547,7 @@ def main():
                          "when the stored values are BF16/FP16)")
     ap.add_argument("--recompute-every", dest="recompute_every", type=int, default=DEFAULTS["recompute_every"],
                     help="Mann iterations between recomputations of e = y - A x")
-    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=700,
+    ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=670,
                     help="Mann iterations to tolerance the reference arm scales its sample to (the GPU path's count at the default settings)")
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
