@@ -421,6 +421,8 @@ def run_serve(args):
     served = srv.run(timed)
     worst = 0.0
     for r in reqs:
+        if r.rid not in served["results"] or r.rid not in serial["results"]:
+            continue      # failed in one of the modes: counted below
         a, b = served["results"][r.rid]["x"], serial["results"][r.rid]["x"]
         worst = max(worst, float(np.linalg.norm(a - b) / max(1e-30, np.linalg.norm(b))))
     conv = all(d["converged"] for d in served["results"].values())
@@ -433,6 +435,7 @@ def run_serve(args):
                    "p99_s": serial["p99"]},
         "speedup_vs_serial": served["recons_per_s"] / serial["recons_per_s"],
         "max_nrmse_served_vs_serial": worst, "converged": conv,
+        "failed": {"served": len(served["failed"]), "one_at_a_time": len(serial["failed"])},
         "dtype": args.serve_dtype + "-A/f32", "data": "synthetic",
         "config": {"workload": "stream of %d 2D requests, sizes %s, agents %s, Poisson arrivals at %.2f/s "
                                "(%gx one-at-a-time capacity)" % (len(reqs), SERVE_SIZES, SERVE_AGENTS, rate,

@@ -23,7 +23,7 @@ import time
 
 import numpy as np
 
-from . import (Sysmatrix, load, make_params, mace_build_sysmatrix, mace_init)  # noqa: F401
+from . import (MaceError, Sysmatrix, load, make_params, mace_build_sysmatrix, mace_init)  # noqa: F401
 
 Request = collections.namedtuple(
     "Request", "rid arrival nx ny n_views n_channels n_agents y lam sigma_x view_agent")
@@ -86,11 +86,14 @@ class Server:
     def run(self, requests, serial=False, now=time.perf_counter):
         """Serve `requests` (arrival times in seconds from the start).  With
         serial=True one request at a time (the plain GPU form).  Returns a dict
-        with per-request results and throughput / latency figures."""
+        with per-request results, `failed` (requests the library rejected or
+        that diverged, with the error; the others are served on) and
+        throughput / latency figures over the completed requests."""
         torch = self.torch
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         active = []
         done = {}
+        failed = {}     # requests the library rejected or that diverged
         t0 = now()
         while pending or active:
             t = now() - t0
@@ -105,16 +108,23 @@ class Server:
                 if held + need > self.budget and active:
                     break
                 pending.popleft()
-                sm = self._matrix(r)
-                stream = torch.cuda.Stream()
-                prm = make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
-                st = mace_init(sm, r.y, r.lam, prm, stream=stream)
-                # first chunk, its status copy, and the next chunk behind it
-                st.launch(self.chunk)
-                st.poll_async()
-                seen = self.chunk
-                if seen < self.max_iter:
+                st = None
+                try:
+                    sm = self._matrix(r)
+                    stream = torch.cuda.Stream()
+                    prm = make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
+                    st = mace_init(sm, r.y, r.lam, prm, stream=stream)
+                    # first chunk, its status copy, and the next chunk behind it
                     st.launch(self.chunk)
+                    st.poll_async()
+                    seen = self.chunk
+                    if seen < self.max_iter:
+                        st.launch(self.chunk)
+                except MaceError as e:
+                    failed[r.rid] = dict(error=str(e), code=e.code, finish=now() - t0)
+                    if st is not None:
+                        st.close()
+                    continue
                 active.append(dict(req=r, st=st, stream=stream, start=now() - t0, seen=seen,
                                    bytes=state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)))
             if not active:
@@ -125,32 +135,40 @@ class Server:
             progressed = False
             for a in active:
                 st = a["st"]
-                ready, r_, conv = st.poll_ready()
-                if not ready:
+                try:
+                    ready, r_, conv = st.poll_ready()
+                    if not ready:
+                        still.append(a)
+                        continue
+                    progressed = True
+                    if conv or a["seen"] >= self.max_iter:
+                        x = st.consensus()
+                        fin = now() - t0
+                        done[a["req"].rid] = dict(x=x, iters=st.stats()["iters"], residual=r_, converged=conv,
+                                                  latency=fin - a["req"].arrival, finish=fin,
+                                                  start=a["start"])
+                        st.close()
+                        continue
+                    # status of the chunk queued behind, then one more chunk
+                    st.poll_async()
+                    a["seen"] = st.stats()["iters"]
+                    if a["seen"] < self.max_iter:
+                        st.launch(self.chunk)
                     still.append(a)
-                    continue
-                progressed = True
-                if conv or a["seen"] >= self.max_iter:
-                    x = st.consensus()
-                    fin = now() - t0
-                    done[a["req"].rid] = dict(x=x, iters=st.stats()["iters"], residual=r_, converged=conv,
-                                              latency=fin - a["req"].arrival, finish=fin,
-                                              start=a["start"])
+                except MaceError as e:
+                    # divergence (non-finite residual), a timed-out wait or a
+                    # CUDA error: retire this request, keep serving the rest
+                    progressed = True
+                    failed[a["req"].rid] = dict(error=str(e), code=e.code, finish=now() - t0,
+                                                start=a["start"])
                     st.close()
-                    continue
-                # status of the chunk queued behind, then one more chunk
-                st.poll_async()
-                a["seen"] = st.stats()["iters"]
-                if a["seen"] < self.max_iter:
-                    st.launch(self.chunk)
-                still.append(a)
             active = still
             if not progressed:
                 time.sleep(0.0002)
         makespan = max(d["finish"] for d in done.values()) if done else 0.0
         lat = np.array([d["latency"] for d in done.values()])
         first = min(r.arrival for r in requests) if requests else 0.0
-        return dict(results=done, recons_per_s=len(done) / max(1e-9, makespan - first),
+        return dict(results=done, failed=failed, recons_per_s=len(done) / max(1e-9, makespan - first),
                     p50=float(np.percentile(lat, 50)) if len(lat) else None,
                     p99=float(np.percentile(lat, 99)) if len(lat) else None,
                     makespan=makespan)

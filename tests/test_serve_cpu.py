@@ -36,6 +36,8 @@ class FakeState:
         self.ready_calls += 1
         if self.ready_calls % 2:
             return False, 0.0, False
+        if self.conv_at == -1:
+            raise serve.MaceError(-6, "non-finite Mann residual (divergence)")
         r = 1e-9 if self.polled_at >= self.conv_at else 1.0
         return True, r, r < 1e-6
 
@@ -58,6 +60,8 @@ def fake_server(monkeypatch):
     active = {"now": 0, "max": 0}
 
     def fake_init(sm, y, lam, prm, stream=None):
+        if int(y[0, 0]) == -2:
+            raise serve.MaceError(-1, "y and weights must be finite and weights >= 0")
         st = FakeState(int(lam[0, 0]), int(y[0, 0]))
         active["now"] += 1
         active["max"] = max(active["max"], active["now"])
@@ -138,3 +142,16 @@ def test_max_iter_stops_an_unconverged_request(fake_server):
     assert not d["converged"]
     assert d["iters"] == 60
     assert out["results"][1]["converged"]
+
+
+def test_failed_requests_are_retired_and_the_rest_served(fake_server):
+    make, active = fake_server
+    srv = make(max_active=3, chunk=10)
+    # request 1 is rejected by mace_init, request 3 diverges on the GPU
+    out = srv.run(_requests([20, -2, 30, -1, 10]))
+    assert sorted(out["results"]) == [0, 2, 4]
+    assert sorted(out["failed"]) == [1, 3]
+    assert out["failed"][1]["code"] == -1 and out["failed"][3]["code"] == -6
+    for rid in (0, 2, 4):
+        assert out["results"][rid]["converged"]
+    assert active["now"] == 0          # every state that was made is closed
