@@ -542,7 +542,7 @@ def run_autotune(args):
             "rho": args.rho, "tol": args.tol, "probe_iters": args.probe_iters, "best": pick, "candidates": table}
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -588,7 +588,11 @@ def main():
                     help="rank super-voxel sizes and chains on the workload by estimated time to tolerance "
                          "(its own JSON line)")
     ap.add_argument("--probe-iters", dest="probe_iters", type=int, default=100)
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.autotune:
         print(json.dumps(run_autotune(args)))
         return

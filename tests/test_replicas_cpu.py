@@ -52,3 +52,4 @@ def test_reduce_max_without_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_max(3.0, None, "cpu") == 3.0
+
