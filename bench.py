@@ -42,6 +42,17 @@ WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 chan
                 n=512, n_views=720, n_channels=725, n_agents=16)
 
 
+def sweep_source_sha():
+    """sha256 of the ICD sweep kernel's source (the traffic counters in
+    profiles/ are only used for the kernel they were taken from)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("common.cuh", "sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_1911_09278_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -157,11 +168,16 @@ def forward_geometry(args):
     return args.forward == "geometry" or (args.forward == "auto" and args.dtype != "f32")
 
 
+def forward_param(args):
+    """The library's forward_geometry argument for --forward (None: its default)."""
+    return None if args.forward == "auto" else args.forward == "geometry"
+
+
 def solver_params(mace, sigma_x, args):
     return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=args.rho,
                             sweeps_per_iter=2, symmetric=True, recompute_every=args.recompute_every,
                             max_iter=args.max_iter, tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains,
-                            forward_geometry=forward_geometry(args))
+                            forward_geometry=forward_param(args))
 
 
 def run_mace(args, rank, world):
@@ -254,13 +270,17 @@ def run_mace(args, rank, world):
     e2e = recons / el_e2e
     hbm, peak_kind = peaks()
     # roofline of the ICD sweep kernel: algorithmic bytes per launch = the
-    # stored matrix once + per reconstruction the state it reads and writes
-    # (X read and written, w and theta2 read per agent and pixel, the FP64
-    # consensus, the error sinogram read and written once)
+    # stored matrix's content read once for the whole batch (its non-zero
+    # values, and one 16-bit run header (first channel, length) per (pixel,
+    # view)) + per reconstruction the state it reads and writes (X read and
+    # written, w and theta2 read per agent and pixel, the FP64 consensus, the
+    # error sinogram and weights read and written once)
     n = WORKLOAD["n"] ** 2
     N = WORKLOAD["n_agents"]
+    vbytes = 4 if args.dtype == "f32" else 2
+    matrix_bytes = info["nnz"] * vbytes + n * WORKLOAD["n_views"] * 2
     per_recon = N * n * (4 + 4 + 4 + 4) + n * 8 + 2 * WORKLOAD["n_views"] * WORKLOAD["n_channels"] * 8
-    alg_bytes = info["bytes_columns"] + B * per_recon
+    alg_bytes = matrix_bytes + B * per_recon
     avg_launch_s = (timing["ms"] / 1000.0) / max(1, timing["launches"])
     achieved = alg_bytes / avg_launch_s / 1e9 if timing["launches"] else None
     traffic = None
@@ -269,8 +289,9 @@ def run_mace(args, rank, world):
         try:
             with open(tf) as f:
                 tt = json.load(f)
+            # counters of this exact kernel source and launch configuration only
             if (tt.get("batch") == B and tt.get("sv") == args.sv and tt.get("dtype") == args.dtype
-                    and tt.get("chains") == args.chains):
+                    and tt.get("chains") == args.chains and tt.get("kernel_source_sha256") == sweep_source_sha()):
                 traffic = tt.get("bytes_per_launch")
         except Exception:
             pass
@@ -300,7 +321,9 @@ def run_mace(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind, "kernel": "icd_sweep_kernel",
-                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1000.0},
+                     "alg_bytes_per_launch": alg_bytes, "alg_matrix_bytes": matrix_bytes,
+                     "alg_state_bytes_per_recon": per_recon, "stored_matrix_bytes": info["bytes_columns"],
+                     "avg_launch_ms": avg_launch_s * 1000.0},
         "clocks": clocks,
     }
     # kernel launches inside one timed step: init (check, pack, consensus,
@@ -528,7 +551,7 @@ def run_autotune(args):
     sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
     params = dict(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
                   symmetric=True, recompute_every=args.recompute_every, max_iter=args.max_iter, tol=args.tol,
-                  concurrency=args.concurrency, sv_order=0, forward_geometry=forward_geometry(args))
+                  concurrency=args.concurrency, sv_order=0, forward_geometry=forward_param(args))
     best, table = autotune.tune(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"],
                                 WORKLOAD["n_agents"], y, lam, params, batch=args.batch, dtype=args.dtype,
                                 probe_iters=args.probe_iters)

@@ -109,9 +109,9 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   1 a stride permutation spreading consecutive super-voxels apart.
  *   Pixels inside a super-voxel are visited in raster order.
  *   chains: reconstructions of a batch one warp updates together, sharing
- *   every column load (0 or 1: one; 2 or 4: that many when they divide the
- *   batch; with 2 the warp works as two 16-lane halves, one per
- *   reconstruction).  Results do not depend on it.
+ *   every column load (0 or 1: one; 2 or 4: two when the batch is even, the
+ *   warp then working as two 16-lane halves, one per reconstruction).
+ *   Results do not depend on it.
  *   pnp: 0 = Algorithm 1 (the prior inside every agent, weight beta/N);
  *   1 = Algorithm 3 (Sec. III, MACE with a plug-and-play prior): the agents
  *   hold the data terms only and use proximal parameter sqrt(N) sigma; the
@@ -121,13 +121,14 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   one accepted with pnp = 1, 8-neighbourhood), solved in FP64 by Jacobi
  *   iterations to round-off.  H is firmly non-expansive, so by Theorem 3 and
  *   Lemma 2 the fixed point is the MAP image of the whole cost.
- *   forward_geometry: 0 = the periodic recompute e_i = y_i - A_i X_i (and
- *   the initial one) reads A_i from the stored columns; 1 = it evaluates
- *   A_i's strip-integral footprints from the geometry (the super-voxel's
- *   projection in FP64, the rest in FP32), so with BF16/FP16 stored values
- *   the recompute still sees the exact projector.  The ICD updates keep
- *   using the stored values; the fixed point then matches the exact MAP
- *   image more closely than that of the rounded matrix. */
+ *   forward_geometry: how the periodic recompute e_i = y_i - A_i X_i (and
+ *   the initial one) gets A_i.  1 = it evaluates A_i's strip-integral
+ *   footprints from the geometry (the super-voxel's projection in FP64, the
+ *   rest in FP32), so with BF16/FP16 stored values the recompute still sees
+ *   the exact projector; 2 = it reads the stored values; 0 (default) = 1
+ *   for BF16/FP16 stored values, 2 for FP32.  The ICD updates keep using
+ *   the stored values; with the geometry recompute the fixed point matches
+ *   the exact MAP image more closely than that of the rounded matrix. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -161,10 +162,14 @@ typedef struct {
 /* Build the stored system matrix (the paper precomputes and stores A,
  * Sec. I and Table 3) for every agent: voxel-column-major per super-voxel
  * (sv_size x sv_size pixel tiles), per view a run (first channel, length
- * 0..3, values).  dtype selects the stored value type.  Runs on the GPU on
- * cuda_stream (a cudaStream_t or NULL).  *out receives the handle.
- * Errors: MACE_EINVAL (sizes, angles, partition, sv_size not 4, 8 or 16,
- * more than 4096 views), MACE_ENOMEM, MACE_ECUDA. */
+ * 0..3, values): one header byte per (pixel, view) holding the run's length
+ * and its first channel relative to the super-voxel's band in that view,
+ * the first two values per view, and the third values of three-channel runs
+ * in a short list.  dtype selects the stored value type.  Runs on the GPU
+ * on cuda_stream (a cudaStream_t or NULL).  *out receives the handle.
+ * Errors: MACE_EINVAL (sizes, angles, partition, sv_size not 4, 8, 16 or
+ * 32, more than 4096 views, a super-voxel band wider than 62 channels in a
+ * view), MACE_ENOMEM, MACE_ECUDA. */
 int mace_build_sysmatrix(const mace_geometry *geom, const mace_partition *part,
                          mace_dtype dtype, int32_t sv_size, void *cuda_stream,
                          mace_sysmatrix **out);
@@ -187,7 +192,8 @@ int mace_sysmatrix_column(const mace_sysmatrix *sm, int32_t g, int32_t i, int32_
  * ordered on cuda_stream.  All arrays of a state below carry the leading
  * batch dimension.
  * Errors: MACE_EINVAL (batch not in [1, 4096], parameters out of range,
- * non-finite or negative weights), MACE_ENOMEM, MACE_ECUDA. */
+ * non-finite or negative weights, more than 128 views in an agent),
+ * MACE_ENOMEM, MACE_ECUDA. */
 int mace_init(const mace_sysmatrix *sm, int32_t batch, const float *y, const float *weights,
               int32_t ptr_is_device, const mace_params *params, const float *w0,
               void *cuda_stream, mace_state **out);

@@ -21,26 +21,32 @@ static constexpr uint32_t kSpinLimit = 1u << 26;  // bounded device waits
 static constexpr int kStatusTimeout = 1;
 
 // --- stored column format ----------------------------------------------------
-// Column of one pixel for one agent (the per-view runs, flattened):
-//   u32 nnz; u16 bidx[nnz]   (position of each value in the super-voxel's band:
-//                             runs of the agent's views in view order)
-//   zero padding to 16 bytes; T vals[nnz]; zero padding to 16 bytes.
-// The 4-byte header puts entries (2k, 2k+1) of bidx in one aligned u32 and of
-// vals in one aligned 8-byte (FP32) or 4-byte (BF16/FP16) word, so one lane
-// loads a pair with two instructions.  For odd nnz the pair's second half is
-// padding: index 0, value 0.
-// View v's band covers channels [lo_v, lo_v + len_v) and starts at
-// boff_v = sum_{u < v} len_u, so the value of channel c sits at
-// boff_v + c - lo_v: the run (first channel, length, values) of every view is
-// recoverable from bidx and the band descriptors.
-__host__ __device__ inline uint32_t col_idx_bytes(int nnz)
+// Column of one pixel for one agent with Vg views: the per-view runs (first
+// channel, run length <= 3, values) of the paper's stored matrix, laid out so
+// that lane l of a warp can take view l:
+//   u16 n3                        views whose run has three channels
+//   u8  hdr[Vg]                   per view: r | L << 6, with L the run length
+//                                 (0..3) and r = c0 - lo the first channel
+//                                 relative to the super-voxel's band of that
+//                                 view (0 when L = 0)
+//   (pad to 8 bytes)  T v01[Vg][2] the run's first two values (zero past L)
+//   u16 ovc[n3]                   the views with L = 3, each coded as
+//                                 (r + 2) * vpad + v: the band position
+//                                 (row r + 2, view v) of the third value
+//   (pad to 4 bytes)  T ov[n3]    their third values
+//   (zero padding to 16 bytes)
+// The value the run stores for channel lo_v + r + k is v01[v][k] (k < 2) or
+// the matching ov entry (k = 2).  vpad (the view stride of a band row) is a
+// property of the matrix: the number of views of its largest agent rounded
+// up to a multiple of 16.
+__host__ __device__ inline int col_v01(int Vg) { return (2 + Vg + 7) & ~7; }
+__host__ __device__ inline int col_ovc(int Vg, int vb) { return col_v01(Vg) + 2 * vb * Vg; }
+__host__ __device__ inline int col_ovv(int Vg, int vb, int n3) { return (col_ovc(Vg, vb) + 2 * n3 + 3) & ~3; }
+__host__ __device__ inline uint32_t col_bytes(int Vg, int vb, int n3)
 {
-    return (4u + 2u * (uint32_t)nnz + 15u) & ~15u;
+    return (uint32_t)((col_ovv(Vg, vb, n3) + n3 * vb + 15) & ~15);
 }
-__host__ __device__ inline uint32_t col_bytes_of(int nnz, int vbytes)
-{
-    return col_idx_bytes(nnz) + (((uint32_t)nnz * vbytes + 15u) & ~15u);
-}
+static constexpr int kMaxRunOff = 63;   // r is stored in 6 bits
 
 template <typename T> __device__ __forceinline__ float ld_val(const uint8_t *p, int idx);
 template <> __device__ __forceinline__ float ld_val<float>(const uint8_t *p, int idx) { return ((const float *)p)[idx]; }
@@ -53,7 +59,7 @@ template <> __device__ __forceinline__ float ld_val<__half>(const uint8_t *p, in
     return __half2float(((const __half *)p)[idx]);
 }
 
-// values 2k and 2k+1 of a column's value array, widened to float
+// values 2k and 2k+1 of a value array, widened to float
 template <typename T> __device__ __forceinline__ float2 ld_pair(const uint8_t *p, int k);
 template <> __device__ __forceinline__ float2 ld_pair<float>(const uint8_t *p, int k) { return ((const float2 *)p)[k]; }
 template <> __device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const uint8_t *p, int k)
@@ -110,6 +116,30 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
         : "memory");
 }
 
+// L2 policy for data read once per pass (the stored matrix): evicted first,
+// so the small state every super-voxel re-reads (e, Lambda, X, w, theta2)
+// stays in L2 while the matrix streams through
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// The same, armed and issued by lane 0 of the warp only (predicated, so the
+// warp does not diverge around it), with an L2 cache policy
+__device__ __forceinline__ void tma_load_1d_lane0(void *dst, const void *src, uint32_t bytes, uint64_t *bar, int lane,
+                                                  uint64_t policy)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.eq.u32 p, %4, 0;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%3], %2;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %5;\n\t}"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "r"((uint32_t)lane), "l"(policy)
+        : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -118,84 +148,46 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// the same with 32-bit shared-window destination addresses
+__device__ __forceinline__ void cp_async4_s(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8_s(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ float lds_f32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, float2 v)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// --- super-voxel band bookkeeping ---------------------------------------------
-// Shared by the kernels that walk a super-voxel's columns: per view the band
-// descriptor, its offset in the flattened band and, per band entry, its view.
-// Returns the band size.  Warp-cooperative.  bd may point to global or shared
-// memory; bdesc may alias bd.
-__device__ __forceinline__ int load_band_layout(const uint32_t *bd, int Vg, uint32_t *bdesc,
-                                                uint16_t *boff, uint16_t *bview, int lane)
+// --- super-voxel band in shared memory ----------------------------------------
+// The kernels that walk a super-voxel's columns keep its band of the agent's
+// sinogram as rows t = 0 .. wmax-1 of vpad views: entry (t, v) is channel
+// lo_v + t of view v, for t < len_v (band descriptor lo_v | len_v << 16), and
+// otherwise a spare that no channel maps to.  A run (r, L) of view v touches
+// rows r .. r + L - 1; wmax is the widest band plus one, so row r + 1 always
+// exists.
+__host__ __device__ inline size_t aux_warp_bytes(int vpad, int wmax)
 {
-    const unsigned FULL = 0xffffffffu;
-    int run = 0;
-    for (int r = 0; r * 32 < Vg; ++r) {
-        const int v = r * 32 + lane;
-        const uint32_t d = v < Vg ? bd[v] : 0u;
-        const int len = (int)(d >> 16);
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (v < Vg) {
-            const int b0 = run + incl - len;
-            boff[v] = (uint16_t)b0;
-            bdesc[v] = d;
-            for (int k = 0; k < len; ++k) bview[b0 + k] = (uint16_t)v;
-        }
-        run += __shfl_sync(FULL, incl, 31);
-    }
-    __syncwarp();
-    return run;
-}
-
-// The same bookkeeping with, per band entry, its index in the agent block
-// ([Vg][D]) instead of its view, so loading and flushing the band need one
-// shared-memory read per entry.  Returns the band size.  Warp-cooperative.
-__device__ __forceinline__ int load_band_index(const uint32_t *bd, int Vg, int D, uint32_t *bdesc,
-                                               uint32_t *bglob, int lane)
-{
-    const unsigned FULL = 0xffffffffu;
-    int run = 0;
-    for (int r = 0; r * 32 < Vg; ++r) {
-        const int v = r * 32 + lane;
-        const uint32_t d = v < Vg ? bd[v] : 0u;
-        const int len = (int)(d >> 16);
-        int incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (v < Vg) {
-            const int b0 = run + incl - len;
-            bdesc[v] = d;
-            const uint32_t g0 = (uint32_t)v * (uint32_t)D + (d & 0xFFFFu);
-            for (int k = 0; k < len; ++k) bglob[b0 + k] = g0 + (uint32_t)k;
-        }
-        run += __shfl_sync(FULL, incl, 31);
-    }
-    __syncwarp();
-    return run;
-}
-
-// global index (row of the agent block, [Vg][D]) of band entry f
-__device__ __forceinline__ int64_t band_global(int f, const uint32_t *bdesc, const uint16_t *boff,
-                                               const uint16_t *bview, int D)
-{
-    const int v = bview[f];
-    return (int64_t)v * D + (int)(bdesc[v] & 0xFFFFu) + (f - boff[v]);
-}
-
-// Per-warp shared memory of the kernels that walk columns outside the sweep:
-// band descriptors, offsets, entry views and one float per band entry.
-__host__ __device__ inline size_t aux_warp_bytes(int max_band, int max_views)
-{
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    return r16((size_t)max_views * 4) + r16((size_t)max_views * 2) + r16((size_t)max_band * 2) +
-           r16((size_t)max_band * 4);
+    return ((size_t)vpad * 4 + 15) / 16 * 16 + ((size_t)wmax * vpad * 4 + 15) / 16 * 16;
 }

@@ -11,13 +11,13 @@
 //                      ||w^(k+1) - w^(k)||^2 and ||w^(k+1)||^2.
 //
 // The stored system matrix is voxel-column-major per super-voxel (an SxS tile
-// of pixels): for every agent, super-voxel and pixel, a column listing the
-// pixel's non-zeros as (position in the super-voxel's band of the agent's
-// sinogram, value) pairs; the format is in common.cuh.  One warp owns one
-// super-voxel at a time (sweep.cuh): it stages the super-voxel's band of the
-// agent's error sinogram e_i and weights Lambda_i in shared memory, streams
-// the columns in with TMA bulk copies into a per-warp ring, visits the pixels
-// in order, and flushes its change of e back to global memory at the end.
+// of pixels): for every agent, super-voxel and pixel, a column holding the
+// pixel's run (first channel, length, values) in each of the agent's views;
+// the format is in common.cuh.  One warp owns one super-voxel at a time
+// (sweep.cuh): it stages the super-voxel's band of the agent's error sinogram
+// e_i and weights Lambda_i in shared memory, streams the columns in with TMA
+// bulk copies into a per-warp ring, visits the pixels in order, and adds its
+// change of e back to global memory at the end.
 // This file holds the matrix builder, the other kernels and the host side.
 #include <string.h>
 #include <math.h>
@@ -136,7 +136,8 @@ struct mace_sysmatrix {
     GeoParams geo;
     int nz;
     int V, N, S, nsvx, nsvy, nsv, S2;
-    int max_views, max_band, max_col_bytes, max_nnz = 0;
+    int max_views, max_col_bytes, max_n3 = 0;
+    int vpad, wmax;                   // band rows in shared memory: vpad views, wmax rows
     mace_dtype dtype;
     int vbytes;                       // bytes per stored value
     cudaStream_t stream;
@@ -149,7 +150,6 @@ struct mace_sysmatrix {
     ViewGeo *d_vgeo = nullptr;        // footprint constants per view in agent order
     int *d_view_off = nullptr;        // [N+1]
     uint32_t *d_band = nullptr;       // [nsv * V]: agent g block at nsv*view_off[g], (lo | len << 16)
-    uint32_t *d_band_tot = nullptr;   // [N * nsv]
     int64_t *d_sv_base = nullptr;     // [N * nsv] byte offset of the super-voxel block
     uint32_t *d_col_off = nullptr;    // [N * nsv * (S2 + 1)] byte offsets inside the block
     uint8_t *d_cols = nullptr;
@@ -190,7 +190,8 @@ __global__ void band_kernel(GeoParams G, const double2 *__restrict__ cs, const i
 
 __global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
                                int N, int S, int nsvx, int nsv, int vbytes,
-                               uint32_t *__restrict__ col_bytes, uint32_t *__restrict__ col_nnz)
+                               uint32_t *__restrict__ col_bytes_out, uint32_t *__restrict__ col_nnz,
+                               uint32_t *__restrict__ col_n3)
 {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int S2 = S * S;
@@ -200,15 +201,18 @@ __global__ void colsize_kernel(GeoParams G, const double2 *__restrict__ cs, cons
     int sv = rem / S2, t = rem % S2;
     int si = sv / nsvx, sj = sv % nsvx;
     int i = si * S + t / S, j = sj * S + t % S;
-    if (i >= G.ny || j >= G.nx) { col_bytes[tid] = 0; col_nnz[tid] = 0; return; }
+    if (i >= G.ny || j >= G.nx) { col_bytes_out[tid] = 0; col_nnz[tid] = 0; col_n3[tid] = 0; return; }
     int v0 = view_off[g], Vg = view_off[g + 1] - v0;
-    int nz = 0;
+    int nz = 0, n3 = 0;
     for (int v = 0; v < Vg; ++v) {
         int c0;
-        nz += footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr);
+        const int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr);
+        nz += L;
+        n3 += L == 3;
     }
-    col_bytes[tid] = col_bytes_of(nz, vbytes);
+    col_bytes_out[tid] = col_bytes(Vg, vbytes, n3);
     col_nnz[tid] = nz;
+    col_n3[tid] = n3;
 }
 
 template <typename T> __device__ __forceinline__ T from_double(double x);
@@ -218,10 +222,11 @@ template <> __device__ __forceinline__ __half from_double<__half>(double x) { re
 
 template <typename T>
 __global__ void fill_kernel(GeoParams G, const double2 *__restrict__ cs, const int *__restrict__ view_off,
-                            int N, int S, int nsvx, int nsv, const uint32_t *__restrict__ band,
+                            int N, int S, int nsvx, int nsv, int vpad, const uint32_t *__restrict__ band,
                             const int64_t *__restrict__ sv_base, const uint32_t *__restrict__ col_off,
                             uint8_t *__restrict__ cols)
 {
+    // one thread per column; the buffer is zeroed beforehand (padding)
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int S2 = S * S;
     if (tid >= (int64_t)N * nsv * S2) return;
@@ -235,26 +240,31 @@ __global__ void fill_kernel(GeoParams G, const double2 *__restrict__ cs, const i
     const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
     int64_t gsv = (int64_t)g * nsv + sv;
     uint8_t *col = cols + sv_base[gsv] + col_off[gsv * (S2 + 1) + t];
-    uint16_t *bidx = (uint16_t *)col;
-    int nz = 0, boff = 0;
+    const int vb = (int)sizeof(T);
+    // pass 1: the three-channel count fixes where the third values go
+    int n3 = 0;
     for (int v = 0; v < Vg; ++v) {
-        double a[3];
         int c0;
-        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
-        int lo = (int)(bd[v] & 0xFFFFu);
-        for (int k = 0; k < L; ++k) bidx[2 + nz + k] = (uint16_t)(boff + c0 - lo + k);
-        nz += L;
-        boff += (int)(bd[v] >> 16);
+        n3 += footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, nullptr) == 3;
     }
-    *(uint32_t *)col = (uint32_t)nz;
-    T *vals = (T *)(col + col_idx_bytes(nz));
-    nz = 0;
+    *(uint16_t *)col = (uint16_t)n3;
+    T *v01 = (T *)(col + col_v01(Vg));
+    uint16_t *ovc = (uint16_t *)(col + col_ovc(Vg, vb));
+    T *ov = (T *)(col + col_ovv(Vg, vb, n3));
+    int k3 = 0;
     for (int v = 0; v < Vg; ++v) {
         double a[3];
         int c0;
-        int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
-        for (int k = 0; k < L; ++k) vals[nz + k] = from_double<T>(a[k]);
-        nz += L;
+        const int L = footprint_dev(G, cs[v0 + v].x, cs[v0 + v].y, i, j, c0, a);
+        const int r = L > 0 ? c0 - (int)(bd[v] & 0xFFFFu) : 0;
+        col[2 + v] = (uint8_t)(r | L << 6);
+        v01[2 * v] = from_double<T>(L > 0 ? a[0] : 0.0);
+        v01[2 * v + 1] = from_double<T>(L > 1 ? a[1] : 0.0);
+        if (L == 3) {
+            ovc[k3] = (uint16_t)((r + 2) * vpad + v);
+            ov[k3] = from_double<T>(a[2]);
+            ++k3;
+        }
     }
 }
 
@@ -284,7 +294,8 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
     if (rc) return rc;
     if (!part || part->n_agents < 1 || part->n_agents > geom->n_views)
         return fail(MACE_EINVAL, "n_agents must be in [1, n_views]");
-    if (sv_size != 4 && sv_size != 8 && sv_size != 16) return fail(MACE_EINVAL, "sv_size must be 4, 8 or 16");
+    if (sv_size != 4 && sv_size != 8 && sv_size != 16 && sv_size != 32)
+        return fail(MACE_EINVAL, "sv_size must be 4, 8, 16 or 32");
     if (dtype != MACE_F32 && dtype != MACE_BF16 && dtype != MACE_F16)
         return fail(MACE_EINVAL, "unknown dtype");
 
@@ -362,7 +373,6 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
         cudaMalloc(&M->d_cs, sizeof(double2) * M->V) != cudaSuccess ||
         cudaMalloc(&M->d_view_off, sizeof(int) * (M->N + 1)) != cudaSuccess ||
         cudaMalloc(&M->d_band, sizeof(uint32_t) * nband) != cudaSuccess ||
-        cudaMalloc(&M->d_band_tot, sizeof(uint32_t) * M->N * M->nsv) != cudaSuccess ||
         cudaMalloc(&M->d_sv_base, sizeof(int64_t) * M->N * M->nsv) != cudaSuccess ||
         cudaMalloc(&M->d_col_off, sizeof(uint32_t) * M->N * M->nsv * (M->S2 + 1)) != cudaSuccess)
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for system-matrix metadata");
@@ -373,29 +383,32 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
 
     band_kernel<<<(unsigned)((nband + 255) / 256), 256, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S,
                                                                M->nsvx, M->nsv, M->d_band);
-    uint32_t *d_bytes = nullptr, *d_nnz = nullptr;
+    uint32_t *d_bytes = nullptr, *d_nnz = nullptr, *d_n3 = nullptr;
     if (cudaMalloc(&d_bytes, sizeof(uint32_t) * ncol) != cudaSuccess ||
-        cudaMalloc(&d_nnz, sizeof(uint32_t) * ncol) != cudaSuccess) {
+        cudaMalloc(&d_nnz, sizeof(uint32_t) * ncol) != cudaSuccess ||
+        cudaMalloc(&d_n3, sizeof(uint32_t) * ncol) != cudaSuccess) {
         cudaFree(d_bytes);
+        cudaFree(d_nnz);
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for column sizes");
     }
     colsize_kernel<<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S,
-                                                                  M->nsvx, M->nsv, M->vbytes, d_bytes, d_nnz);
-    std::vector<uint32_t> h_bytes(ncol), h_nnz(ncol), h_band(nband);
+                                                                  M->nsvx, M->nsv, M->vbytes, d_bytes, d_nnz, d_n3);
+    std::vector<uint32_t> h_bytes(ncol), h_nnz(ncol), h_n3(ncol), h_band(nband);
     cudaError_t ce = cudaMemcpyAsync(h_bytes.data(), d_bytes, sizeof(uint32_t) * ncol, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_nnz.data(), d_nnz, sizeof(uint32_t) * ncol, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_n3.data(), d_n3, sizeof(uint32_t) * ncol, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_band.data(), M->d_band, sizeof(uint32_t) * nband, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     cudaFree(d_bytes);
     cudaFree(d_nnz);
+    cudaFree(d_n3);
     if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix size pass: ") + cudaGetErrorString(ce));
 
     // offsets (host prefix sums; a one-off cost per geometry)
     std::vector<int64_t> sv_base(M->N * M->nsv);
     std::vector<uint32_t> col_off((int64_t)M->N * M->nsv * (M->S2 + 1));
-    std::vector<uint32_t> band_tot(M->N * M->nsv);
     int64_t total = 0;
-    M->max_band = 0;
+    int max_len = 1;
     M->max_col_bytes = 16;
     M->agent_bytes.assign(M->N, 0);
     for (int g = 0; g < M->N; ++g) {
@@ -409,41 +422,41 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
                 uint32_t b = h_bytes[gsv * M->S2 + t];
                 off += b;
                 M->max_col_bytes = std::max<int>(M->max_col_bytes, (int)b);
-                M->max_nnz = std::max<int>(M->max_nnz, (int)h_nnz[gsv * M->S2 + t]);
+                M->max_n3 = std::max<int>(M->max_n3, (int)h_n3[gsv * M->S2 + t]);
                 M->nnz += h_nnz[gsv * M->S2 + t];
             }
             col_off[gsv * (M->S2 + 1) + M->S2] = off;
             total += off;
             M->agent_bytes[g] += off;
-            uint32_t bt = 0;
             const uint32_t *bd = h_band.data() + (int64_t)M->nsv * M->view_off[g] + (int64_t)sv * Vg;
-            for (int v = 0; v < Vg; ++v) {
-                uint32_t len = bd[v] >> 16;
-                if (len > 128) return cleanup(MACE_EINVAL, "super-voxel band wider than 128 channels; use a smaller sv_size");
-                bt += len;
-            }
-            band_tot[gsv] = bt;
-            if (bt > 65535) return cleanup(MACE_EINVAL, "super-voxel band larger than 65535 entries; use a smaller sv_size");
-            M->max_band = std::max<int>(M->max_band, (int)bt);
+            for (int v = 0; v < Vg; ++v) max_len = std::max(max_len, (int)(bd[v] >> 16));
         }
     }
+    // band rows: one spare past the widest band (a run's second entry may sit
+    // there); run offsets are stored in 6 bits
+    if (max_len > kMaxRunOff - 1)
+        return cleanup(MACE_EINVAL, "super-voxel band wider than 62 channels in a view; use a smaller sv_size");
+    M->wmax = max_len + 1;
+    M->vpad = (M->max_views + 15) & ~15;
+    if ((int64_t)M->vpad * M->wmax > 65535)
+        return cleanup(MACE_EINVAL, "super-voxel band of an agent larger than 65535 entries; use fewer views per agent");
     M->bytes_cols = total;
     if (cudaMalloc(&M->d_cols, total > 0 ? total : 16) != cudaSuccess)
         return cleanup(MACE_ENOMEM, "cudaMalloc failed for the system matrix (" + std::to_string(total) + " bytes)");
     ce = cudaMemcpyAsync(M->d_sv_base, sv_base.data(), sizeof(int64_t) * sv_base.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_col_off, col_off.data(), sizeof(uint32_t) * col_off.size(), cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(M->d_band_tot, band_tot.data(), sizeof(uint32_t) * band_tot.size(), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(M->d_cols, 0, total > 0 ? total : 16, s);
     if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix upload: ") + cudaGetErrorString(ce));
+    const unsigned fb = (unsigned)((ncol + 127) / 128);
     if (M->dtype == MACE_F32)
-        fill_kernel<float><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
-                                                                          M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+        fill_kernel<float><<<fb, 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv, M->vpad,
+                                              M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
     else if (M->dtype == MACE_BF16)
-        fill_kernel<__nv_bfloat16><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
-                                                                                  M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+        fill_kernel<__nv_bfloat16><<<fb, 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
+                                                      M->vpad, M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
     else
-        fill_kernel<__half><<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv,
-                                                                           M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
+        fill_kernel<__half><<<fb, 128, 0, s>>>(M->geo, M->d_cs, M->d_view_off, M->N, M->S, M->nsvx, M->nsv, M->vpad,
+                                               M->d_band, M->d_sv_base, M->d_col_off, M->d_cols);
     ce = cudaStreamSynchronize(s);
     if (ce == cudaSuccess) ce = cudaGetLastError();
     if (ce != cudaSuccess) return cleanup(MACE_ECUDA, std::string("system-matrix build: ") + cudaGetErrorString(ce));
@@ -462,7 +475,7 @@ extern "C" int mace_sysmatrix_get_info(const mace_sysmatrix *M, mace_sysmatrix_i
     info->max_views = M->max_views;
     info->nnz = M->nnz;
     info->bytes_columns = M->bytes_cols;
-    info->bytes_meta = (int64_t)M->nsv * M->V * 4 + (int64_t)M->N * M->nsv * (8 + 4 + 4 * (M->S2 + 1));
+    info->bytes_meta = (int64_t)M->nsv * M->V * 4 + (int64_t)M->N * M->nsv * (8 + 4 * (M->S2 + 1));
     for (int g = 0; g < M->N && g < 64; ++g) info->agent_bytes[g] = M->agent_bytes[g];
     return MACE_OK;
 }
@@ -503,21 +516,33 @@ extern "C" int mace_sysmatrix_column(const mace_sysmatrix *M, int32_t g, int32_t
         CUDA_TRY(cudaMemcpy(col.data(), M->d_cols + base + off[0], col.size(), cudaMemcpyDeviceToHost));
     for (int v = 0; v < Vg; ++v) { c0[v] = 0; len[v] = 0; vals[3 * v] = vals[3 * v + 1] = vals[3 * v + 2] = 0.f; }
     if (col.empty()) return MACE_OK;
-    uint32_t nz;
-    memcpy(&nz, col.data(), 4);
-    const uint8_t *vals_p = col.data() + col_idx_bytes((int)nz);
-    std::vector<int> boff(Vg + 1, 0);
-    for (int v = 0; v < Vg; ++v) boff[v + 1] = boff[v] + (int)(bd[v] >> 16);
-    for (int k = 0; k < (int)nz; ++k) {
-        uint16_t b;
-        memcpy(&b, col.data() + 4 + 2 * k, 2);
-        int v = (int)(std::upper_bound(boff.begin(), boff.end(), (int)b) - boff.begin()) - 1;
-        int ch = (int)(bd[v] & 0xFFFFu) + (b - boff[v]);
-        if (len[v] == 0) c0[v] = ch;
-        if (len[v] >= 3 || ch != c0[v] + len[v]) return fail(MACE_EINVAL, "stored column is not a set of runs");
-        vals[3 * v + len[v]] = value_to_float(vals_p + (size_t)k * M->vbytes, M->dtype);
-        len[v]++;
+    const int vb = M->vbytes;
+    uint16_t n3;
+    memcpy(&n3, col.data(), 2);
+    if (col_bytes(Vg, vb, n3) != col.size()) return fail(MACE_EINVAL, "stored column has an inconsistent size");
+    const uint8_t *v01 = col.data() + col_v01(Vg);
+    const uint8_t *ovc = col.data() + col_ovc(Vg, vb);
+    const uint8_t *ov = col.data() + col_ovv(Vg, vb, n3);
+    int k3 = 0;
+    for (int v = 0; v < Vg; ++v) {
+        const int hb = col[2 + v], r = hb & 63, L = hb >> 6;
+        len[v] = L;
+        if (L == 0) continue;
+        const int lo = (int)(bd[v] & 0xFFFFu), blen = (int)(bd[v] >> 16);
+        if (r + L > blen) return fail(MACE_EINVAL, "stored run leaves its super-voxel band");
+        c0[v] = lo + r;
+        vals[3 * v] = value_to_float(v01 + (size_t)(2 * v) * vb, M->dtype);
+        if (L > 1) vals[3 * v + 1] = value_to_float(v01 + (size_t)(2 * v + 1) * vb, M->dtype);
+        if (L == 3) {
+            uint16_t code;
+            memcpy(&code, ovc + 2 * k3, 2);
+            if (k3 >= n3 || code != (uint16_t)((r + 2) * M->vpad + v))
+                return fail(MACE_EINVAL, "stored three-channel list does not match the runs");
+            vals[3 * v + 2] = value_to_float(ov + (size_t)k3 * vb, M->dtype);
+            ++k3;
+        }
     }
+    if (k3 != n3) return fail(MACE_EINVAL, "stored three-channel list does not match the runs");
     return MACE_OK;
 }
 
@@ -528,7 +553,6 @@ extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
     cudaFree(M->d_vgeo);
     cudaFree(M->d_view_off);
     cudaFree(M->d_band);
-    cudaFree(M->d_band_tot);
     cudaFree(M->d_sv_base);
     cudaFree(M->d_col_off);
     cudaFree(M->d_cols);
@@ -666,24 +690,49 @@ __global__ void residual_kernel(const double *__restrict__ part, int nblk, int B
 }
 
 // --- error sinogram: e = y - A X ---------------------------------------------
+// Per-warp shared memory of the kernels below: the super-voxel's band
+// descriptors and one float per band entry (rows of vpad views).
+struct AuxSmem {
+    uint32_t *bdesc;
+    float *acc;
+};
+__device__ __forceinline__ AuxSmem aux_smem(uint8_t *smem, int vpad, int wmax)
+{
+    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(vpad, wmax);
+    AuxSmem a;
+    a.bdesc = (uint32_t *)base;
+    a.acc = (float *)(base + ((size_t)vpad * 4 + 15) / 16 * 16);
+    return a;
+}
+
+// Adds each band entry's accumulated value to the agent's e.  Lane l takes
+// views l, l + 32, ...
+__device__ __forceinline__ void flush_band(const AuxSmem &a, int Vg, int vpad, int D, float2 *eLg, int lane)
+{
+    for (int v = lane; v < Vg; v += 32) {
+        const uint32_t d = a.bdesc[v];
+        const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
+        for (int t = 0; t < len; ++t) {
+            const float x = a.acc[t * vpad + v];
+            if (x != 0.f) atomicAdd(&eLg[(int64_t)v * D + lo + t].x, x);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                                       const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                                                       const int *__restrict__ view_off, float2 *__restrict__ eL,
                                                       const float *__restrict__ X, int B, int N, int nsv, int nsvx, int S,
-                                                      int nx, int ny, int D, int64_t ne, int max_band, int max_views)
+                                                      int nx, int ny, int D, int64_t ne, int vpad, int wmax)
 {
     // one warp per (reconstruction, agent, super-voxel): accumulate -A x over
     // the super-voxel's columns in its band, then add the band to e (which
-    // holds y on entry)
+    // holds y on entry).  Lane l takes the runs of views l, l + 32, ... and
+    // entries l, l + 32, ... of the three-channel list.
     extern __shared__ __align__(16) uint8_t smem[];
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
-    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
-    uint32_t *bdesc = (uint32_t *)base;
-    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
-    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
-    float *acc = (float *)((uint8_t *)bview + r16((size_t)max_band * 2));
+    const AuxSmem a = aux_smem(smem, vpad, wmax);
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv);
@@ -693,10 +742,11 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint8_t *svcols = cols + sv_base[gsv];
     const uint32_t *coff = col_off + gsv * (S2 + 1);
-    float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
     const float *Xg = X + (int64_t)pair * nx * ny;
-    const int band_tot = load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
-    for (int f = lane; f < band_tot; f += 32) acc[f] = 0.f;
+    const int vb = (int)sizeof(T), v01 = col_v01(Vg), ovc = col_ovc(Vg, vb);
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    for (int v = lane; v < Vg; v += 32) a.bdesc[v] = bd[v];
+    for (int f = lane; f < wmax * vpad; f += 32) a.acc[f] = 0.f;
     __syncwarp();
     for (int t = 0; t < S2; ++t) {
         if (coff[t + 1] == coff[t]) continue;
@@ -704,19 +754,21 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
         const float xs = Xg[(int64_t)i * nx + j];
         if (xs == 0.f) continue;
         const uint8_t *col = svcols + coff[t];
-        const uint16_t *cidx = (const uint16_t *)col;
-        const int nnz = cidx[0];
-        const uint8_t *cval = col + col_idx_bytes(nnz);
-        for (int k = lane; k < nnz; k += 32) {
-            const int bb = cidx[2 + k];
-            acc[bb] = fmaf(-ld_val<T>(cval, k), xs, acc[bb]);
+        const int n3 = *(const uint16_t *)col;
+        for (int v = lane; v < Vg; v += 32) {
+            const int r = col[2 + v] & 63;
+            const float2 av = ld_pair<T>(col + v01, v);
+            a.acc[r * vpad + v] = fmaf(-av.x, xs, a.acc[r * vpad + v]);
+            a.acc[(r + 1) * vpad + v] = fmaf(-av.y, xs, a.acc[(r + 1) * vpad + v]);
+        }
+        const uint8_t *ov = col + col_ovv(Vg, vb, n3);
+        for (int k = lane; k < n3; k += 32) {
+            const int code = ((const uint16_t *)(col + ovc))[k];
+            a.acc[code] = fmaf(-ld_val<T>(ov, k), xs, a.acc[code]);
         }
         __syncwarp();
     }
-    for (int f = lane; f < band_tot; f += 32) {
-        const float a = acc[f];
-        if (a != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, D)].x, a);
-    }
+    flush_band(a, Vg, vpad, D, eL + (int64_t)b * ne + (int64_t)v0 * D, lane);
 }
 
 // The same product with A evaluated from the geometry instead of read from
@@ -745,39 +797,33 @@ __device__ __forceinline__ float trap_cdf_f(float u, const ViewGeo &G)
 
 __global__ void __launch_bounds__(256) forward_geometry_kernel(const ViewGeo *__restrict__ vgeo,
                                                                const uint32_t *__restrict__ band,
-                                                               const int *__restrict__ view_off, float2 *__restrict__ eL,
+                                                               const int *__restrict__ view_off,
+                                                               float2 *__restrict__ eL,
                                                                const float *__restrict__ X, int B, int N, int nsv, int nsvx,
-                                                               int S, int nx, int ny, int D, int64_t ne, int max_band,
-                                                               int max_views)
+                                                               int S, int nx, int ny, int D, int64_t ne, int vpad, int wmax)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
-    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
-    uint32_t *bdesc = (uint32_t *)base;
-    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
-    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
-    float *acc = (float *)((uint8_t *)bview + r16((size_t)max_band * 2));
+    const AuxSmem a = aux_smem(smem, vpad, wmax);
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv);
     const int b = pair / N, g = pair - b * N;
     const int i0 = (sv / nsvx) * S, j0 = (sv % nsvx) * S, S2 = S * S;
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
-    float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
     const float *Xg = X + (int64_t)pair * nx * ny;
-    const int band_tot = load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
-    for (int f = lane; f < band_tot; f += 32) acc[f] = 0.f;
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    for (int v = lane; v < Vg; v += 32) a.bdesc[v] = bd[v];
+    for (int f = lane; f < wmax * vpad; f += 32) a.acc[f] = 0.f;
     __syncwarp();
     for (int v = lane; v < Vg; v += 32) {
-        const int lo_v = (int)(bdesc[v] & 0xFFFFu), len_v = (int)(bdesc[v] >> 16);
+        const int lo_v = (int)(a.bdesc[v] & 0xFFFFu), len_v = (int)(a.bdesc[v] >> 16);
         if (len_v == 0) continue;
         const ViewGeo G = vgeo[v0 + v];
         const double q0 = fma((double)j0, G.cq, fma(-(double)i0, G.sq, G.q00));
         const double qb = floor(q0);
         const int qi = (int)qb;
         const float qf = (float)(q0 - qb), cqf = (float)G.cq, sqf = (float)G.sq;
-        const int bo = (int)boff[v] - lo_v;
         for (int t = 0; t < S2; ++t) {
             const int ti = t / S, tj = t - ti * S;
             if (i0 + ti >= ny || j0 + tj >= nx) continue;
@@ -791,16 +837,16 @@ __global__ void __launch_bounds__(256) forward_geometry_kernel(const ViewGeo *__
                 if ((float)c >= q + G.half) break;
                 const float next = trap_cdf_f((float)(c + 1) - q, G);
                 const int ch = qi + c;
-                if (ch >= lo_v && ch < lo_v + len_v) acc[bo + ch] = fmaf(-G.scale * (next - prev), xs, acc[bo + ch]);
+                if (ch >= lo_v && ch < lo_v + len_v) {
+                    float *ap = &a.acc[(ch - lo_v) * vpad + v];
+                    *ap = fmaf(-G.scale * (next - prev), xs, *ap);
+                }
                 prev = next;
             }
         }
     }
     __syncwarp();
-    for (int f = lane; f < band_tot; f += 32) {
-        const float a = acc[f];
-        if (a != 0.f) atomicAdd(&eLg[band_global(f, bdesc, boff, bview, D)].x, a);
-    }
+    flush_band(a, Vg, vpad, D, eL + (int64_t)b * ne + (int64_t)v0 * D, lane);
 }
 
 __global__ void pack_kernel(const float *__restrict__ y, const float *__restrict__ lam, const int *__restrict__ agent_view,
@@ -842,11 +888,12 @@ __global__ void check_weights_kernel(const float *__restrict__ y, const float *_
     if (!isfinite(a) || !isfinite(b) || b < 0.f) atomicOr(bad, 1);
 }
 
+template <typename T>
 __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                               const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                               const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
-                              int nsvx, int S, int nx, int ny, int D, int64_t ne, int dtype, int max_band,
-                              int max_views, float *__restrict__ theta2, double *__restrict__ total)
+                              int nsvx, int S, int nx, int ny, int D, int64_t ne, int vpad, int wmax,
+                              float *__restrict__ theta2, double *__restrict__ total)
 {
     // theta2[b][g][s] = sum_{k in J_g} A_ks^2 Lambda_k (the data term of the
     // coordinate curvature in Algorithm 2, constant over the iterations),
@@ -854,12 +901,8 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
     // column.  total += the FP64 sum over everything (for the normalised
     // sigma).  One warp per (b, agent, super-voxel).
     extern __shared__ __align__(16) uint8_t smem[];
-    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const int lane = threadIdx.x & 31;
-    uint8_t *base = smem + (threadIdx.x >> 5) * aux_warp_bytes(max_band, max_views);
-    uint32_t *bdesc = (uint32_t *)base;
-    uint16_t *boff = (uint16_t *)(base + r16((size_t)max_views * 4));
-    uint16_t *bview = (uint16_t *)((uint8_t *)boff + r16((size_t)max_views * 2));
+    const AuxSmem a = aux_smem(smem, vpad, wmax);
     const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= (int64_t)B * N * nsv) return;
     const int pair = (int)(item / nsv), sv = (int)(item % nsv), S2 = S * S;
@@ -868,9 +911,12 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
     const int v0 = view_off[g], Vg = view_off[g + 1] - v0;
     const int64_t gsv = (int64_t)g * nsv + sv;
     const uint32_t *coff = col_off + gsv * (S2 + 1);
-    const float2 *eLg = eL + (int64_t)b * ne + (int64_t)v0 * D;
+    const float2 *lg = eL + (int64_t)b * ne + (int64_t)v0 * D;
     float *t2g = theta2 + (int64_t)pair * nx * ny;
-    load_band_layout(band + (int64_t)nsv * v0 + (int64_t)sv * Vg, Vg, bdesc, boff, bview, lane);
+    const int vb = (int)sizeof(T), v01 = col_v01(Vg), ovc = col_ovc(Vg, vb);
+    const uint32_t *bd = band + (int64_t)nsv * v0 + (int64_t)sv * Vg;
+    for (int v = lane; v < Vg; v += 32) a.bdesc[v] = bd[v];
+    __syncwarp();
     double sum = 0.0;
     for (int t = 0; t < S2; ++t) {
         const int i = si * S + t / S, j = sj * S + t % S;
@@ -878,12 +924,20 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
         double acc = 0.0;
         if (coff[t + 1] != coff[t]) {
             const uint8_t *col = cols + sv_base[gsv] + coff[t];
-            const uint16_t *cidx = (const uint16_t *)col;
-            const int nnz = cidx[0];
-            const uint8_t *cval = col + col_idx_bytes(nnz);
-            for (int k = lane; k < nnz; k += 32) {
-                const float a = ld_any(cval, k, dtype);
-                acc += (double)a * a * eLg[band_global(cidx[2 + k], bdesc, boff, bview, D)].y;
+            const int n3 = *(const uint16_t *)col;
+            for (int v = lane; v < Vg; v += 32) {
+                const int hb = col[2 + v], r = hb & 63, L = hb >> 6;
+                const float2 av = ld_pair<T>(col + v01, v);
+                const int64_t e0 = (int64_t)v * D + (a.bdesc[v] & 0xFFFFu) + r;
+                if (L > 0) acc += (double)av.x * av.x * lg[e0].y;
+                if (L > 1) acc += (double)av.y * av.y * lg[e0 + 1].y;
+            }
+            const uint8_t *ov = col + col_ovv(Vg, vb, n3);
+            for (int k = lane; k < n3; k += 32) {
+                const int code = ((const uint16_t *)(col + ovc))[k];
+                const int v = code % vpad, row = code / vpad;
+                const float a2 = ld_val<T>(ov, k);
+                acc += (double)a2 * a2 * lg[(int64_t)v * D + (a.bdesc[v] & 0xFFFFu) + row].y;
             }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         }
@@ -955,11 +1009,11 @@ template <typename T>
 static void launch_forward_t(mace_state *st, unsigned blocks)
 {
     const mace_sysmatrix *M = st->M;
-    const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
+    const size_t sm = 8 * aux_warp_bytes(M->vpad, M->wmax);
     cudaFuncSetAttribute(forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     forward_kernel<T><<<blocks, 256, sm, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
                                                        st->d_eL, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
-                                                       M->geo.ny, M->geo.D, st->ne, M->max_band, M->max_views);
+                                                       M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax);
 }
 
 // e_i = y_i - A_i X_i for every reconstruction and agent
@@ -970,12 +1024,15 @@ static int launch_forward(mace_state *st)
     unsigned blocks = (unsigned)((items * 32 + 255) / 256);
     int64_t tot = (int64_t)st->B * st->ne;
     reset_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, tot);
-    if (st->P.forward_geometry) {
-        const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
+    // forward_geometry 0 (auto): from the geometry when the stored values are
+    // rounded (BF16/FP16), from the stored values when they are FP32
+    const bool geo = st->P.forward_geometry == 1 || (st->P.forward_geometry == 0 && M->dtype != MACE_F32);
+    if (geo) {
+        const size_t sm = 8 * aux_warp_bytes(M->vpad, M->wmax);
         cudaFuncSetAttribute(forward_geometry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         forward_geometry_kernel<<<blocks, 256, sm, st->stream>>>(M->d_vgeo, M->d_band, M->d_view_off, st->d_eL, st->d_X,
                                                                  st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
-                                                                 M->geo.ny, M->geo.D, st->ne, M->max_band, M->max_views);
+                                                                 M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax);
         CUDA_TRY(cudaGetLastError());
         return MACE_OK;
     }
@@ -991,9 +1048,9 @@ static int launch_forward(mace_state *st)
 static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26)
 {
     switch (M->dtype) {
-    case MACE_F32: return mace_sweep_kernel_f32(M->max_nnz, M->S, K, nb26);
-    case MACE_BF16: return mace_sweep_kernel_bf16(M->max_nnz, M->S, K, nb26);
-    default: return mace_sweep_kernel_f16(M->max_nnz, M->S, K, nb26);
+    case MACE_F32: return mace_sweep_kernel_f32(M->max_views, K, nb26);
+    case MACE_BF16: return mace_sweep_kernel_bf16(M->max_views, K, nb26);
+    default: return mace_sweep_kernel_f16(M->max_views, K, nb26);
     }
 }
 
@@ -1021,24 +1078,28 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.nx = M->geo.nx;
     A.ny = M->geo.ny;
     A.D = M->geo.D;
+    A.S = M->S;
     A.ne = st->ne;
     A.backward = backward;
-    A.max_band = M->max_band;
+    A.vpad = M->vpad;
+    A.wmax = M->wmax;
     A.col_stride = (M->max_col_bytes + 15) & ~15;
-    A.max_views = M->max_views;
     A.inv_s2 = (float)(1.0 / (st->sigma_abs * st->sigma_abs));
     A.pscale = st->P.pnp ? 0.f : (float)(st->P.beta / (double)M->N);
     if (st->P.pnp)   // data-only agents with proximal parameter sqrt(N) sigma (Algorithm 3)
         A.inv_s2 = (float)(1.0 / ((double)M->N * st->sigma_abs * st->sigma_abs));
-    A.prior = st->P.prior;
-    A.inv_sx2 = (float)(1.0 / (st->P.sigma_x * st->P.sigma_x));
-    A.inv_Tsx = (float)(1.0 / (st->P.T * st->P.sigma_x));
-    A.qexp = (float)(st->P.p - st->P.q);
-    A.half_q_inv_sx2 = (float)(0.5 * st->P.q / (st->P.sigma_x * st->P.sigma_x));
+    // prior weight constants: the quadratic prior runs the Q-GGMRF formula
+    // with a = 0 (inv_Tsx = 0); a Q-GGMRF with q = p = 2 is the quadratic
+    // rho(D) = D^2 / (4 sigma_x^2)
+    const double isx2 = 1.0 / (st->P.sigma_x * st->P.sigma_x);
+    const bool qg = st->P.prior == 1 && st->P.q < st->P.p;
+    A.inv_sx2 = (float)((st->P.prior == 1 && !qg) ? 0.5 * isx2 : isx2);
+    A.inv_Tsx = qg ? (float)(1.0 / (st->P.T * st->P.sigma_x)) : 0.f;
+    A.qexp = qg ? (float)(st->P.p - st->P.q) : 1.f;
+    A.half_q_inv_sx2 = qg ? (float)(0.5 * st->P.q * isx2) : 0.f;
     double bsum = 4.0 + 4.0 / std::sqrt(2.0);
     A.b_edge = (float)(1.0 / bsum);
     A.b_diag = (float)((1.0 / std::sqrt(2.0)) / bsum);
-    A.nb26 = st->P.neighbourhood == 26;
     double b3 = 6.0 + 12.0 / std::sqrt(2.0) + 8.0 / std::sqrt(3.0);
     A.b26[0] = (float)(1.0 / b3);
     A.b26[1] = (float)(1.0 / std::sqrt(2.0) / b3);
@@ -1070,26 +1131,20 @@ static int configure_sweep(mace_state *st)
     // the sweep addresses columns in 16-byte units with 32 bits
     if (M->bytes_cols >= ((int64_t)1 << 36)) return fail(MACE_EINVAL, "stored matrix larger than 64 GiB");
     // chains per warp: reconstructions of the batch that share each column
-    // load (a divisor of the batch; 1 when the columns are not cached)
-    int K = 1;
-    if ((M->max_nnz + 63) / 64 <= 3 && M->S != 16 && st->P.neighbourhood != 26) {
-        // one chain unless asked: sharing the column between chains saves
-        // column traffic but costs registers and shared memory, and measured
-        // slower on the 512^2 workload
-        const int want = st->P.chains > 0 ? st->P.chains : 1;
-        for (int k : {4, 2})
-            if (k <= want && st->B % k == 0) { K = k; break; }
-    }
+    // load (two when asked and the batch is even; volumes run one)
+    const bool nb26 = st->P.neighbourhood == 26;
+    int K = (st->P.chains >= 2 && st->B % 2 == 0 && !nb26) ? 2 : 1;
     sweep_fn fn = nullptr;
     for (;;) {
-        st->warp_smem = warp_smem_layout(M->max_band, col_stride, M->S, M->max_views, K,
-                                         st->P.neighbourhood == 26).total;
-        fn = sweep_kernel_ptr(M, K, st->P.neighbourhood == 26);
+        st->warp_smem = warp_smem_layout(M->vpad, M->wmax, col_stride, M->S, K, nb26).total;
+        const int R = sweep_rounds(M->max_views, K);
+        const bool ovf_ok = M->max_n3 <= sweep_ovf_rounds(R, K) * (32 / K);
+        fn = ovf_ok ? sweep_kernel_ptr(M, K, nb26) : nullptr;
         if (fn && st->warp_smem <= (size_t)max_smem) break;
         if (K == 1) break;
-        K /= 2;
+        K = 1;
     }
-    if (!fn) return fail(MACE_EINVAL, "unsupported super-voxel size");
+    if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix (more than 128 views per agent)");
     if (st->warp_smem > (size_t)max_smem)
         return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
     st->chains = K;
@@ -1165,8 +1220,8 @@ static int check_params(const mace_params *P)
     if (P->chains != 0 && P->chains != 1 && P->chains != 2 && P->chains != 4)
         return fail(MACE_EINVAL, "chains must be 0, 1, 2 or 4");
     if (P->pnp != 0 && P->pnp != 1) return fail(MACE_EINVAL, "pnp must be 0 or 1");
-    if (P->forward_geometry != 0 && P->forward_geometry != 1)
-        return fail(MACE_EINVAL, "forward_geometry must be 0 or 1");
+    if (P->forward_geometry < 0 || P->forward_geometry > 2)
+        return fail(MACE_EINVAL, "forward_geometry must be 0, 1 or 2");
     if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
         return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
@@ -1309,7 +1364,8 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_status, 0, sizeof(int), s);
     if (ce == cudaSuccess) {
         check_weights_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, m, st->d_status);
-        pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, d_av, batch, M->V, M->geo.D, st->d_eL, st->d_y);
+        pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(d_yin, d_lin, d_av, batch, M->V, M->geo.D, st->d_eL,
+                                                                st->d_y);
         ce = cudaMemcpyAsync(&bad, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -1327,12 +1383,27 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
         if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_theta2, 0, sizeof(float) * NN, s);
         if (ce == cudaSuccess) {
             int64_t items = (int64_t)batch * M->N * M->nsv;
-            const size_t sm = 8 * aux_warp_bytes(M->max_band, M->max_views);
-            cudaFuncSetAttribute(theta2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            theta2_kernel<<<(unsigned)((items * 32 + 255) / 256), 256, sm, s>>>(
-                M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off, st->d_eL, batch, M->N, M->nsv,
-                M->nsvx, M->S, M->geo.nx, M->geo.ny, M->geo.D, st->ne, (int)M->dtype, M->max_band, M->max_views,
-                st->d_theta2, d_t2);
+            const size_t sm = 8 * aux_warp_bytes(M->vpad, M->wmax);
+            const unsigned tb = (unsigned)((items * 32 + 255) / 256);
+            if (M->dtype == MACE_F32) {
+                cudaFuncSetAttribute(theta2_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                theta2_kernel<float><<<tb, 256, sm, s>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band,
+                                                         M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->nsvx, M->S,
+                                                         M->geo.nx, M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax,
+                                                         st->d_theta2, d_t2);
+            } else if (M->dtype == MACE_BF16) {
+                cudaFuncSetAttribute(theta2_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                theta2_kernel<__nv_bfloat16><<<tb, 256, sm, s>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band,
+                                                                 M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->nsvx,
+                                                                 M->S, M->geo.nx, M->geo.ny, M->geo.D, st->ne, M->vpad,
+                                                                 M->wmax, st->d_theta2, d_t2);
+            } else {
+                cudaFuncSetAttribute(theta2_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                theta2_kernel<__half><<<tb, 256, sm, s>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band,
+                                                          M->d_view_off, st->d_eL, batch, M->N, M->nsv, M->nsvx, M->S,
+                                                          M->geo.nx, M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax,
+                                                          st->d_theta2, d_t2);
+            }
             ce = cudaGetLastError();
             if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
         }

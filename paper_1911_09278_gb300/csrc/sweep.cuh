@@ -2,6 +2,25 @@
 // coordinate descent for the proximal map F_i(v_i; sigma), Eq. "ICDUpdate1")
 // for every agent of every reconstruction of a batch, over the stored system
 // matrix.  Instantiated per stored value type in sweep_<type>.cu.
+//
+// Work decomposition.  C warps serve each (batch group, agent) pair and stay
+// resident; warp c takes the super-voxels c, c+C, c+2C, ... of the visiting
+// order, so about C super-voxels of one agent are in flight.  A warp runs K
+// chains: K reconstructions of the batch that share every column load (K = 2:
+// two 16-lane halves, one per reconstruction).  Inside a chain, lane l owns
+// the agent's views l, l + 32/K, l + 64/K, ...: for each pixel it reads its
+// views' runs from the column (one header byte and the first two values per
+// view), gathers their (e, Lambda) band entries, and after the step writes
+// them back; the third values of three-channel runs form a short list that
+// the lanes share.
+//
+// The super-voxel's band of (e, Lambda) lives in shared memory as rows t of
+// vpad views, chains interleaved: entry (t, v) of chain k at float2 index
+// (t vpad + v) K + k.  Lanes of one round touch views 16 apart in bank space,
+// so a gather is conflict-free whatever the runs' offsets.  Columns stream in
+// through a per-warp ring of TMA bulk copies; each column is decoded into
+// registers one pixel ahead, so its slot is refilled at once and the next
+// pixel's gathers only wait for the current pixel's update.
 #pragma once
 
 #include "common.cuh"
@@ -13,76 +32,63 @@ struct SweepArgs {
     const uint32_t *band;
     const int *view_off;
     const int32_t *sv_order;
-    float2 *eL;
+    float2 *eL;                 // [B][V][D] (e, Lambda): error sinogram and weights
     float *X;
     const float *w;
     const double *wbar;
     const float *vexp;
     const float *theta2;        // [B][N][n]: sum over the agent's views of A_js^2 Lambda_j
     int *status;
-    int B, N, nsv, nsvx, nx, ny, D;
+    int B, N, nsv, nsvx, nx, ny, D, S;
     int64_t ne;
     int nwarps;                 // warps with work (the last block may have idle ones)
     int backward;
-    int max_band, col_stride, max_views;   // per-warp shared-memory layout (S is a template parameter)
+    int vpad, wmax, col_stride;
     float inv_s2, pscale;
-    int prior;                  // 0 quadratic, 1 Q-GGMRF
-    float inv_sx2, inv_Tsx, qexp, half_q_inv_sx2;   // prior constants
+    float inv_sx2, inv_Tsx, qexp, half_q_inv_sx2;   // prior constants (quadratic: inv_Tsx = 0)
     float b_edge, b_diag;       // 8-neighbourhood weights (face, diagonal)
-    int nb26;                   // 1: the batch is the z-stack of one volume, 26-neighbourhood prior
     float b26[3];               // 26-neighbourhood weights by squared distance 1, 2, 3
 };
 
 typedef void (*sweep_fn)(SweepArgs);
 
-// Per-warp shared-memory layout (bytes, each part 16-aligned).  Shared by
-// the warp's K chains (reconstructions of one batch group that run the same
-// agent over the same super-voxels, so every column is loaded once for all):
-//   ring:   kRing * col_stride            column staging (TMA destination)
-//   bars:   kRing * 8                     mbarriers
-//   bdesc:  2 * max_views * 4             band descriptors (lo | len << 16), current and next super-voxel
-//   bglob:  max_band * 4                  index of each band entry in the agent block [Vg][D]
-//   coff:   (S^2 + 1) * 4                 column byte offsets of the next super-voxel (staging)
-//   pl:     2 * S^2 * 4                   per visited pixel: tile index | neighbour mask << 9
-//   cl:     2 * S^2 * 8                   per visited pixel: (column offset from the matrix start
-//                                         in 16-byte units, bytes)
-//   halo:   2 * (S+2)^2 * 4               X tiles of the slices below and above (volumes only)
-// and per chain:
-//   beL:    (max_band + 1) * 8            (e, Lambda) of the band, e kept current; the last
-//                                         entry takes the stores of lanes past a column's end
-//   bsnap:  max_band * 4                  e of the band when the super-voxel began
-//   xt:     (S+2)^2 * 4                   X tile with one-pixel halo
-//   vt2:    S^2 * 8                       per visited pixel (v / sigma^2, theta2 + 1 / sigma^2)
+// Per-warp shared-memory layout (bytes, each part 16-aligned):
+//   ring:   kRing * col_stride          column staging (TMA destination)
+//   bars:   kRing * 8                   mbarriers
+//   bdesc:  2 * vpad * 4                band descriptors (lo | len << 16), current and next super-voxel
+//   coff:   (S^2 + 1) * 4               column byte offsets of the next super-voxel (staging)
+//   pl:     2 * S^2 * 4                 per visited pixel: tile index | neighbour mask << 11
+//                                       | pixel offset in the super-voxel << 20
+//   cl:     2 * S^2 * 8                 per visited pixel: (column offset in 16-byte units, bytes)
+//   halo:   2 * (S+2)^2 * 4             X tiles of the slices below and above (volumes only)
+//   band:   (wmax vpad K + 1) * 8       (e, Lambda), chains interleaved; the last entry is a
+//                                       sink that idle lanes read and write with value 0
+//   snap:   K wmax vpad * 4             e of the band when the super-voxel began
+//   xt:     K (S+2)^2 * 4               X tiles with a one-pixel halo
+//   vt2:    K S^2 * 8                   per visited pixel (v / sigma^2, theta2 + 1 / sigma^2)
 struct WarpSmem {
-    size_t ring, bars, bdesc, bglob, coff, pl, cl, halo, chain0, chain_size;
-    size_t beL, bsnap, xt, vt2;
+    size_t ring, bars, bdesc, coff, pl, cl, halo, band, snap, xt, vt2;
     size_t total;
 };
 
-__host__ __device__ inline WarpSmem warp_smem_layout(int max_band, int col_stride, int S, int max_views, int K,
-                                                     int halo)
+__host__ __device__ inline WarpSmem warp_smem_layout(int vpad, int wmax, int col_stride, int S, int K, bool halo)
 {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t S2 = (size_t)S * S, TA = (size_t)(S + 2) * (S + 2);
-    if (max_band < 1) max_band = 1;   // the gathers may read band entry 0
     WarpSmem L;
     size_t o = 0;
     L.ring = o;  o += r16((size_t)kRing * col_stride);
     L.bars = o;  o += r16(kRing * 8);
-    L.bdesc = o; o += r16((size_t)2 * max_views * 4);
-    L.bglob = o; o += r16((size_t)max_band * 4);
+    L.bdesc = o; o += r16((size_t)2 * vpad * 4);
     L.coff = o;  o += r16((S2 + 1) * 4);
     L.pl = o;    o += r16(2 * S2 * 4);
     L.cl = o;    o += r16(2 * S2 * 8);
     L.halo = o;  o += halo ? r16(2 * TA * 4) : 0;
-    L.chain0 = o;
-    size_t c = 0;
-    L.beL = c;   c += r16((size_t)(max_band + 1) * 8);   // + a sink entry for masked-off stores
-    L.bsnap = c; c += r16((size_t)max_band * 4);
-    L.xt = c;    c += r16(TA * 4);
-    L.vt2 = c;   c += r16(S2 * 8);
-    L.chain_size = c;
-    L.total = o + (size_t)K * c;
+    L.band = o;  o += r16(((size_t)wmax * vpad * K + 1) * 8);
+    L.snap = o;  o += r16((size_t)K * wmax * vpad * 4);
+    L.xt = o;    o += r16((size_t)K * TA * 4);
+    L.vt2 = o;   o += r16((size_t)K * S2 * 8);
+    L.total = o;
     return L;
 }
 
@@ -109,65 +115,98 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
-// Surrogate weight rho'(D)/D of the prior potential (quadratic: 1/sigma_x^2;
-// Q-GGMRF with p = 2: (2 + q a) / (2 sigma_x^2 (1 + a)^2), a = |D/(T sigma_x)|^(p-q),
-// the power taken as 2^((p-q) log2 |D/(T sigma_x)|); a = 0 at D = 0).
+// Surrogate weight rho'(D)/D of the prior potential (Q-GGMRF with p = 2:
+// (2 + q a) / (2 sigma_x^2 (1 + a)^2), a = |D/(T sigma_x)|^(p-q), the power
+// taken as 2^((p-q) log2 |D/(T sigma_x)|), a = 0 at D = 0).  Branch-free:
+// the quadratic prior (weight 1/sigma_x^2) runs the same arithmetic with
+// inv_Tsx = 0, so a = 0.
 __device__ __forceinline__ float prior_weight(const SweepArgs &A, float d)
 {
-    if (A.prior == 0) return A.inv_sx2;
     const float a = ex2_approx(A.qexp * lg2_approx(fabsf(d * A.inv_Tsx)));
     const float r = rcp_approx(1.f + a);
     return fmaf(A.half_q_inv_sx2, a, A.inv_sx2) * r * r;
 }
 
-// Register cap of the one-chain sweep kernel: residency is limited by
-// registers and shared memory together, and at 96 registers (21 warps per SM)
-// the one-chain kernels do not spill; two-chain kernels are capped at 128
-// (16 warps per SM), four-chain kernels keep their registers.
+__device__ __forceinline__ float2 lds_f2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_f(uint32_t a, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// One column decoded for one lane: for each owned view j the shared address
+// of its run's first band entry (the second is one band row further) and
+// the two values; for each share of the three-channel list the address and
+// value of its third entry.  Idle lanes carry value 0: a share points at
+// the sink, a view at entry (wmax - 1, 0) of chain 0, whose next row is the
+// sink.  Row wmax - 1 holds no channel of any view (wmax is the widest band
+// plus one), so every write there stores back the value read.
+template <int R, int RO>
+struct ColRegs {
+    uint32_t addr[R];
+    float a0[R], a1[R];
+    uint32_t oaddr[RO];
+    float a2[RO];
+};
+// The raw words of a column as read from its ring slot, before decoding.
+template <int R, int RO>
+struct ColRaw {
+    uint32_t hb[R];
+    float2 a[R];
+    uint32_t code[RO];
+    float a2[RO];
+    int n3;
+};
+
+// Register cap: 128 keeps 16 warps per SM (shared memory allows about as
+// many on the benchmark's configuration) without spills.
 #ifndef MACE_SWEEP_MAXNREG
-#define MACE_SWEEP_MAXNREG 96
+#define MACE_SWEEP_MAXNREG 128
 #endif
 
-// One warp runs K chains (reconstructions b0 .. b0+K-1 of one batch group,
-// all on agent g) over a fixed sequence of super-voxels: slots c, c+C, c+2C,
-// ... of the visiting order, where C warps serve the same (group, agent) -- so
-// about C super-voxels of one agent of one reconstruction are in flight at a
-// time.  Inside a super-voxel the pixels are visited in order; each pixel's
-// column (a flat list of (band position, value) pairs) is streamed once by
-// TMA for all K chains.  With one or four chains lane k takes the pairs k,
-// k+32, ... for every chain (PR rounds: at most 64*PR entries; PR == 0: any
-// count, one chain); with two chains the warp works as two 16-lane halves,
-// half h updating chain h and taking the pairs hl, hl+16, ... (PR rounds of
-// 16 lanes: at most 32*PR entries).  Pairs stay in registers between the
-// reduction and the update, and the ring slot is refilled once they have been
-// consumed.  The next super-voxel's metadata, visiting list and first columns
-// are prepared while the current one is processed.
-// NB26: the batch is the z-stack of one volume, 26-neighbourhood prior (K = 1).
-template <typename T, int PR, int S, int K, bool NB26>
-__global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) icd_sweep_kernel(SweepArgs A)
+// R: rounds of views per lane (R * 32/K >= the agent's views); RO: rounds of
+// the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
+// z-stack of one volume, 26-neighbourhood prior (K = 1).
+template <typename T, int K, int R, int RO, bool NB26>
+__global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    constexpr int S2 = S * S, TS = S + 2, TA = TS * TS;
-    static_assert(PR > 0 || K == 1, "uncached columns support one chain");
+    static_assert(K == 1 || K == 2, "one or two chains per warp");
     static_assert(!NB26 || K == 1, "volumes run one chain per warp");
-    static_assert((kRing & (kRing - 1)) == 0, "ring size is a power of two");
+    static_assert((kRing & (kRing - 1)) == 0 && kRing >= 3, "ring size is a power of two >= 4");
+    constexpr int LPC = 32 / K;                 // lanes per chain
+    constexpr int vb = (int)sizeof(T);
+    const int S = A.S, S2 = S * S, TS = S + 2, TA = TS * TS;
+    const int lS = 31 - __clz(S);               // S is a power of two
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.max_band, A.col_stride, S, A.max_views, K, NB26);
+    const WarpSmem Ly = warp_smem_layout(A.vpad, A.wmax, A.col_stride, S, K, NB26);
     uint8_t *base = smem + wib * Ly.total;
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
     uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
-    uint32_t *bglob = (uint32_t *)(base + Ly.bglob);
     uint32_t *scoff = (uint32_t *)(base + Ly.coff);
     uint32_t *pl2 = (uint32_t *)(base + Ly.pl);
     uint2 *cl2 = (uint2 *)(base + Ly.cl);
-    uint8_t *chains = base + Ly.chain0;
     float *halo_lo = (float *)(base + Ly.halo);
     float *halo_hi = halo_lo + TA;
+    float2 *band = (float2 *)(base + Ly.band);
+    float *snap = (float *)(base + Ly.snap);
+    float *xt0 = (float *)(base + Ly.xt);
+    float2 *vt20 = (float2 *)(base + Ly.vt2);
 
+    const int vpad = A.vpad, wmax = A.wmax;
+    const int nrow = wmax * vpad;               // band entries of one chain
     if (lane == 0)
         for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
+    // the whole band starts at zero: entries outside a super-voxel's band
+    // (spares) are only ever read and written with matrix value 0, so they
+    // stay finite whatever a previous super-voxel left there
+    for (int f = lane; f <= nrow * K; f += 32) band[f] = make_float2(0.f, 0.f);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncwarp();
 
@@ -182,14 +221,35 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
     const int grp = pair / A.N, g = pair - grp * A.N;
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
     const int Cw = A.nwarps / (G * A.N);
-    auto chain = [&](int k) { return chains + (size_t)k * Ly.chain_size; };
 
-    // this lane's prior neighbour: lanes 0..7 the in-plane 8-neighbourhood,
-    // or (volumes) lanes 0..25 the 26-neighbourhood; other lanes read the
-    // pixel itself with weight 0.  mbit: the neighbour's bit in a pixel's
-    // 3x3 in-image mask.  With two chains the warp works as two 16-lane
-    // halves (half h: chain h), each with its own lanes 0..7.
-    const int plane_lane = K == 2 ? (lane & 15) : lane;
+    // lane roles in the pixel loop: chain h, index hl inside the chain's lanes
+    const int h = K == 2 ? (lane >> 4) : 0;
+    const int hl = K == 2 ? (lane & 15) : lane;
+    const uint32_t band_s = smem_u32(band);
+    const uint32_t sink_s = band_s + (uint32_t)nrow * K * 8u;
+    const uint32_t tstr = (uint32_t)vpad * K * 8u;      // bytes between band rows
+    const int v01 = col_v01(Vg), ovc = col_ovc(Vg, vb);
+    const uint32_t bdesc_s = smem_u32(bdesc2);
+    const uint32_t snap0 = smem_u32(snap) + (uint32_t)(h * nrow + hl) * 4u;   // snapshot of entry (0, hl)
+    const uint32_t sstr = (uint32_t)vpad * 4u;          // bytes between snapshot rows
+    // round j: view hl + LPC j, so the round's shared address and column
+    // offsets are the first round's plus a constant (a lane past the agent's
+    // views reads bytes of its ring slot or of the warp's next region, and
+    // drops them)
+    const uint32_t lbase0 = band_s + (uint32_t)(hl * K + h) * 8u;   // entry (0, hl)
+    const uint32_t hoff0 = 2u + (uint32_t)hl;                        // view hl's header byte
+    const uint32_t voff0 = (uint32_t)(v01 + 2 * vb * hl);           // view hl's value pair
+    uint32_t vokm = 0;        // bit j: round j's view exists
+#pragma unroll
+    for (int j = 0; j < R; ++j) vokm |= (hl + LPC * j < Vg ? 1u : 0u) << j;
+    // tile rows of P lanes (P a power of two >= S + 2, at most 32)
+    const int lP = TS <= 8 ? 3 : TS <= 16 ? 4 : 5;
+    const int tr0 = lane >> lP, tc0 = lane & ((1 << lP) - 1), trs = 32 >> lP;
+
+    // this lane's prior neighbour: lanes 0..7 of each chain the in-plane
+    // 8-neighbourhood, or (volumes) lanes 0..25 the 26-neighbourhood; other
+    // lanes read the pixel itself with weight 0.  mbit: the neighbour's bit in
+    // a pixel's 3x3 in-image mask.
     int pdz = 0, pdi = 0, pdj = 0;
     float pb = 0.f;
     if (NB26) {
@@ -202,32 +262,22 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
             const int zz = grp + pdz;
             pb = (zz >= 0 && zz < A.B) ? A.pscale * A.b26[d2 - 1] : 0.f;
         }
-    } else if (plane_lane < 8) {
-        const int kk = plane_lane < 4 ? plane_lane : plane_lane + 1;
+    } else if (hl < 8) {
+        const int kk = hl < 4 ? hl : hl + 1;
         pdi = kk / 3 - 1;
         pdj = kk % 3 - 1;
         pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
     }
     const int mbit = (pdi + 1) * 3 + (pdj + 1);
     const int noff = pdi * TS + pdj;
-    const float *nbase[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float *xt = (const float *)(chain(k) + Ly.xt);
-        nbase[k] = (pdz == 0 ? xt : (pdz < 0 ? halo_lo : halo_hi)) + noff;
-    }
-    // two chains: this lane's half's neighbour pointer
-    const float *nb_half = (const float *)(chain(K == 2 ? (lane >> 4) : 0) + Ly.xt) + noff;
+    float *xth = xt0 + h * TA;                   // this lane's chain's X tile
+    const float2 *vt2h = vt20 + h * S2;
+    const float *nb_tile = (pdz == 0 ? xth : (pdz < 0 ? halo_lo : halo_hi)) + noff;
 
     // chain k: reconstruction grp*K + k
-    auto eLk = [&](int k) { return A.eL + (int64_t)(grp * K + k) * A.ne + (int64_t)v0 * A.D; };
-    auto Xk = [&](int k) { return A.X + ((int64_t)(grp * K + k) * A.N + g) * n; };
-
-    // pixel t = ti * S + tj of a visiting-list word (tile index (ti+1)*TS + tj+1)
-    auto tile_pixel = [&](uint32_t word) {
-        const int tc = (int)(word & 0x1FFu);
-        return (tc / TS - 1) * S + (tc % TS - 1);
-    };
+    auto rb_of = [&](int k) { return (int64_t)(grp * K + k); };
+    float2 *const eLh = A.eL + rb_of(h) * A.ne + (int64_t)v0 * A.D;   // this lane's chain, agent g
+    auto Xk = [&](int k) { return A.X + (rb_of(k) * A.N + g) * n; };
 
     // --- super-voxel metadata -------------------------------------------
     auto sv_of = [&](int m) {           // m-th super-voxel of this warp, -1 past the end
@@ -236,8 +286,9 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
         return A.sv_order[A.backward ? A.nsv - 1 - slot : slot];
     };
     // visiting list of super-voxel sv from its column offsets sc: per
-    // non-empty pixel in visiting order its pixel/tile indices and in-image
-    // neighbour mask, and its column's offset and size; returns the count
+    // non-empty pixel in visiting order its tile index, in-image neighbour
+    // mask and pixel offset, and its column's offset and size; returns the
+    // count
     auto build_list = [&](int svb, const uint32_t *sc, uint32_t *pl, uint2 *cl) {
         const int bi = (svb / A.nsvx) * S, bj = (svb % A.nsvx) * S;
         const int64_t svoff = A.sv_base[(int64_t)g * A.nsv + svb];
@@ -248,7 +299,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
             const bool ne = k < S2 && sc[t + 1] != sc[t];
             const unsigned m = __ballot_sync(FULL, ne);
             if (ne) {
-                const int ti = t / S, tj = t % S, i = bi + ti, j = bj + tj;
+                const int ti = t >> lS, tj = t & (S - 1), i = bi + ti, j = bj + tj;
                 uint32_t mask = 0;
 #pragma unroll
                 for (int di = -1; di <= 1; ++di)
@@ -257,7 +308,7 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
                         if (i + di >= 0 && i + di < A.ny && j + dj >= 0 && j + dj < A.nx)
                             mask |= 1u << ((di + 1) * 3 + dj + 1);
                 const int pos = count + __popc(m & lt_mask);
-                pl[pos] = (uint32_t)((ti + 1) * TS + tj + 1) | mask << 9;
+                pl[pos] = (uint32_t)((ti + 1) * TS + tj + 1) | mask << 11 | (uint32_t)t << 20;
                 cl[pos] = make_uint2((uint32_t)((svoff + sc[t]) >> 4), sc[t + 1] - sc[t]);
             }
             count += __popc(m);
@@ -265,11 +316,12 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
         __syncwarp();
         return count;
     };
-    // TMA of one column into ring stage idx % kRing (one lane)
+    // TMA of one column into ring stage idx % kRing, issued by lane 0 (all
+    // lanes run the call; the others are predicated off, no branch)
+    const uint64_t stream_policy = l2_evict_first_policy();
     auto issue = [&](uint32_t idx, const uint8_t *src, uint32_t bytes) {
         const uint32_t stg = idx & (kRing - 1);
-        mbar_expect_tx(&bars[stg], bytes);
-        tma_load_1d(ring + (size_t)stg * A.col_stride, src, bytes, &bars[stg]);
+        tma_load_1d_lane0(ring + (size_t)stg * A.col_stride, src, bytes, &bars[stg], lane, stream_policy);
     };
 
     int sv = sv_of(0);
@@ -284,89 +336,154 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
     }
     int count = build_list(sv, scoff, pl2, cl2);
     // The warp's columns form one sequence (its super-voxels' visiting lists
-    // one after the other).  seq: columns consumed; issued: columns whose
-    // copy has been started; seq0: sequence number of the current
-    // super-voxel's first column.  Columns of the current and of the next
-    // super-voxel (once its list is built) may be in flight, at most kRing.
-    uint32_t issued = 0, seq = 0, seq0 = 0;
+    // one after the other).  dec: columns decoded; issued: columns whose copy
+    // has been started; seq0: sequence number of the current super-voxel's
+    // first column.  A slot is refilled one column late: when column d is
+    // decoded, the data of column d-1 has been used by the stores of the
+    // pixel before, so its slot is free; at most kRing - 1 copies are in
+    // flight beside the column held in registers.
+    uint32_t issued = 0, dec = 0, seq0 = 0;
     int count_n = 0;
     int cur = 0;
+    auto col_src = [&](uint2 c) { return A.cols + ((uint64_t)c.x << 4); };
+    // column x of the sequence from the current (cl) or next (cl_n) list
     auto list_entry = [&](uint32_t x, const uint2 *cl, const uint2 *cl_n) {
         return x < (uint32_t)count ? cl[x] : cl_n[x - count];
     };
-    auto col_src = [&](uint2 c) { return A.cols + ((uint64_t)c.x << 4); };
     auto fill_ring = [&](const uint2 *cl, const uint2 *cl_n) {
-        while (issued - seq < (uint32_t)kRing && issued - seq0 < (uint32_t)(count + count_n)) {
+        while (issued - dec < (uint32_t)(kRing - 1) && issued - seq0 < (uint32_t)(count + count_n)) {
             const uint2 c = list_entry(issued - seq0, cl, cl_n);
-            if (lane == 0) issue(issued, col_src(c), c.y);
+            issue(issued, col_src(c), c.y);
             ++issued;
         }
     };
     fill_ring(cl2, cl2 + S2);
-    int status_seen = 0;
-    // wait for column seq; false when the bounded wait gave up (the host is
+    // drain this warp's copies in flight (bounded) before leaving early
+    auto drain = [&]() {
+        for (uint32_t q2 = dec; q2 < issued; ++q2) {
+            uint32_t sp2 = 0;
+            while (!mbar_try_wait(&bars[q2 & (kRing - 1)], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
+        }
+    };
+    // wait for column dec; false when the bounded wait gave up (the host is
     // flagged and this warp's copies in flight are drained first)
     auto wait_column = [&]() {
-        const uint32_t stg = seq & (kRing - 1);
-        const uint32_t parity = (seq / kRing) & 1u;
+        const uint32_t stg = dec & (kRing - 1);
+        const uint32_t parity = (dec / kRing) & 1u;
         uint32_t spins = 0;
         while (!__all_sync(FULL, mbar_try_wait(&bars[stg], parity))) {
             if (++spins > kSpinLimit) {
                 if (lane == 0) atomicExch(A.status, kStatusTimeout);
-                for (uint32_t q2 = seq + 1; q2 < issued; ++q2) {
-                    uint32_t sp2 = 0;
-                    while (!mbar_try_wait(&bars[q2 & (kRing - 1)], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
-                }
+                drain();
                 return false;
             }
         }
         return true;
     };
+    // read column dec from its ring slot (first half of decoding: the loads)
+    auto col_load = [&](ColRaw<R, RO> &w) {
+        const uint8_t *col = ring + (size_t)(dec & (kRing - 1)) * A.col_stride;
+        w.n3 = *(const uint16_t *)col;
+        const uint8_t *ch = col + hoff0, *cv = col + voff0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            w.hb[j] = ch[LPC * j];
+            w.a[j] = ld_pair<T>(cv + 2 * vb * LPC * j, 0);
+        }
+        const int ovv = (ovc + 2 * w.n3 + 3) & ~3;
+#pragma unroll
+        for (int o = 0; o < RO; ++o) {
+            const int i = hl + LPC * o;
+            const int il = i < w.n3 ? i : 0;
+            w.code[o] = *(const uint16_t *)(col + ovc + 2 * il);
+            w.a2[o] = ld_val<T>(col + ovv, il);
+        }
+    };
+    // second half: band addresses and values; then the slot of the column
+    // decoded before is refilled with the next column of the sequence
+    auto col_finish = [&](const ColRaw<R, RO> &w, ColRegs<R, RO> &c, const uint2 *cl, const uint2 *cl_n) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const bool ok = (vokm >> j) & 1u;
+            c.addr[j] = ok ? lbase0 + 256u * j + (w.hb[j] & 63u) * tstr : sink_s - tstr;
+            c.a0[j] = ok ? w.a[j].x : 0.f;
+            c.a1[j] = ok ? w.a[j].y : 0.f;
+        }
+#pragma unroll
+        for (int o = 0; o < RO; ++o) {
+            const bool ok = hl + LPC * o < w.n3;
+            c.oaddr[o] = ok ? band_s + (w.code[o] * K + h) * 8u : sink_s;
+            c.a2[o] = ok ? w.a2[o] : 0.f;
+        }
+        ++dec;
+        if (issued - dec < (uint32_t)(kRing - 1) && issued - seq0 < (uint32_t)(count + count_n)) {
+            const uint2 rf = list_entry(issued - seq0, cl, cl_n);
+            issue(issued, col_src(rf), rf.y);
+            ++issued;
+        }
+    };
+
+    int status_seen = 0;
+    ColRegs<R, RO> cc, cn;
+    bool have_cur = false;    // cc holds the current super-voxel's first column
 
     for (int m = 0; sv >= 0; ++m) {
-        uint32_t *bdesc = bdesc2 + cur * A.max_views;
+        uint32_t *bdesc = bdesc2 + cur * vpad;
         const uint32_t *pl = pl2 + cur * S2;
         const uint2 *cl = cl2 + cur * S2;
-        uint32_t *bdesc_n = bdesc2 + (cur ^ 1) * A.max_views;
+        uint32_t *bdesc_n = bdesc2 + (cur ^ 1) * vpad;
         uint32_t *pl_n = pl2 + (cur ^ 1) * S2;
         uint2 *cl_n = cl2 + (cur ^ 1) * S2;
         const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
+        const int i0 = si * S, j0 = sj * S;
 
-        // --- band layout; band, X and theta2 tiles of every chain -----------
-        const int band_tot = load_band_index(bdesc, Vg, A.D, bdesc, bglob, lane);
+        // --- band (e, Lambda) of every chain, X tiles, theta2 ---------------
+        // the lanes of chain h load and later flush the entries of chain h,
+        // lane hl taking views hl, hl + 32/K, ... (the same lane for the same
+        // global entry in every super-voxel, so a flushed change is seen by
+        // the next load of that entry); e also goes into the snapshot
+        for (int v = hl; v < Vg; v += LPC) {
+            const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
+            const int len = (int)(d >> 16);
+            const float2 *src = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
+            uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+            for (int t = 0; t < len; ++t) {
+                cp_async8_s(ds, src + t);
+                cp_async4_s(ss, src + t);
+                ds += tstr;
+                ss += sstr;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            float2 *beL = (float2 *)(ch + Ly.beL);
-            float *xt = (float *)(ch + Ly.xt);
-            float2 *vt2 = (float2 *)(ch + Ly.vt2);
-            const float2 *eL = eLk(k);
-            for (int f = lane; f < band_tot; f += 32) cp_async8(&beL[f], &eL[bglob[f]]);
-            // lanes past a column's end gather entry 0 with weight 0: keep it finite
-            if (band_tot == 0 && lane == 0) beL[0] = make_float2(0.f, 0.f);
+            float *xt = xt0 + k * TA;
+            float2 *vt2 = vt20 + k * S2;
             const float *Xg = Xk(k);
-            for (int q = lane; q < TA; q += 32) {
-                const int i = si * S + q / TS - 1, j = sj * S + q % TS - 1;
-                if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&xt[q], &Xg[(int64_t)i * A.nx + j]);
-                else xt[q] = 0.f;
-            }
-            const float *t2g = A.theta2 + ((int64_t)(grp * K + k) * A.N + g) * n;
+            for (int ti = tr0; ti < TS; ti += trs)
+                for (int tj = tc0; tj < TS; tj += 32) {
+                    const int i = i0 + ti - 1, j = j0 + tj - 1;
+                    if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&xt[ti * TS + tj], &Xg[(int64_t)i * A.nx + j]);
+                    else xt[ti * TS + tj] = 0.f;
+                }
+            const float *t2g = A.theta2 + (rb_of(k) * A.N + g) * n;
             for (int q = lane; q < count; q += 32) {
-                const int t = tile_pixel(pl[q]);
-                cp_async4(&vt2[q].y, &t2g[(int64_t)(si * S + t / S) * A.nx + sj * S + t % S]);
+                const int t = (int)(pl[q] >> 20);
+                cp_async4(&vt2[q].y, &t2g[(int64_t)(i0 + (t >> lS)) * A.nx + j0 + (t & (S - 1))]);
             }
         }
         if (NB26) {
             // X tiles of the neighbouring slices
-            for (int h = 0; h < 2; ++h) {
-                const int zz = grp + (h ? 1 : -1);
-                float *ht = h ? halo_hi : halo_lo;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int zz = grp + (hh ? 1 : -1);
+                float *ht = hh ? halo_hi : halo_lo;
                 const float *Xz = (zz >= 0 && zz < A.B) ? A.X + ((int64_t)zz * A.N + g) * n : nullptr;
-                for (int q = lane; q < TA; q += 32) {
-                    const int i = si * S + q / TS - 1, j = sj * S + q % TS - 1;
-                    if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&ht[q], &Xz[(int64_t)i * A.nx + j]);
-                    else ht[q] = 0.f;
-                }
+                for (int ti = tr0; ti < TS; ti += trs)
+                    for (int tj = tc0; tj < TS; tj += 32) {
+                        const int i = i0 + ti - 1, j = j0 + tj - 1;
+                        if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx)
+                            cp_async4(&ht[ti * TS + tj], &Xz[(int64_t)i * A.nx + j]);
+                        else ht[ti * TS + tj] = 0.f;
+                    }
             }
         }
         cp_async_commit();
@@ -383,11 +500,11 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
         // plain loads while the copies above are in flight
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float2 *vt2 = (float2 *)(chain(k) + Ly.vt2);
-            const int64_t rb = (int64_t)(grp * K + k);
+            float2 *vt2 = vt20 + k * S2;
+            const int64_t rb = rb_of(k);
             for (int q = lane; q < count; q += 32) {
-                const int t = tile_pixel(pl[q]);
-                const int64_t s = (int64_t)(si * S + t / S) * A.nx + sj * S + t % S;
+                const int t = (int)(pl[q] >> 20);
+                const int64_t s = (int64_t)(i0 + (t >> lS)) * A.nx + j0 + (t & (S - 1));
                 const float vv = A.vexp ? A.vexp[(rb * A.N + g) * n + s]
                                         : (float)(2.0 * A.wbar[rb * n + s] - (double)A.w[(rb * A.N + g) * n + s]);
                 vt2[q].x = vv * A.inv_s2;
@@ -403,267 +520,138 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
         fill_ring(cl, cl_n);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            const float2 *beL = (const float2 *)(ch + Ly.beL);
-            float *bsnap = (float *)(ch + Ly.bsnap);
-            for (int f = lane; f < band_tot; f += 32) bsnap[f] = beL[f].x;
-            float2 *vt2 = (float2 *)(ch + Ly.vt2);
+            float2 *vt2 = vt20 + k * S2;
             for (int q = lane; q < count; q += 32) vt2[q].y += A.inv_s2;
         }
         __syncwarp();
         if (status_seen != 0) {
             // another warp gave up: drain this warp's copies in flight and stop
-            for (uint32_t q2 = seq; q2 < issued; ++q2) {
-                uint32_t sp2 = 0;
-                while (!mbar_try_wait(&bars[q2 & (kRing - 1)], (q2 / kRing) & 1u) && ++sp2 < kSpinLimit) {}
-            }
+            drain();
             return;
+        }
+        if (!have_cur && count > 0) {
+            if (!wait_column()) return;
+            ColRaw<R, RO> w0;
+            col_load(w0);
+            col_finish(w0, cc, cl, cl_n);
+            have_cur = true;
         }
 
         // --- visit the pixels ------------------------------------------------
-#pragma unroll 2
-        for (int q = 0; q < count; ++q) {
+        // one pixel with its column in c; the next column (this super-voxel's
+        // or the next one's first) is decoded into c2 meanwhile.  False when a
+        // bounded wait gave up.
+        auto pixel = [&](int q, ColRegs<R, RO> &c, ColRegs<R, RO> &c2) {
+            // gathers of this pixel's band entries (the previous pixel's
+            // update is visible after its __syncwarp)
+            float2 g0[R], g1[R], g2[RO];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                g0[j] = lds_f2(c.addr[j]);
+                g1[j] = lds_f2(c.addr[j] + tstr);
+            }
+#pragma unroll
+            for (int o = 0; o < RO; ++o) g2[o] = lds_f2(c.oaddr[o]);
+            // prior through the surrogate weights (lane l of a chain:
+            // neighbour l), from the X tiles only.  No branch: out-of-image
+            // neighbours and idle lanes get weight 0.
             const uint32_t pq = pl[q];
-            const int tc = (int)(pq & 0x1FFu);
-            // the column that refills the slot this pixel frees (the ring
-            // always has room for one once a column is consumed): the next
-            // of the sequence, if its list is known; read now, off the
-            // critical path
-            const bool rf_any = issued - seq0 < (uint32_t)(count + count_n);
-            uint2 rf = make_uint2(0u, 0u);
-            if (rf_any) rf = list_entry(issued - seq0, cl, cl_n);
-            if constexpr (K == 2) {
-                // Two chains: half h (lanes 16h .. 16h+15) updates chain h
-                // over the shared column, covering all its pairs; the control
-                // flow, the column wait and refill and the reductions serve
-                // both pixel updates.
-                const int h = lane >> 4, hl = lane & 15;
-                uint8_t *chh = chain(h);
-                float *xth = (float *)(chh + Ly.xt);
-                const float2 vq = ((const float2 *)(chh + Ly.vt2))[q];
-                const float xs = xth[tc];
-                const float d = xs - nb_half[tc];
-                const float pbv = ((pq >> (9 + mbit)) & 1u) ? pb : 0.f;
-                float pr2 = pbv * prior_weight(A, d);
-                const float pr1 = pr2 * d;
-                const float prox = fmaf(xs, A.inv_s2, -vq.x);   // (x - v) / sigma^2
+            const int tc = (int)(pq & 0x7FFu);
+            const float2 vq = vt2h[q];
+            const float xs = xth[tc];
+            const float d = xs - nb_tile[tc];
+            const float pbv = ((pq >> (11 + mbit)) & 1u) ? pb : 0.f;
+            float pr2 = pbv * prior_weight(A, d);
+            const float pr1 = pr2 * d;
+            const float prox = fmaf(xs, A.inv_s2, -vq.x);   // (x - v) / sigma^2
+            if (NB26) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+            } else {
 #pragma unroll
                 for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
-                pr2 = __shfl_sync(FULL, pr2, lane & 16);
-                if (!wait_column()) return;
-                const uint8_t *col = ring + (size_t)(seq & (kRing - 1)) * A.col_stride;
-                const int nnz = *(const uint16_t *)col;
-                const uint32_t *cidx2 = (const uint32_t *)(col + 4);
-                const uint8_t *cval = col + col_idx_bytes(nnz);
-                const int npairs = (nnz + 1) >> 1;
-                const int lastp = max(npairs - 1, 0);
-                constexpr int R2 = PR;   // rounds of 16 lanes
-                uint32_t ib[R2];
-                float2 av[R2];
+                pr2 = __shfl_sync(FULL, pr2, lane & ~(LPC - 1));
+            }
+            // data term: -sum A Lambda e over this lane's entries, plus the
+            // prior's gradient; theta2 = sum A^2 Lambda is stored
+            float pa = pr1, pc = 0.f;
 #pragma unroll
-                for (int r = 0; r < R2; ++r) {
-                    const int pe = r * 16 + hl;
-                    const int pcl = min(pe, lastp);
-                    const uint32_t i0 = cidx2[pcl];
-                    const float2 a0 = ld_pair<T>(cval, pcl);
-                    const bool ok = pe < npairs;
-                    ib[r] = ok ? i0 : 0u;
-                    av[r] = ok ? a0 : make_float2(0.f, 0.f);
-                }
-                float2 *beL = (float2 *)(chh + Ly.beL);
-                float ex[R2][2], pa = 0.f, pc = 0.f;
-#pragma unroll
-                for (int r = 0; r < R2; ++r) {
-                    const float2 e0 = beL[ib[r] & 0xFFFFu], e1 = beL[ib[r] >> 16];
-                    ex[r][0] = e0.x;
-                    ex[r][1] = e1.x;
-                    pa = fmaf(-av[r].x * e0.y, e0.x, pa);
-                    pc = fmaf(-av[r].y * e1.y, e1.x, pc);
-                }
-                float p1 = (pa + pc) + pr1;
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
-                // both halves have consumed the column: refill its slot
-                ++seq;
-                if (rf_any) {
-                    if (lane == 0) issue(issued, col_src(rf), rf.y);
-                    ++issued;
-                }
-                const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
-                const int sink = A.max_band;
-#pragma unroll
-                for (int r = 0; r < R2; ++r) {
-                    const int pe = r * 16 + hl;
-                    const int d0 = pe < npairs ? (int)(ib[r] & 0xFFFFu) : sink;
-                    const int d1 = 2 * pe + 1 < nnz ? (int)(ib[r] >> 16) : sink;
-                    beL[d0].x = fmaf(-av[r].x, alpha, ex[r][0]);
-                    beL[d1].x = fmaf(-av[r].y, alpha, ex[r][1]);
-                }
-                xth[tc] = xs + alpha;
-                __syncwarp();
-            } else {
-            // prior through the surrogate weights (lane l: neighbour l), from
-            // the X tiles only; its curvature is reduced here, before the
-            // column is needed.  No branch: out-of-image neighbours and idle
-            // lanes get weight 0.
-            const float pbv = ((pq >> (9 + mbit)) & 1u) ? pb : 0.f;
-            float xs[K], pr1[K], pr2[K], prox[K], t2[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float *xt = (const float *)(chain(k) + Ly.xt);
-                const float2 vq = ((const float2 *)(chain(k) + Ly.vt2))[q];
-                xs[k] = xt[tc];
-                const float d = xs[k] - nbase[k][tc];
-                pr2[k] = pbv * prior_weight(A, d);
-                pr1[k] = pr2[k] * d;
-                prox[k] = fmaf(xs[k], A.inv_s2, -vq.x);   // (x - v) / sigma^2
-                t2[k] = vq.y;                             // theta2 + 1 / sigma^2
+            for (int j = 0; j < R; ++j) {
+                pa = fmaf(-c.a0[j] * g0[j].y, g0[j].x, pa);
+                pc = fmaf(-c.a1[j] * g1[j].y, g1[j].x, pc);
             }
 #pragma unroll
-            for (int o = 1; o < (NB26 ? 32 : 8); o <<= 1)
-#pragma unroll
-                for (int k = 0; k < K; ++k) pr2[k] += __shfl_xor_sync(FULL, pr2[k], o);
-            if (!NB26) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) pr2[k] = __shfl_sync(FULL, pr2[k], 0);
+            for (int o = 0; o < RO; ++o) pa = fmaf(-c.a2[o] * g2[o].y, g2[o].x, pa);
+            float p1 = pa + pc;
+            const bool more = dec - seq0 < (uint32_t)(count + count_n);
+            if (more) {
+                if (!wait_column()) return false;
+                ColRaw<R, RO> wn;
+                col_load(wn);
+                col_finish(wn, c2, cl, cl_n);
             }
-
-            if (!wait_column()) return;
-            const uint8_t *col = ring + (size_t)(seq & (kRing - 1)) * A.col_stride;
-            const int nnz = *(const uint16_t *)col;
-            const uint32_t *cidx2 = (const uint32_t *)(col + 4);
-            const uint8_t *cval = col + col_idx_bytes(nnz);
-
-            // data term of each chain: -sum A Lambda e in two interleaved
-            // accumulators, plus the prior's gradient (lanes 0..7 / 0..25);
-            // theta2 = sum A^2 Lambda is stored
-            float alpha[K];
-            if constexpr (PR > 0) {
-                // pair loads without branches: lanes past the column's end
-                // read its last pair (or pair 0 of an empty column, inside
-                // the slot) and take (0, 0)
-                const int npairs = (nnz + 1) >> 1;
-                const int lastp = max(npairs - 1, 0);
-                uint32_t ib[PR];
-                float2 av[PR];
 #pragma unroll
-                for (int r = 0; r < PR; ++r) {
-                    const int pe = r * 32 + lane;
-                    const int pc = min(pe, lastp);
-                    const uint32_t i0 = cidx2[pc];
-                    const float2 a0 = ld_pair<T>(cval, pc);
-                    const bool ok = pe < npairs;
-                    ib[r] = ok ? i0 : 0u;
-                    av[r] = ok ? a0 : make_float2(0.f, 0.f);
-                }
-                // pairs past the column's end are (0, 0) and add nothing;
-                // every gather is issued back to back
-                float ex[K][PR][2], pa[K], pc[K];
+            for (int o = LPC / 2; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
+            // the step's sign and zero set come from the numerator alone, so an
+            // approximate reciprocal leaves the fixed point unchanged
+            const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
+            // update e: a lane's own views' entries, and its share of the
+            // three-channel list (idle lanes write the zero sink with value 0)
 #pragma unroll
-                for (int k = 0; k < K; ++k) { pa[k] = 0.f; pc[k] = 0.f; }
-#pragma unroll
-                for (int r = 0; r < PR; ++r) {
-                    const int b0 = (int)(ib[r] & 0xFFFFu), b1 = (int)(ib[r] >> 16);
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        const float2 *beL = (const float2 *)(chain(k) + Ly.beL);
-                        const float2 e0 = beL[b0], e1 = beL[b1];
-                        ex[k][r][0] = e0.x;
-                        ex[k][r][1] = e1.x;
-                        pa[k] = fmaf(-av[r].x * e0.y, e0.x, pa[k]);
-                        pc[k] = fmaf(-av[r].y * e1.y, e1.x, pc[k]);
-                    }
-                }
-                float p1[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) p1[k] = (pa[k] + pc[k]) + pr1[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                    for (int k = 0; k < K; ++k) p1[k] += __shfl_xor_sync(FULL, p1[k], o);
-                // Every lane's pairs have now been consumed (each loaded pair
-                // feeds p1, and the full-warp reduction has joined all lanes),
-                // so no read of the slot is outstanding: refill it now, before
-                // the update.  Issuing right after the loads instead would let
-                // a fast (L2-hit) copy overwrite the slot under reads still in
-                // flight.
-                ++seq;
-                if (rf_any) {
-                    if (lane == 0) issue(issued, col_src(rf), rf.y);
-                    ++issued;
-                }
-                // the step's sign and zero set come from the numerator alone, so an
-                // approximate reciprocal leaves the fixed point unchanged
-#pragma unroll
-                for (int k = 0; k < K; ++k) alpha[k] = -(p1[k] + prox[k]) * rcp_approx(t2[k] + pr2[k]);
-                // update e: the entries of one column are distinct band positions;
-                // stores past the column's end go to the sink entry (no branch)
-                const int sink = A.max_band;
-#pragma unroll
-                for (int r = 0; r < PR; ++r) {
-                    const int pe = r * 32 + lane;
-                    const int d0 = pe < npairs ? (int)(ib[r] & 0xFFFFu) : sink;
-                    const int d1 = 2 * pe + 1 < nnz ? (int)(ib[r] >> 16) : sink;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        float2 *beL = (float2 *)(chain(k) + Ly.beL);
-                        beL[d0].x = fmaf(-av[r].x, alpha[k], ex[k][r][0]);
-                        beL[d1].x = fmaf(-av[r].y, alpha[k], ex[k][r][1]);
-                    }
-                }
-            } else {
-                float2 *beL = (float2 *)(chain(0) + Ly.beL);
-                float pa = 0.f, pc = 0.f;
-                for (int pe = lane; 2 * pe < nnz; pe += 32) {
-                    const uint32_t ib = cidx2[pe];
-                    const float2 av = ld_pair<T>(cval, pe);
-                    const float2 e0 = beL[ib & 0xFFFFu], e1 = beL[ib >> 16];
-                    pa = fmaf(-av.x * e0.y, e0.x, pa);
-                    pc = fmaf(-av.y * e1.y, e1.x, pc);
-                }
-                float p1 = (pa + pc) + pr1[0];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
-                alpha[0] = -(p1 + prox[0]) * rcp_approx(t2[0] + pr2[0]);
-                for (int pe = lane; 2 * pe < nnz; pe += 32) {
-                    const uint32_t ib = cidx2[pe];
-                    const float2 av = ld_pair<T>(cval, pe);
-                    const int b0 = (int)(ib & 0xFFFFu), b1 = (int)(ib >> 16);
-                    beL[b0].x = fmaf(-av.x, alpha[0], beL[b0].x);
-                    if (2 * pe + 1 < nnz) beL[b1].x = fmaf(-av.y, alpha[0], beL[b1].x);
-                }
+            for (int j = 0; j < R; ++j) {
+                sts_f(c.addr[j], fmaf(-c.a0[j], alpha, g0[j].x));
+                sts_f(c.addr[j] + tstr, fmaf(-c.a1[j], alpha, g1[j].x));
             }
-            // X update: every lane holds alpha and stores the same value
 #pragma unroll
-            for (int k = 0; k < K; ++k) ((float *)(chain(k) + Ly.xt))[tc] = xs[k] + alpha[k];
+            for (int o = 0; o < RO; ++o) sts_f(c.oaddr[o], fmaf(-c.a2[o], alpha, g2[o].x));
+            // X update: every lane of the chain stores the same value
+            xth[tc] = xs + alpha;
             __syncwarp();
-            if constexpr (PR == 0) {
-                // the slot was read until the update above
-                ++seq;
-                if (rf_any) {
-                    if (lane == 0) issue(issued, col_src(rf), rf.y);
-                    ++issued;
-                }
+            return true;
+        };
+        int q = 0;
+        if constexpr (R <= 3) {
+            // two pixels per trip, the decoded columns alternating between
+            // cc and cn (no register copy)
+            for (; q + 1 < count; q += 2) {
+                if (!pixel(q, cc, cn)) return;
+                if (!pixel(q + 1, cn, cc)) return;
             }
+        } else {
+            for (; q + 1 < count; ++q) {
+                if (!pixel(q, cc, cn)) return;
+                cc = cn;
             }
         }
+        if (q < count) {
+            if (!pixel(q, cc, cn)) return;
+            cc = cn;
+        }
+        // the next super-voxel's first column is decoded already when the
+        // sequence went on past this one
+        have_cur = dec - seq0 > (uint32_t)count;
 
-        // --- write back: X tiles and the change of e --------------------------
+        // --- write back: X tiles and the change of e ---------------------------
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            uint8_t *ch = chain(k);
-            const float *xt = (const float *)(ch + Ly.xt);
+            const float *xt = xt0 + k * TA;
             float *Xg = Xk(k);
-            for (int q = lane; q < S2; q += 32) {
-                const int i = si * S + q / S, j = sj * S + q % S;
-                if (i < A.ny && j < A.nx) Xg[(int64_t)i * A.nx + j] = xt[(q / S + 1) * TS + (q % S + 1)];
+            for (int p = lane; p < S2; p += 32) {
+                const int ti = p >> lS, tj = p & (S - 1);
+                if (i0 + ti < A.ny && j0 + tj < A.nx)
+                    Xg[(int64_t)(i0 + ti) * A.nx + j0 + tj] = xt[(ti + 1) * TS + tj + 1];
             }
-            const float2 *beL = (const float2 *)(ch + Ly.beL);
-            const float *bsnap = (const float *)(ch + Ly.bsnap);
-            float2 *eL = eLk(k);
-            for (int f = lane; f < band_tot; f += 32) {
-                const float de = beL[f].x - bsnap[f];
-                if (de != 0.f) atomicAdd(&eL[bglob[f]].x, de);
+        }
+        for (int v = hl; v < Vg; v += LPC) {
+            const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
+            const int len = (int)(d >> 16);
+            float2 *eg = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
+            uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+            for (int t = 0; t < len; ++t) {
+                const float de = lds_f32(ds) - lds_f32(ss);
+                if (de != 0.f) atomicAdd(&eg[t].x, de);
+                ds += tstr;
+                ss += sstr;
             }
         }
         __syncwarp();
@@ -677,52 +665,35 @@ __global__ void __maxnreg__(K == 1 ? MACE_SWEEP_MAXNREG : K == 2 ? 128 : 224) ic
     }
 }
 
-// Entries per column in rounds: one or four chains take pairs over 32 lanes
-// (PR = ceil(max_nnz / 64) in {2, 3}; 0: any count, one chain); two chains
-// take pairs over one 16-lane half (PR = ceil(max_nnz / 32) in {4, 5, 6}).
-template <typename T, int S, bool CHAINS>
-static sweep_fn sweep_lookup_s(int max_nnz, int K, bool nb26)
-{
-    const int r32 = (max_nnz + 63) / 64, r16 = (max_nnz + 31) / 32;
-    if (nb26) {
-        if (K != 1) return nullptr;
-        if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 1, true>;
-        if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 1, true>;
-        return icd_sweep_kernel<T, 0, S, 1, true>;
-    }
-    if constexpr (CHAINS) {
-        if (K == 2) {
-            if (r16 <= 4) return icd_sweep_kernel<T, 4, S, 2, false>;
-            if (r16 <= 5) return icd_sweep_kernel<T, 5, S, 2, false>;
-            if (r16 <= 6) return icd_sweep_kernel<T, 6, S, 2, false>;
-            return nullptr;
-        }
-        if (K == 4) {
-            if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 4, false>;
-            if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 4, false>;
-            return nullptr;
-        }
-    }
-    if (K != 1) return nullptr;
-    if (r32 <= 2) return icd_sweep_kernel<T, 2, S, 1, false>;
-    if (r32 <= 3) return icd_sweep_kernel<T, 3, S, 1, false>;
-    return icd_sweep_kernel<T, 0, S, 1, false>;
-}
+// Rounds of views per lane and of the three-channel list for an agent of at
+// most max_views views and columns of at most max_n3 three-channel runs.
+inline int sweep_rounds(int max_views, int K) { return (max_views + 32 / K - 1) / (32 / K); }
+inline int sweep_ovf_rounds(int R, int K) { return (K == 2 || R >= 3) ? 2 : 1; }
 
-// The sweep kernel for columns of at most max_nnz entries, super-voxel size
-// S, K chains and the 8- or 26-neighbourhood; nullptr if that combination is
-// not built.
-template <typename T>
-static sweep_fn sweep_lookup(int max_nnz, int S, int K, bool nb26)
+template <typename T, int K, bool NB26>
+static sweep_fn sweep_lookup_k(int R)
 {
-    switch (S) {
-    case 4: return sweep_lookup_s<T, 4, true>(max_nnz, K, nb26);
-    case 8: return sweep_lookup_s<T, 8, true>(max_nnz, K, nb26);
-    case 16: return sweep_lookup_s<T, 16, false>(max_nnz, K, nb26);
+    switch (R) {
+    case 1: return icd_sweep_kernel<T, K, 1, (K == 2 ? 2 : 1), NB26>;
+    case 2: return icd_sweep_kernel<T, K, 2, (K == 2 ? 2 : 1), NB26>;
+    case 3: return icd_sweep_kernel<T, K, 3, 2, NB26>;
+    case 4: return icd_sweep_kernel<T, K, 4, 2, NB26>;
     default: return nullptr;
     }
 }
 
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_nnz, int S, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_nnz, int S, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_nnz, int S, int K, bool nb26);
+// The sweep kernel for agents of at most max_views views with K chains and
+// the 8- or 26-neighbourhood; nullptr if that combination is not built.
+template <typename T>
+static sweep_fn sweep_lookup(int max_views, int K, bool nb26)
+{
+    const int R = sweep_rounds(max_views, K);
+    if (nb26) return K == 1 ? sweep_lookup_k<T, 1, true>(R) : nullptr;
+    if (K == 1) return sweep_lookup_k<T, 1, false>(R);
+    if (K == 2) return sweep_lookup_k<T, 2, false>(R);
+    return nullptr;
+}
+
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26);

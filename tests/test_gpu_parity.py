@@ -74,7 +74,7 @@ def test_one_pass_matches_algorithm2(gpu_lib, prior, backward, batch):
     prm = mace.make_params(prior=prior, sigma_x=c["sigma_x"], sigma=0.5, sigma_mode=1, concurrency=1,
                            chains=batch)
     st = mace.mace_init(sm, np.stack([c["y"]] * batch), np.stack([c["lam"]] * batch), prm, batch=batch)
-    assert st.stats()["chains"] == batch
+    assert st.stats()["chains"] == (2 if batch % 2 == 0 else 1)
     st.set_state(w0, X0)
     st.prox_pass(v, backward=backward)
     _, Xg = st.get_state()
