@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 # (normalised) and rho from the convergence study recorded with the design
 # notes
 DEFAULTS = dict(batch=2, concurrency=-1, sigma=0.17, rho=0.95, tol=8e-7, max_iter=4000, sv=4, dtype="f32",
-                chains=2, recompute_every=10, forward="auto")
+                chains=2, recompute_every=10, forward="auto", deterministic=False)
 
 WORKLOAD = dict(name="parallel-beam 2D 512x512, 720 views over 180 deg, 725 channels, "
                      "16 interleaved agents x 45 views, Q-GGMRF (p=2, q=1.2, T=1), FP32",
@@ -177,7 +177,7 @@ def solver_params(mace, sigma_x, args):
     return mace.make_params(prior="qggmrf", sigma_x=sigma_x, sigma=args.sigma, sigma_mode=1, rho=args.rho,
                             sweeps_per_iter=2, symmetric=True, recompute_every=args.recompute_every,
                             max_iter=args.max_iter, tol=args.tol, concurrency=args.concurrency, sv_order=0, chains=args.chains,
-                            forward_geometry=forward_param(args))
+                            forward_geometry=forward_param(args), deterministic=args.deterministic)
 
 
 def run_mace(args, rank, world):
@@ -310,7 +310,7 @@ def run_mace(args, rank, world):
         "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Poisson counts)",
         "config": {"workload": WORKLOAD["name"], "batch_per_gpu": B, "sv_size": args.sv, "chains": args.chains,
                    "concurrency_per_agent": args.concurrency, "sigma_normalised": args.sigma, "rho": args.rho,
-                   "tol": args.tol, "recompute_every": args.recompute_every,
+                   "tol": args.tol, "recompute_every": args.recompute_every, "deterministic": bool(args.deterministic),
                    "e_recompute": "geometry" if forward_geometry(args) else "stored values", "iterations": iters_main, "converged": conv_main,
                    "accuracy": accuracy,
                    "parallelism": "replicas" if world > 1 else "single",
@@ -586,6 +586,8 @@ def build_parser():
                          "when the stored values are BF16/FP16)")
     ap.add_argument("--recompute-every", dest="recompute_every", type=int, default=DEFAULTS["recompute_every"],
                     help="Mann iterations between recomputations of e = y - A x")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="lock-step super-voxel phases and fixed-point sums: bit-identical results run to run")
     ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=670,
                     help="Mann iterations to tolerance the reference arm scales its sample to (the GPU path's count at the default settings)")
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)

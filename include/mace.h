@@ -128,7 +128,17 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   the exact projector; 2 = it reads the stored values; 0 (default) = 1
  *   for BF16/FP16 stored values, 2 for FP32.  The ICD updates keep using
  *   the stored values; with the geometry recompute the fixed point matches
- *   the exact MAP image more closely than that of the rounded matrix. */
+ *   the exact MAP image more closely than that of the rounded matrix.
+ *   deterministic: 0 = the super-voxels of an agent in flight run freely:
+ *   each reads the error sinogram when it starts and adds its change back
+ *   when it ends (float atomics), so the result depends on the GPU's
+ *   scheduling at the level of float rounding; 1 = they advance in lock-step
+ *   phases (a phase is one super-voxel per warp: all of a phase's reads come
+ *   before any of its writes, all its writes before the next phase's reads)
+ *   and the changes are summed in 64-bit fixed point, so every run, alone or
+ *   beside other work, eagerly or from a captured graph, gives the same bits.
+ *   The e recompute and the initial normalisation are order-independent in
+ *   both modes. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -146,6 +156,7 @@ typedef struct {
     int32_t chains;
     int32_t pnp;
     int32_t forward_geometry;
+    int32_t deterministic;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */

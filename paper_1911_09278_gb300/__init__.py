@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32),
                 ("chains", ctypes.c_int32), ("pnp", ctypes.c_int32),
-                ("forward_geometry", ctypes.c_int32)]
+                ("forward_geometry", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -228,14 +228,14 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
                 max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0, pnp=False,
-                forward_geometry=None):
+                forward_geometry=None, deterministic=False):
     """forward_geometry: None = the library's default (the geometry-evaluated
     e recompute for BF16/FP16 stored values), True = always from the
     geometry, False = always from the stored values."""
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
                   max_iter, tol, concurrency, sv_order, chains, int(bool(pnp)),
-                  0 if forward_geometry is None else (1 if forward_geometry else 2))
+                  0 if forward_geometry is None else (1 if forward_geometry else 2), int(bool(deterministic)))
 
 
 class State:

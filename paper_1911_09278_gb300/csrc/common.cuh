@@ -78,6 +78,20 @@ __device__ __forceinline__ float ld_any(const uint8_t *p, int idx, int dtype)
     return ld_val<__half>(p, idx);
 }
 
+// --- order-independent accumulation of e --------------------------------------
+// Changes of e that several warps add to one entry go into a 64-bit integer
+// accumulator in units of 2^-40 (integer addition is associative, so the sum
+// does not depend on the order of the additions) and are folded into e once
+// all are in.  |changes| < 2^23.
+static constexpr float kEScale = 1099511627776.0f;        // 2^40
+static constexpr float kEUnit = 9.094947017729282e-13f;   // 2^-40
+__device__ __forceinline__ void efix_add(unsigned long long *p, float d)
+{
+    const long long q = __float2ll_rn(d * kEScale);
+    if (q != 0) atomicAdd(p, (unsigned long long)q);
+}
+__device__ __forceinline__ float efix_value(unsigned long long v) { return __ll2float_rn((long long)v) * kEUnit; }
+
 // --- PTX helpers -------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -571,6 +571,8 @@ struct mace_state {
     int64_t ne;                // error-sinogram entries of one reconstruction
     double sigma_abs;
     float2 *d_eL = nullptr;    // (e, Lambda) [B][agents: V_g][D]
+    unsigned long long *d_dacc = nullptr;   // changes of e in fixed point (2^-40), same layout
+    unsigned *d_phase = nullptr;            // deterministic sweeps: phase counter per (group, agent)
     float *d_y = nullptr;      // y, same layout
     float *d_w = nullptr;      // [B][N][n]
     float *d_X = nullptr;      // [B][N][n]
@@ -705,24 +707,22 @@ __device__ __forceinline__ AuxSmem aux_smem(uint8_t *smem, int vpad, int wmax)
     return a;
 }
 
-// Adds each band entry's accumulated value to the agent's e.  Lane l takes
-// views l, l + 32, ...
-__device__ __forceinline__ void flush_band(const AuxSmem &a, int Vg, int vpad, int D, float2 *eLg, int lane)
+// Adds each band entry's accumulated value to the agent's accumulator of
+// changes of e (fixed point: the warps' additions sum to the same value in
+// any order).  Lane l takes views l, l + 32, ...
+__device__ __forceinline__ void flush_band(const AuxSmem &a, int Vg, int vpad, int D, unsigned long long *dg, int lane)
 {
     for (int v = lane; v < Vg; v += 32) {
         const uint32_t d = a.bdesc[v];
         const int lo = (int)(d & 0xFFFFu), len = (int)(d >> 16);
-        for (int t = 0; t < len; ++t) {
-            const float x = a.acc[t * vpad + v];
-            if (x != 0.f) atomicAdd(&eLg[(int64_t)v * D + lo + t].x, x);
-        }
+        for (int t = 0; t < len; ++t) efix_add(dg + (int64_t)v * D + lo + t, a.acc[t * vpad + v]);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict__ cols, const int64_t *__restrict__ sv_base,
                                                       const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
-                                                      const int *__restrict__ view_off, float2 *__restrict__ eL,
+                                                      const int *__restrict__ view_off, unsigned long long *__restrict__ dacc,
                                                       const float *__restrict__ X, int B, int N, int nsv, int nsvx, int S,
                                                       int nx, int ny, int D, int64_t ne, int vpad, int wmax)
 {
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const uint8_t *__restrict_
         }
         __syncwarp();
     }
-    flush_band(a, Vg, vpad, D, eL + (int64_t)b * ne + (int64_t)v0 * D, lane);
+    flush_band(a, Vg, vpad, D, dacc + (int64_t)b * ne + (int64_t)v0 * D, lane);
 }
 
 // The same product with A evaluated from the geometry instead of read from
@@ -798,7 +798,7 @@ __device__ __forceinline__ float trap_cdf_f(float u, const ViewGeo &G)
 __global__ void __launch_bounds__(256) forward_geometry_kernel(const ViewGeo *__restrict__ vgeo,
                                                                const uint32_t *__restrict__ band,
                                                                const int *__restrict__ view_off,
-                                                               float2 *__restrict__ eL,
+                                                               unsigned long long *__restrict__ dacc,
                                                                const float *__restrict__ X, int B, int N, int nsv, int nsvx,
                                                                int S, int nx, int ny, int D, int64_t ne, int vpad, int wmax)
 {
@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(256) forward_geometry_kernel(const ViewGeo *__
         }
     }
     __syncwarp();
-    flush_band(a, Vg, vpad, D, eL + (int64_t)b * ne + (int64_t)v0 * D, lane);
+    flush_band(a, Vg, vpad, D, dacc + (int64_t)b * ne + (int64_t)v0 * D, lane);
 }
 
 __global__ void pack_kernel(const float *__restrict__ y, const float *__restrict__ lam, const int *__restrict__ agent_view,
@@ -865,10 +865,43 @@ __global__ void pack_kernel(const float *__restrict__ y, const float *__restrict
     yg[tid] = yy;
 }
 
-__global__ void reset_error_kernel(const float *__restrict__ yg, float2 *__restrict__ eL, int64_t ne)
+__global__ void reset_error_kernel(const float *__restrict__ yg, float2 *__restrict__ eL,
+                                   unsigned long long *__restrict__ dacc, int64_t ne)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < ne) eL[k].x = yg[k];
+    if (k < ne) {
+        eL[k].x = yg[k];
+        dacc[k] = 0ull;
+    }
+}
+
+// e += the accumulated changes (one rounding per entry), accumulator cleared
+__global__ void fold_error_kernel(float2 *__restrict__ eL, unsigned long long *__restrict__ dacc, int64_t ne)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ne) {
+        const unsigned long long q = dacc[k];
+        if (q != 0ull) {
+            eL[k].x += efix_value(q);
+            dacc[k] = 0ull;
+        }
+    }
+}
+
+// Sum of m doubles in a fixed order (one block: strided partial sums, then a
+// fixed tree), so the result does not depend on scheduling
+__global__ void sum_fixed_kernel(const double *__restrict__ x, int64_t m, double *__restrict__ out)
+{
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int64_t k = threadIdx.x; k < m; k += blockDim.x) a += x[k];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
 }
 
 __global__ void broadcast_kernel(const double *__restrict__ wbar, float *__restrict__ X, int B, int N, int64_t n)
@@ -893,13 +926,14 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
                               const uint32_t *__restrict__ col_off, const uint32_t *__restrict__ band,
                               const int *__restrict__ view_off, const float2 *__restrict__ eL, int B, int N, int nsv,
                               int nsvx, int S, int nx, int ny, int D, int64_t ne, int vpad, int wmax,
-                              float *__restrict__ theta2, double *__restrict__ total)
+                              float *__restrict__ theta2, double *__restrict__ part)
 {
     // theta2[b][g][s] = sum_{k in J_g} A_ks^2 Lambda_k (the data term of the
     // coordinate curvature in Algorithm 2, constant over the iterations),
     // accumulated in FP64 and stored in FP32; zero for pixels without a
-    // column.  total += the FP64 sum over everything (for the normalised
-    // sigma).  One warp per (b, agent, super-voxel).
+    // column.  part[item] = the FP64 sum over the warp's pixels (summed in a
+    // fixed order afterwards, for the normalised sigma).  One warp per (b,
+    // agent, super-voxel).
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const AuxSmem a = aux_smem(smem, vpad, wmax);
@@ -944,7 +978,7 @@ __global__ void theta2_kernel(const uint8_t *__restrict__ cols, const int64_t *_
         if (lane == 0) t2g[(int64_t)i * nx + j] = (float)acc;
         sum += acc;
     }
-    if (lane == 0) atomicAdd(total, sum);
+    if (lane == 0) part[item] = sum;
 }
 
 // One Jacobi iteration of the plug-and-play denoiser H (Algorithm 3): the
@@ -1012,7 +1046,7 @@ static void launch_forward_t(mace_state *st, unsigned blocks)
     const size_t sm = 8 * aux_warp_bytes(M->vpad, M->wmax);
     cudaFuncSetAttribute(forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     forward_kernel<T><<<blocks, 256, sm, st->stream>>>(M->d_cols, M->d_sv_base, M->d_col_off, M->d_band, M->d_view_off,
-                                                       st->d_eL, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
+                                                       st->d_dacc, st->d_X, st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
                                                        M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax);
 }
 
@@ -1023,34 +1057,35 @@ static int launch_forward(mace_state *st)
     int64_t items = (int64_t)st->B * M->N * M->nsv;
     unsigned blocks = (unsigned)((items * 32 + 255) / 256);
     int64_t tot = (int64_t)st->B * st->ne;
-    reset_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, tot);
+    reset_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_y, st->d_eL, st->d_dacc, tot);
     // forward_geometry 0 (auto): from the geometry when the stored values are
     // rounded (BF16/FP16), from the stored values when they are FP32
     const bool geo = st->P.forward_geometry == 1 || (st->P.forward_geometry == 0 && M->dtype != MACE_F32);
     if (geo) {
         const size_t sm = 8 * aux_warp_bytes(M->vpad, M->wmax);
         cudaFuncSetAttribute(forward_geometry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        forward_geometry_kernel<<<blocks, 256, sm, st->stream>>>(M->d_vgeo, M->d_band, M->d_view_off, st->d_eL, st->d_X,
+        forward_geometry_kernel<<<blocks, 256, sm, st->stream>>>(M->d_vgeo, M->d_band, M->d_view_off, st->d_dacc, st->d_X,
                                                                  st->B, M->N, M->nsv, M->nsvx, M->S, M->geo.nx,
                                                                  M->geo.ny, M->geo.D, st->ne, M->vpad, M->wmax);
-        CUDA_TRY(cudaGetLastError());
-        return MACE_OK;
+    } else {
+        switch (M->dtype) {
+        case MACE_F32: launch_forward_t<float>(st, blocks); break;
+        case MACE_BF16: launch_forward_t<__nv_bfloat16>(st, blocks); break;
+        default: launch_forward_t<__half>(st, blocks); break;
+        }
     }
-    switch (M->dtype) {
-    case MACE_F32: launch_forward_t<float>(st, blocks); break;
-    case MACE_BF16: launch_forward_t<__nv_bfloat16>(st, blocks); break;
-    default: launch_forward_t<__half>(st, blocks); break;
-    }
+    // e = y - A X: the products were summed in fixed point (any order)
+    fold_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_eL, st->d_dacc, tot);
     CUDA_TRY(cudaGetLastError());
     return MACE_OK;
 }
 
-static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26)
+static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26, bool det)
 {
     switch (M->dtype) {
-    case MACE_F32: return mace_sweep_kernel_f32(M->max_views, K, nb26);
-    case MACE_BF16: return mace_sweep_kernel_bf16(M->max_views, K, nb26);
-    default: return mace_sweep_kernel_f16(M->max_views, K, nb26);
+    case MACE_F32: return mace_sweep_kernel_f32(M->max_views, K, nb26, det);
+    case MACE_BF16: return mace_sweep_kernel_bf16(M->max_views, K, nb26, det);
+    default: return mace_sweep_kernel_f16(M->max_views, K, nb26, det);
     }
 }
 
@@ -1105,12 +1140,35 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.b26[1] = (float)(1.0 / std::sqrt(2.0) / b3);
     A.b26[2] = (float)(1.0 / std::sqrt(3.0) / b3);
     A.nwarps = st->sweep_warps;
+    A.phase = st->d_phase;
+    A.dacc = st->d_dacc;
     dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
-    sweep_fn fn = sweep_kernel_ptr(M, st->chains, st->P.neighbourhood == 26);
+    sweep_fn fn = sweep_kernel_ptr(M, st->chains, st->P.neighbourhood == 26, st->P.deterministic != 0);
     if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix");
-    fn<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    if (st->P.deterministic) {
+        // lock-step phases need every warp of a pair resident at once: a
+        // cooperative launch guarantees it; the changes of e are folded in
+        // after the launch
+        const int pairs = (st->B / st->chains) * M->N;
+        CUDA_TRY(cudaMemsetAsync(st->d_phase, 0, sizeof(unsigned) * pairs, st->stream));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = st->sweep_smem;
+        cfg.stream = st->stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, A));
+        const int64_t tot = (int64_t)st->B * st->ne;
+        fold_error_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st->stream>>>(st->d_eL, st->d_dacc, tot);
+    } else {
+        fn<<<grid, block, st->sweep_smem, st->stream>>>(A);
+    }
     if (rec) {
         CUDA_TRY(cudaEventRecord(st->ev[st->ev_used + 1], st->stream));
         st->ev_used += 2;
@@ -1139,7 +1197,7 @@ static int configure_sweep(mace_state *st)
         st->warp_smem = warp_smem_layout(M->vpad, M->wmax, col_stride, M->S, K, nb26).total;
         const int R = sweep_rounds(M->max_views, K);
         const bool ovf_ok = M->max_n3 <= sweep_ovf_rounds(R, K) * (32 / K);
-        fn = ovf_ok ? sweep_kernel_ptr(M, K, nb26) : nullptr;
+        fn = ovf_ok ? sweep_kernel_ptr(M, K, nb26, st->P.deterministic != 0) : nullptr;
         if (fn && st->warp_smem <= (size_t)max_smem) break;
         if (K == 1) break;
         K = 1;
@@ -1192,6 +1250,9 @@ static int configure_sweep(mace_state *st)
             for (int64_t b = 0; b < C; ++b)
                 if (start[b] + j < start[b + 1]) st->sv_order[k++] = start[b] + j;
     }
+    if (st->P.deterministic && !st->d_phase &&
+        cudaMalloc(&st->d_phase, sizeof(unsigned) * (st->B / st->chains) * M->N) != cudaSuccess)
+        return fail(MACE_ENOMEM, "cudaMalloc phase counters");
     if (!st->d_sv_order && cudaMalloc(&st->d_sv_order, sizeof(int32_t) * M->nsv) != cudaSuccess)
         return fail(MACE_ENOMEM, "cudaMalloc sv order");
     CUDA_TRY(cudaMemcpyAsync(st->d_sv_order, st->sv_order.data(), sizeof(int32_t) * M->nsv, cudaMemcpyHostToDevice,
@@ -1222,6 +1283,7 @@ static int check_params(const mace_params *P)
     if (P->pnp != 0 && P->pnp != 1) return fail(MACE_EINVAL, "pnp must be 0 or 1");
     if (P->forward_geometry < 0 || P->forward_geometry > 2)
         return fail(MACE_EINVAL, "forward_geometry must be 0, 1 or 2");
+    if (P->deterministic != 0 && P->deterministic != 1) return fail(MACE_EINVAL, "deterministic must be 0 or 1");
     if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
         return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
@@ -1231,6 +1293,8 @@ extern "C" void mace_free_state(mace_state *st)
 {
     if (!st) return;
     cudaFree(st->d_eL);
+    cudaFree(st->d_dacc);
+    cudaFree(st->d_phase);
     cudaFree(st->d_y);
     cudaFree(st->d_w);
     cudaFree(st->d_X);
@@ -1324,6 +1388,7 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
         return fail(code, msg);
     };
     if (cudaMalloc(&st->d_eL, sizeof(float2) * m) != cudaSuccess ||
+        cudaMalloc(&st->d_dacc, sizeof(unsigned long long) * m) != cudaSuccess ||
         cudaMalloc(&st->d_y, sizeof(float) * m) != cudaSuccess ||
         cudaMalloc(&st->d_w, sizeof(float) * NN) != cudaSuccess ||
         cudaMalloc(&st->d_X, sizeof(float) * NN) != cudaSuccess ||
@@ -1377,9 +1442,9 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     // theta2 per (b, agent, pixel) and its mean; sigma in image units
     {
         double *d_t2 = nullptr;
+        const int64_t t2items = (int64_t)batch * M->N * M->nsv;
         double h_t2 = 0.0;
-        ce = cudaMalloc(&d_t2, sizeof(double));
-        if (ce == cudaSuccess) ce = cudaMemsetAsync(d_t2, 0, sizeof(double), s);
+        ce = cudaMalloc(&d_t2, sizeof(double) * (t2items + 1));
         if (ce == cudaSuccess) ce = cudaMemsetAsync(st->d_theta2, 0, sizeof(float) * NN, s);
         if (ce == cudaSuccess) {
             int64_t items = (int64_t)batch * M->N * M->nsv;
@@ -1405,7 +1470,11 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
                                                           st->d_theta2, d_t2);
             }
             ce = cudaGetLastError();
-            if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_t2, d_t2, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) {
+                sum_fixed_kernel<<<1, 1024, 0, s>>>(d_t2, t2items, d_t2 + t2items);
+                ce = cudaGetLastError();
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_t2, d_t2 + t2items, sizeof(double), cudaMemcpyDeviceToHost, s);
         }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         cudaFree(d_t2);

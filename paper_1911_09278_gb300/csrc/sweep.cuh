@@ -48,7 +48,31 @@ struct SweepArgs {
     float inv_sx2, inv_Tsx, qexp, half_q_inv_sx2;   // prior constants (quadratic: inv_Tsx = 0)
     float b_edge, b_diag;       // 8-neighbourhood weights (face, diagonal)
     float b26[3];               // 26-neighbourhood weights by squared distance 1, 2, 3
+    // deterministic mode: the C warps of a (group, agent) pair run their
+    // super-voxels in lock-step phases (counter per pair, zero at launch);
+    // changes of e go to the fixed-point accumulator, e is read as e + dacc
+    unsigned *phase;
+    unsigned long long *dacc;   // [B][V][D]
 };
+
+// Phase counter of a (group, agent) pair: every warp adds 1 when it has read
+// a phase's state and 1 when it has written its changes.  Waits are bounded;
+// on expiry they return false (the caller flags the host and leaves).
+__device__ __forceinline__ void phase_arrive(unsigned *c)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
+}
+__device__ __forceinline__ bool phase_wait(unsigned *c, unsigned target)
+{
+    uint32_t spins = 0;
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if ((int)(v - target) >= 0) return true;
+        if (++spins > kSpinLimit) return false;
+        __nanosleep(64);
+    }
+}
 
 typedef void (*sweep_fn)(SweepArgs);
 
@@ -170,8 +194,9 @@ struct ColRaw {
 
 // R: rounds of views per lane (R * 32/K >= the agent's views); RO: rounds of
 // the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
-// z-stack of one volume, 26-neighbourhood prior (K = 1).
-template <typename T, int K, int R, int RO, bool NB26>
+// z-stack of one volume, 26-neighbourhood prior (K = 1).  DET: deterministic
+// mode (lock-step phases, fixed-point changes of e).
+template <typename T, int K, int R, int RO, bool NB26, bool DET>
 __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -277,6 +302,8 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     // chain k: reconstruction grp*K + k
     auto rb_of = [&](int k) { return (int64_t)(grp * K + k); };
     float2 *const eLh = A.eL + rb_of(h) * A.ne + (int64_t)v0 * A.D;   // this lane's chain, agent g
+    unsigned long long *const dacch = DET ? A.dacc + rb_of(h) * A.ne + (int64_t)v0 * A.D : nullptr;
+    unsigned *const phase_c = DET ? A.phase + pair : nullptr;
     auto Xk = [&](int k) { return A.X + (rb_of(k) * A.N + g) * n; };
 
     // --- super-voxel metadata -------------------------------------------
@@ -325,7 +352,11 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     };
 
     int sv = sv_of(0);
-    if (sv < 0) return;
+    if (sv < 0) {
+        if (DET && lane == 0)
+            for (int p = 0; p < 2 * ((A.nsv + Cw - 1) / Cw); ++p) phase_arrive(A.phase + pair);
+        return;
+    }
     // first super-voxel: metadata with plain loads
     {
         const uint32_t *coff = A.col_off + ((int64_t)g * A.nsv + sv) * (S2 + 1);
@@ -437,11 +468,24 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         const int si = sv / A.nsvx, sj = sv - si * A.nsvx;
         const int i0 = si * S, j0 = sj * S;
 
+        // deterministic mode: this phase's reads wait for every warp of the
+        // pair to have written the previous phase's changes
+        if (DET && m > 0) {
+            bool ok = true;
+            if (lane == 0) ok = phase_wait(phase_c, 2u * (unsigned)Cw * (unsigned)m);
+            if (!__shfl_sync(FULL, ok ? 1 : 0, 0)) {
+                if (lane == 0) atomicExch(A.status, kStatusTimeout);
+                drain();
+                return;
+            }
+            __threadfence();
+        }
         // --- band (e, Lambda) of every chain, X tiles, theta2 ---------------
         // the lanes of chain h load and later flush the entries of chain h,
         // lane hl taking views hl, hl + 32/K, ... (the same lane for the same
         // global entry in every super-voxel, so a flushed change is seen by
         // the next load of that entry); e also goes into the snapshot
+        // (deterministic mode: once the accumulated changes are added)
         for (int v = hl; v < Vg; v += LPC) {
             const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
             const int len = (int)(d >> 16);
@@ -449,7 +493,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
             for (int t = 0; t < len; ++t) {
                 cp_async8_s(ds, src + t);
-                cp_async4_s(ss, src + t);
+                if (!DET) cp_async4_s(ss, src + t);
                 ds += tstr;
                 ss += sstr;
             }
@@ -462,8 +506,13 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             for (int ti = tr0; ti < TS; ti += trs)
                 for (int tj = tc0; tj < TS; tj += 32) {
                     const int i = i0 + ti - 1, j = j0 + tj - 1;
-                    if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) cp_async4(&xt[ti * TS + tj], &Xg[(int64_t)i * A.nx + j]);
-                    else xt[ti * TS + tj] = 0.f;
+                    // deterministic mode: other warps' X through L2 (L1 may be stale)
+                    if (i >= 0 && i < A.ny && j >= 0 && j < A.nx) {
+                        if (DET) xt[ti * TS + tj] = __ldcg(&Xg[(int64_t)i * A.nx + j]);
+                        else cp_async4(&xt[ti * TS + tj], &Xg[(int64_t)i * A.nx + j]);
+                    } else {
+                        xt[ti * TS + tj] = 0.f;
+                    }
                 }
             const float *t2g = A.theta2 + (rb_of(k) * A.N + g) * n;
             for (int q = lane; q < count; q += 32) {
@@ -480,9 +529,12 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
                 for (int ti = tr0; ti < TS; ti += trs)
                     for (int tj = tc0; tj < TS; tj += 32) {
                         const int i = i0 + ti - 1, j = j0 + tj - 1;
-                        if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx)
-                            cp_async4(&ht[ti * TS + tj], &Xz[(int64_t)i * A.nx + j]);
-                        else ht[ti * TS + tj] = 0.f;
+                        if (Xz && i >= 0 && i < A.ny && j >= 0 && j < A.nx) {
+                            if (DET) ht[ti * TS + tj] = __ldcg(&Xz[(int64_t)i * A.nx + j]);
+                            else cp_async4(&ht[ti * TS + tj], &Xz[(int64_t)i * A.nx + j]);
+                        } else {
+                            ht[ti * TS + tj] = 0.f;
+                        }
                     }
             }
         }
@@ -512,6 +564,26 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         }
         if (lane == 0) status_seen = *((volatile int *)A.status);
         cp_async_wait_all();
+        if (DET) {
+            // e = e at launch + the changes accumulated so far; snapshot;
+            // then this warp's reads of the phase are done
+            for (int v = hl; v < Vg; v += LPC) {
+                const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
+                const int len = (int)(d >> 16);
+                const unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
+                uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+#pragma unroll 4
+                for (int t = 0; t < len; ++t) {
+                    const float e = lds_f32(ds) + efix_value(__ldcg(da + t));
+                    sts_f32(ds, e);
+                    sts_f32(ss, e);
+                    ds += tstr;
+                    ss += sstr;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) phase_arrive(phase_c);
+        }
         __syncwarp();
         status_seen = __shfl_sync(FULL, status_seen, 0);
         count_n = 0;
@@ -631,6 +703,17 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         // sequence went on past this one
         have_cur = dec - seq0 > (uint32_t)count;
 
+        // deterministic mode: write only once every warp of the pair has read
+        // this phase's state
+        if (DET) {
+            bool ok = true;
+            if (lane == 0) ok = phase_wait(phase_c, 2u * (unsigned)Cw * (unsigned)m + (unsigned)Cw);
+            if (!__shfl_sync(FULL, ok ? 1 : 0, 0)) {
+                if (lane == 0) atomicExch(A.status, kStatusTimeout);
+                drain();
+                return;
+            }
+        }
         // --- write back: X tiles and the change of e ---------------------------
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -647,12 +730,19 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             const int len = (int)(d >> 16);
             float2 *eg = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
             uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+            unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
             for (int t = 0; t < len; ++t) {
                 const float de = lds_f32(ds) - lds_f32(ss);
-                if (de != 0.f) atomicAdd(&eg[t].x, de);
+                if (DET) efix_add(da + t, de);
+                else if (de != 0.f) atomicAdd(&eg[t].x, de);
                 ds += tstr;
                 ss += sstr;
             }
+        }
+        if (DET) {
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) phase_arrive(phase_c);
         }
         __syncwarp();
         // hand the staged next-super-voxel state over; its successor's list
@@ -662,6 +752,15 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         count = count_n;
         count_n = 0;
         cur ^= 1;
+        if (sv < 0 && DET && lane == 0) {
+            // phases past this warp's last super-voxel: nothing to read or
+            // write, but the pair's counter counts every warp
+            const int nph = (A.nsv + Cw - 1) / Cw;
+            for (int p = m + 1; p < nph; ++p) {
+                phase_arrive(phase_c);
+                phase_arrive(phase_c);
+            }
+        }
     }
 }
 
@@ -670,30 +769,34 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
 inline int sweep_rounds(int max_views, int K) { return (max_views + 32 / K - 1) / (32 / K); }
 inline int sweep_ovf_rounds(int R, int K) { return (K == 2 || R >= 3) ? 2 : 1; }
 
-template <typename T, int K, bool NB26>
+template <typename T, int K, bool NB26, bool DET>
 static sweep_fn sweep_lookup_k(int R)
 {
     switch (R) {
-    case 1: return icd_sweep_kernel<T, K, 1, (K == 2 ? 2 : 1), NB26>;
-    case 2: return icd_sweep_kernel<T, K, 2, (K == 2 ? 2 : 1), NB26>;
-    case 3: return icd_sweep_kernel<T, K, 3, 2, NB26>;
-    case 4: return icd_sweep_kernel<T, K, 4, 2, NB26>;
+    case 1: return icd_sweep_kernel<T, K, 1, (K == 2 ? 2 : 1), NB26, DET>;
+    case 2: return icd_sweep_kernel<T, K, 2, (K == 2 ? 2 : 1), NB26, DET>;
+    case 3: return icd_sweep_kernel<T, K, 3, 2, NB26, DET>;
+    case 4: return icd_sweep_kernel<T, K, 4, 2, NB26, DET>;
     default: return nullptr;
     }
 }
 
-// The sweep kernel for agents of at most max_views views with K chains and
-// the 8- or 26-neighbourhood; nullptr if that combination is not built.
+// The sweep kernel for agents of at most max_views views with K chains, the
+// 8- or 26-neighbourhood and the free or deterministic schedule; nullptr if
+// that combination is not built.
 template <typename T>
-static sweep_fn sweep_lookup(int max_views, int K, bool nb26)
+static sweep_fn sweep_lookup(int max_views, int K, bool nb26, bool det)
 {
     const int R = sweep_rounds(max_views, K);
-    if (nb26) return K == 1 ? sweep_lookup_k<T, 1, true>(R) : nullptr;
-    if (K == 1) return sweep_lookup_k<T, 1, false>(R);
-    if (K == 2) return sweep_lookup_k<T, 2, false>(R);
+    if (nb26) {
+        if (K != 1) return nullptr;
+        return det ? sweep_lookup_k<T, 1, true, true>(R) : sweep_lookup_k<T, 1, true, false>(R);
+    }
+    if (K == 1) return det ? sweep_lookup_k<T, 1, false, true>(R) : sweep_lookup_k<T, 1, false, false>(R);
+    if (K == 2) return det ? sweep_lookup_k<T, 2, false, true>(R) : sweep_lookup_k<T, 2, false, false>(R);
     return nullptr;
 }
 
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26);
-__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26, bool det);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26, bool det);
+__attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26, bool det);

@@ -2,7 +2,7 @@
 // per value type, so the library's device code compiles in parallel).
 #include "sweep.cuh"
 
-sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26)
+sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26, bool det)
 {
-    return sweep_lookup<float>(max_views, K, nb26);
+    return sweep_lookup<float>(max_views, K, nb26, det);
 }
