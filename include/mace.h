@@ -203,11 +203,21 @@ int mace_sysmatrix_column(const mace_sysmatrix *sm, int32_t g, int32_t i, int32_
  * ordered on cuda_stream.  All arrays of a state below carry the leading
  * batch dimension.
  * Errors: MACE_EINVAL (batch not in [1, 4096], parameters out of range,
- * non-finite or negative weights, more than 128 views in an agent),
- * MACE_ENOMEM, MACE_ECUDA. */
+ * non-finite or negative weights), MACE_ENOMEM, MACE_ECUDA. */
 int mace_init(const mace_sysmatrix *sm, int32_t batch, const float *y, const float *weights,
               int32_t ptr_is_device, const mace_params *params, const float *w0,
               void *cuda_stream, mace_state **out);
+
+/* Device memory a state of `batch` reconstructions on this matrix with these
+ * parameters takes: *persistent = the bytes mace_init allocates and keeps
+ * until mace_free_state; *peak = that plus its transient buffers during
+ * mace_init (input staging when ptr_is_device == 0, per-super-voxel
+ * partial sums).  For admission control by a server (Sec. IV serves no
+ * requests; this is the library's own accounting).  mace_prox_pass
+ * allocates one more [batch][n_agents][n] float32 array on first use, not
+ * counted here.  Errors: MACE_EINVAL (as mace_init's parameter checks). */
+int mace_state_bytes(const mace_sysmatrix *sm, int32_t batch, const mace_params *params,
+                     int32_t ptr_is_device, int64_t *persistent, int64_t *peak);
 
 /* Run n_iters Mann iterations of Algorithm 1 on every reconstruction of the
  * batch.  residual_out (may be NULL) receives the largest relative Mann
@@ -260,9 +270,9 @@ int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_device);
  * 1048576 floats = batch * nz * ny * nx; larger requests return MACE_EINVAL).
  * That array belongs to the library for the life of the process on every
  * GPU that loads it, and all calls on one GPU share it: calls whose GPU work
- * overlaps (other streams or host threads) race on it.  The first call on a
- * GPU looks up the array's address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  Calls no allocator. */
+ * overlaps (other streams or host threads) race on it.  mace_init looks up
+ * the array's device address (cudaGetSymbolAddress) and keeps it in the
+ * state, so this call does no set-up of its own.  Calls no allocator. */
 int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_is_device);
 
 /* Checkpoint / resume: the complete algorithm state is (w, X) (Eq.

@@ -33,7 +33,7 @@ EXPORTS = [
     "mace_get_visit_order",
     "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_poll_async", "mace_poll_ready",
     "mace_reconstruct", "mace_consensus",
-    "mace_set_timing", "mace_get_timing", "mace_wait_selftest", "mace_consensus_noalloc",
+    "mace_set_timing", "mace_get_timing", "mace_wait_selftest", "mace_consensus_noalloc", "mace_state_bytes",
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
@@ -97,6 +97,8 @@ def load(path=LIB_PATH):
     L.mace_get_visit_order.argtypes = [vp, vp]
     L.mace_init.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(Params), vp, vp, pp]
     L.mace_iterate.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.mace_state_bytes.argtypes = [vp, i32, ctypes.POINTER(Params), i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.mace_state_bytes.restype = ctypes.c_int
     L.mace_launch.argtypes = [vp, i32]
     L.mace_poll.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.mace_poll_async.argtypes = [vp]
@@ -382,6 +384,15 @@ def _out_ptr(a, n):
     if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
         raise ValueError("output array must be contiguous float32 with %d elements" % n)
     return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def mace_state_bytes(sm, params, batch=1, inputs_on_device=False):
+    """(persistent, peak) device bytes of a state mace_init would create."""
+    p = ctypes.c_int64()
+    q = ctypes.c_int64()
+    _check(load().mace_state_bytes(sm.handle, batch, ctypes.byref(params), int(bool(inputs_on_device)),
+                                   ctypes.byref(p), ctypes.byref(q)))
+    return p.value, q.value
 
 
 def mace_init(sm, y, weights, params, w0=None, stream=None, batch=None):

@@ -191,6 +191,46 @@ __device__ __forceinline__ void sts_f32(uint32_t a, float v)
 {
     asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a)
+{
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+    return v;
+}
+// stored values at a shared address, widened to float: one, or two adjacent
+template <typename T> __device__ __forceinline__ float lds_val(uint32_t a);
+template <> __device__ __forceinline__ float lds_val<float>(uint32_t a) { return lds_f32(a); }
+template <> __device__ __forceinline__ float lds_val<__nv_bfloat16>(uint32_t a)
+{
+    return __uint_as_float(lds_u16(a) << 16);
+}
+template <> __device__ __forceinline__ float lds_val<__half>(uint32_t a)
+{
+    return __half2float(__ushort_as_half((unsigned short)lds_u16(a)));
+}
+template <typename T> __device__ __forceinline__ float2 lds_pair(uint32_t a);
+template <> __device__ __forceinline__ float2 lds_pair<float>(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+template <> __device__ __forceinline__ float2 lds_pair<__nv_bfloat16>(uint32_t a)
+{
+    const uint32_t w = lds_u32(a);
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+template <> __device__ __forceinline__ float2 lds_pair<__half>(uint32_t a)
+{
+    const uint32_t w = lds_u32(a);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 

@@ -562,6 +562,18 @@ extern "C" void mace_free_sysmatrix(mace_sysmatrix *M)
 // ---------------------------------------------------------------------------
 // reconstruction state
 // ---------------------------------------------------------------------------
+// Device memory that mace_consensus_noalloc writes the consensus images into
+// before copying them to the host.  It is a file-scope array, so every GPU that
+// loads this library holds it (4 MiB) until the process exits, and every call
+// on that GPU shares it: the last call's images stay in it, and calls whose
+// GPU work overlaps (different streams, or different host threads) race on
+// it.  In host code its name is only a stand-in for the symbol; mace_init
+// looks up the device address (cudaGetSymbolAddress, on the state's device)
+// and keeps it in the state.
+static constexpr int64_t kNoAllocFloats = (int64_t)1 << 20;
+static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
+
+
 struct mace_state {
     const mace_sysmatrix *M;
     mace_params P;
@@ -583,6 +595,7 @@ struct mace_state {
     double h_c = 0.0;          // pnp: sigma^2 beta / sigma_x^2
     double *d_wbar = nullptr;  // [B][n]
     double *d_part = nullptr;  // [B][nblk_mann][2] residual partials
+    float *noalloc_addr = nullptr;   // device address of g_noalloc_images on the state's device
     double *d_resid = nullptr; // [B][3]: dw2, ww2, r
     int *d_status = nullptr;   // device status word
     std::vector<int32_t> sv_order;   // super-voxel visiting order of a forward pass
@@ -1196,13 +1209,13 @@ static int configure_sweep(mace_state *st)
     for (;;) {
         st->warp_smem = warp_smem_layout(M->vpad, M->wmax, col_stride, M->S, K, nb26).total;
         const int R = sweep_rounds(M->max_views, K);
-        const bool ovf_ok = M->max_n3 <= sweep_ovf_rounds(R, K) * (32 / K);
+        const bool ovf_ok = R > 4 || M->max_n3 <= sweep_ovf_rounds(R, K) * (32 / K);
         fn = ovf_ok ? sweep_kernel_ptr(M, K, nb26, st->P.deterministic != 0) : nullptr;
         if (fn && st->warp_smem <= (size_t)max_smem) break;
         if (K == 1) break;
         K = 1;
     }
-    if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix (more than 128 views per agent)");
+    if (!fn) return fail(MACE_EINVAL, "no sweep kernel for this matrix");
     if (st->warp_smem > (size_t)max_smem)
         return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
     st->chains = K;
@@ -1404,6 +1417,12 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     st->nblk_mann = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, nsm * 4 / batch), (per + 255) / 256));
     if (cudaMalloc(&st->d_part, sizeof(double) * 2 * st->nblk_mann * batch) != cudaSuccess)
         return bail(MACE_ENOMEM, "cudaMalloc failed for residual partials");
+    {
+        // the no-allocation read-out's array on this device (looked up here,
+        // outside any stream capture, with the state's device current)
+        const cudaError_t e = cudaGetSymbolAddress((void **)&st->noalloc_addr, g_noalloc_images);
+        if (e != cudaSuccess) return bail(MACE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
     cudaStream_t s = st->stream;
     // inputs: stage on the device, validate, pack agent-major
     float *d_yin = nullptr, *d_lin = nullptr;
@@ -1513,6 +1532,36 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
     ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return bail(MACE_ECUDA, std::string("init: ") + cudaGetErrorString(ce));
     *out = st;
+    return MACE_OK;
+}
+
+extern "C" int mace_state_bytes(const mace_sysmatrix *M, int32_t batch, const mace_params *params,
+                                int32_t ptr_is_device, int64_t *persistent, int64_t *peak)
+{
+    if (!M || !persistent || !peak) return fail(MACE_EINVAL, "NULL argument");
+    if (batch < 1 || batch > 4096) return fail(MACE_EINVAL, "batch must be in [1, 4096]");
+    const int rc = check_params(params);
+    if (rc) return rc;
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // what mace_init allocates, call for call
+    const int64_t n = (int64_t)M->geo.nx * M->geo.ny, B = batch;
+    const int64_t m = B * (int64_t)M->V * M->geo.D, NN = B * M->N * n;
+    const int64_t per = (int64_t)M->N * n;
+    const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(std::max(1, nsm * 4 / batch), (per + 255) / 256));
+    const int K = (params->chains >= 2 && batch % 2 == 0 && params->neighbourhood != 26) ? 2 : 1;
+    int64_t p = m * (8 + 8 + 4)                 // (e, Lambda), changes of e, y
+                + NN * 4 * 3                    // w, X, theta2
+                + B * n * 8 + B * 3 * 8 + 4     // consensus, residuals, status
+                + nblk * 2 * B * 8              // residual partials
+                + (int64_t)M->nsv * 4;          // super-voxel order
+    if (params->pnp) p += 2 * B * n * 8;
+    if (params->deterministic) p += (B / K) * M->N * 4;
+    // transient during mace_init: input staging, the view map, theta2 partials
+    const int64_t t = (ptr_is_device ? 0 : 2 * m * 4) + (int64_t)M->V * 4 + (B * M->N * M->nsv + 1) * 8;
+    *persistent = p;
+    *peak = p + t;
     return MACE_OK;
 }
 
@@ -1740,17 +1789,6 @@ extern "C" int mace_consensus(mace_state *st, float *x_out, int32_t ptr_is_devic
 // ---------------------------------------------------------------------------
 // Consensus image without any allocation
 // ---------------------------------------------------------------------------
-// Device memory that mace_consensus_noalloc writes the consensus images into
-// before copying them to the host.  It is a file-scope array, so every GPU that
-// loads this library holds it (4 MiB) until the process exits, and every call
-// on that GPU shares it: the last call's images stay in it, and calls whose
-// GPU work overlaps (different streams, or different host threads) race on
-// it.  In host code its name is only a stand-in for the symbol; the device
-// address is looked up once per GPU with cudaGetSymbolAddress.
-static constexpr int64_t kNoAllocFloats = (int64_t)1 << 20;
-static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
-static float *g_noalloc_addr[256] = {nullptr};
-
 extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_is_device)
 {
     if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
@@ -1759,18 +1797,7 @@ extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_
     if (!ptr_is_device) {
         if (Bn > kNoAllocFloats)
             return fail(MACE_EINVAL, "batch x image larger than the 1048576-float no-allocation buffer");
-        int dev = 0;
-        CUDA_TRY(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= 256) return fail(MACE_EINVAL, "device index out of range");
-        if (!g_noalloc_addr[dev]) {
-            // first call on this GPU: look up the array's device address
-            cudaError_t e = cudaGetSymbolAddress((void **)&g_noalloc_addr[dev], g_noalloc_images);
-            if (e != cudaSuccess) {
-                g_noalloc_addr[dev] = nullptr;
-                return fail(MACE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            }
-        }
-        d_x = g_noalloc_addr[dev];
+        d_x = st->noalloc_addr;
     }
     const int rc = apply_consensus(st, d_x);
     if (rc) return rc;

@@ -204,6 +204,9 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     static_assert(!NB26 || K == 1, "volumes run one chain per warp");
     static_assert((kRing & (kRing - 1)) == 0 && kRing >= 3, "ring size is a power of two >= 4");
     constexpr int LPC = 32 / K;                 // lanes per chain
+    // R = 0: any number of views, each column decoded from its ring slot at
+    // use (RR, RRO size the prefetch registers of the R > 0 kernels)
+    constexpr int RR = R > 0 ? R : 1, RRO = RO > 0 ? RO : 1;
     constexpr int vb = (int)sizeof(T);
     const int S = A.S, S2 = S * S, TS = S + 2, TA = TS * TS;
     const int lS = 31 - __clz(S);               // S is a power of two
@@ -266,7 +269,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     const uint32_t voff0 = (uint32_t)(v01 + 2 * vb * hl);           // view hl's value pair
     uint32_t vokm = 0;        // bit j: round j's view exists
 #pragma unroll
-    for (int j = 0; j < R; ++j) vokm |= (hl + LPC * j < Vg ? 1u : 0u) << j;
+    for (int j = 0; j < RR; ++j) vokm |= (hl + LPC * j < Vg ? 1u : 0u) << j;
     // tile rows of P lanes (P a power of two >= S + 2, at most 32)
     const int lP = TS <= 8 ? 3 : TS <= 16 ? 4 : 5;
     const int tr0 = lane >> lP, tc0 = lane & ((1 << lP) - 1), trs = 32 >> lP;
@@ -298,6 +301,8 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     float *xth = xt0 + h * TA;                   // this lane's chain's X tile
     const float2 *vt2h = vt20 + h * S2;
     const float *nb_tile = (pdz == 0 ? xth : (pdz < 0 ? halo_lo : halo_hi)) + noff;
+    const uint32_t xth_s = smem_u32(xth), nbt_s = smem_u32(nb_tile), vt2h_s = smem_u32(vt2h);
+    const uint32_t ring_s = smem_u32(ring);
 
     // chain k: reconstruction grp*K + k
     auto rb_of = [&](int k) { return (int64_t)(grp * K + k); };
@@ -412,18 +417,18 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         return true;
     };
     // read column dec from its ring slot (first half of decoding: the loads)
-    auto col_load = [&](ColRaw<R, RO> &w) {
+    auto col_load = [&](ColRaw<RR, RRO> &w) {
         const uint8_t *col = ring + (size_t)(dec & (kRing - 1)) * A.col_stride;
         w.n3 = *(const uint16_t *)col;
         const uint8_t *ch = col + hoff0, *cv = col + voff0;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < RR; ++j) {
             w.hb[j] = ch[LPC * j];
             w.a[j] = ld_pair<T>(cv + 2 * vb * LPC * j, 0);
         }
         const int ovv = (ovc + 2 * w.n3 + 3) & ~3;
 #pragma unroll
-        for (int o = 0; o < RO; ++o) {
+        for (int o = 0; o < RRO; ++o) {
             const int i = hl + LPC * o;
             const int il = i < w.n3 ? i : 0;
             w.code[o] = *(const uint16_t *)(col + ovc + 2 * il);
@@ -432,16 +437,16 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     };
     // second half: band addresses and values; then the slot of the column
     // decoded before is refilled with the next column of the sequence
-    auto col_finish = [&](const ColRaw<R, RO> &w, ColRegs<R, RO> &c, const uint2 *cl, const uint2 *cl_n) {
+    auto col_finish = [&](const ColRaw<RR, RRO> &w, ColRegs<RR, RRO> &c, const uint2 *cl, const uint2 *cl_n) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = 0; j < RR; ++j) {
             const bool ok = (vokm >> j) & 1u;
             c.addr[j] = ok ? lbase0 + 256u * j + (w.hb[j] & 63u) * tstr : sink_s - tstr;
             c.a0[j] = ok ? w.a[j].x : 0.f;
             c.a1[j] = ok ? w.a[j].y : 0.f;
         }
 #pragma unroll
-        for (int o = 0; o < RO; ++o) {
+        for (int o = 0; o < RRO; ++o) {
             const bool ok = hl + LPC * o < w.n3;
             c.oaddr[o] = ok ? band_s + (w.code[o] * K + h) * 8u : sink_s;
             c.a2[o] = ok ? w.a2[o] : 0.f;
@@ -455,7 +460,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     };
 
     int status_seen = 0;
-    ColRegs<R, RO> cc, cn;
+    ColRegs<RR, RRO> cc, cn;
     bool have_cur = false;    // cc holds the current super-voxel's first column
 
     for (int m = 0; sv >= 0; ++m) {
@@ -601,9 +606,9 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             drain();
             return;
         }
-        if (!have_cur && count > 0) {
+        if (R > 0 && !have_cur && count > 0) {
             if (!wait_column()) return;
-            ColRaw<R, RO> w0;
+            ColRaw<RR, RRO> w0;
             col_load(w0);
             col_finish(w0, cc, cl, cl_n);
             have_cur = true;
@@ -613,17 +618,17 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         // one pixel with its column in c; the next column (this super-voxel's
         // or the next one's first) is decoded into c2 meanwhile.  False when a
         // bounded wait gave up.
-        auto pixel = [&](int q, ColRegs<R, RO> &c, ColRegs<R, RO> &c2) {
+        auto pixel = [&](int q, ColRegs<RR, RRO> &c, ColRegs<RR, RRO> &c2) {
             // gathers of this pixel's band entries (the previous pixel's
             // update is visible after its __syncwarp)
-            float2 g0[R], g1[R], g2[RO];
+            float2 g0[RR], g1[RR], g2[RRO];
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
+            for (int j = 0; j < RR; ++j) {
                 g0[j] = lds_f2(c.addr[j]);
                 g1[j] = lds_f2(c.addr[j] + tstr);
             }
 #pragma unroll
-            for (int o = 0; o < RO; ++o) g2[o] = lds_f2(c.oaddr[o]);
+            for (int o = 0; o < RRO; ++o) g2[o] = lds_f2(c.oaddr[o]);
             // prior through the surrogate weights (lane l of a chain:
             // neighbour l), from the X tiles only.  No branch: out-of-image
             // neighbours and idle lanes get weight 0.
@@ -648,17 +653,17 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             // prior's gradient; theta2 = sum A^2 Lambda is stored
             float pa = pr1, pc = 0.f;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
+            for (int j = 0; j < RR; ++j) {
                 pa = fmaf(-c.a0[j] * g0[j].y, g0[j].x, pa);
                 pc = fmaf(-c.a1[j] * g1[j].y, g1[j].x, pc);
             }
 #pragma unroll
-            for (int o = 0; o < RO; ++o) pa = fmaf(-c.a2[o] * g2[o].y, g2[o].x, pa);
+            for (int o = 0; o < RRO; ++o) pa = fmaf(-c.a2[o] * g2[o].y, g2[o].x, pa);
             float p1 = pa + pc;
             const bool more = dec - seq0 < (uint32_t)(count + count_n);
             if (more) {
                 if (!wait_column()) return false;
-                ColRaw<R, RO> wn;
+                ColRaw<RR, RRO> wn;
                 col_load(wn);
                 col_finish(wn, c2, cl, cl_n);
             }
@@ -670,19 +675,98 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             // update e: a lane's own views' entries, and its share of the
             // three-channel list (idle lanes write the zero sink with value 0)
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
+            for (int j = 0; j < RR; ++j) {
                 sts_f(c.addr[j], fmaf(-c.a0[j], alpha, g0[j].x));
                 sts_f(c.addr[j] + tstr, fmaf(-c.a1[j], alpha, g1[j].x));
             }
 #pragma unroll
-            for (int o = 0; o < RO; ++o) sts_f(c.oaddr[o], fmaf(-c.a2[o], alpha, g2[o].x));
+            for (int o = 0; o < RRO; ++o) sts_f(c.oaddr[o], fmaf(-c.a2[o], alpha, g2[o].x));
             // X update: every lane of the chain stores the same value
             xth[tc] = xs + alpha;
             __syncwarp();
             return true;
         };
+        // R = 0: one pixel, its column decoded from the ring slot as it is
+        // used (views and list entries in run-time rounds, re-read for the
+        // update); the slot of the column before is refilled at the start
+        const uint32_t pl_s = smem_u32(pl);
+        auto pixel_any = [&](int q) {
+            if (!wait_column()) return false;
+            const uint32_t col = ring_s + (dec & (kRing - 1)) * (uint32_t)A.col_stride;
+            const int n3 = (int)lds_u16(col);
+            const uint32_t ovv = col + (uint32_t)((ovc + 2 * n3 + 3) & ~3);
+            ++dec;
+            if (issued - dec < (uint32_t)(kRing - 1) && issued - seq0 < (uint32_t)(count + count_n)) {
+                const uint2 rf = list_entry(issued - seq0, cl, cl_n);
+                issue(issued, col_src(rf), rf.y);
+                ++issued;
+            }
+            const uint32_t pq = lds_u32(pl_s + 4u * q);
+            const uint32_t tc4 = (pq & 0x7FFu) * 4u;
+            const float2 vq = lds_f2(vt2h_s + 8u * q);
+            const float xs = lds_f32(xth_s + tc4);
+            const float d = xs - lds_f32(nbt_s + tc4);
+            const float pbv = ((pq >> (11 + mbit)) & 1u) ? pb : 0.f;
+            float pr2 = pbv * prior_weight(A, d);
+            const float pr1 = pr2 * d;
+            const float prox = fmaf(xs, A.inv_s2, -vq.x);
+            if (NB26) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+            } else {
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+                pr2 = __shfl_sync(FULL, pr2, lane & ~(LPC - 1));
+            }
+            const int nr = (Vg + LPC - 1) / LPC, nro = (n3 + LPC - 1) / LPC;
+            float pa = pr1, pc = 0.f;
+            for (int j = 0; j < nr; ++j) {
+                const int v = hl + LPC * j;
+                if (v < Vg) {
+                    const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
+                    const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
+                    const float2 e0 = lds_f2(ad), e1 = lds_f2(ad + tstr);
+                    pa = fmaf(-a.x * e0.y, e0.x, pa);
+                    pc = fmaf(-a.y * e1.y, e1.x, pc);
+                }
+            }
+            for (int o = 0; o < nro; ++o) {
+                const int i = hl + LPC * o;
+                if (i < n3) {
+                    const uint32_t ad = band_s + (lds_u16(col + ovc + 2u * i) * K + h) * 8u;
+                    const float2 e2 = lds_f2(ad);
+                    pa = fmaf(-lds_val<T>(ovv + vb * i) * e2.y, e2.x, pa);
+                }
+            }
+            float p1 = pa + pc;
+#pragma unroll
+            for (int o = LPC / 2; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
+            const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
+            for (int j = 0; j < nr; ++j) {
+                const int v = hl + LPC * j;
+                if (v < Vg) {
+                    const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
+                    const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
+                    sts_f(ad, fmaf(-a.x, alpha, lds_f32(ad)));
+                    sts_f(ad + tstr, fmaf(-a.y, alpha, lds_f32(ad + tstr)));
+                }
+            }
+            for (int o = 0; o < nro; ++o) {
+                const int i = hl + LPC * o;
+                if (i < n3) {
+                    const uint32_t ad = band_s + (lds_u16(col + ovc + 2u * i) * K + h) * 8u;
+                    sts_f(ad, fmaf(-lds_val<T>(ovv + vb * i), alpha, lds_f32(ad)));
+                }
+            }
+            sts_f32(xth_s + tc4, xs + alpha);
+            __syncwarp();
+            return true;
+        };
         int q = 0;
-        if constexpr (R <= 3) {
+        if constexpr (R == 0) {
+            for (; q < count; ++q)
+                if (!pixel_any(q)) return;
+        } else if constexpr (R <= 3) {
             // two pixels per trip, the decoded columns alternating between
             // cc and cn (no register copy)
             for (; q + 1 < count; q += 2) {
@@ -695,7 +779,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
                 cc = cn;
             }
         }
-        if (q < count) {
+        if (R > 0 && q < count) {
             if (!pixel(q, cc, cn)) return;
             cc = cn;
         }
@@ -777,13 +861,14 @@ static sweep_fn sweep_lookup_k(int R)
     case 2: return icd_sweep_kernel<T, K, 2, (K == 2 ? 2 : 1), NB26, DET>;
     case 3: return icd_sweep_kernel<T, K, 3, 2, NB26, DET>;
     case 4: return icd_sweep_kernel<T, K, 4, 2, NB26, DET>;
-    default: return nullptr;
+    default: return icd_sweep_kernel<T, K, 0, 1, NB26, DET>;   // any view count
     }
 }
 
 // The sweep kernel for agents of at most max_views views with K chains, the
-// 8- or 26-neighbourhood and the free or deterministic schedule; nullptr if
-// that combination is not built.
+// 8- or 26-neighbourhood and the free or deterministic schedule (agents of
+// more than four rounds of views run the kernel that decodes at use); nullptr
+// if that combination is not built.
 template <typename T>
 static sweep_fn sweep_lookup(int max_views, int K, bool nb26, bool det)
 {

@@ -13,8 +13,10 @@ point where convergence was seen) and waiting ones admitted as slots and
 device memory free up.  Stored system matrices are shared by every request
 with the same geometry and partition and stay resident.
 
-Admission is by device-memory footprint: the request's state plus, for a new
-geometry, its system matrix must fit the budget next to what is resident.
+Admission is by device-memory footprint: the request's state (the library's
+own count, mace_state_bytes, once its geometry's matrix is resident) plus,
+for a new geometry, its system matrix must fit the budget next to what is
+resident.
 This module only orchestrates; every step of a reconstruction runs in
 libmace.so.
 """
@@ -23,19 +25,23 @@ import time
 
 import numpy as np
 
-from . import (MaceError, Sysmatrix, load, make_params, mace_build_sysmatrix, mace_init)  # noqa: F401
+from . import (MaceError, Sysmatrix, load, make_params, mace_build_sysmatrix, mace_init,  # noqa: F401
+               mace_state_bytes)
 
 Request = collections.namedtuple(
     "Request", "rid arrival nx ny n_views n_channels n_agents y lam sigma_x view_agent")
 
 
 def state_bytes(nx, ny, n_views, n_channels, n_agents):
-    """Device bytes of one reconstruction state (mace_init): (e, Lambda) and y
-    per measurement, w and X per agent and pixel, the FP64 consensus and
-    small per-agent counters."""
+    """Estimated device bytes of one reconstruction state, for a geometry
+    whose system matrix is not built yet (then the library's exact count,
+    mace_state_bytes, is not available): per measurement (e, Lambda), the
+    fixed-point accumulator of changes of e and y; per agent and pixel w, X
+    and theta2; the FP64 consensus; the host inputs' staging during
+    mace_init; and a margin for the small buffers."""
     m = n_views * n_channels
     n = nx * ny
-    return m * (8 + 4) + n_agents * n * (4 + 4) + n * 8 + 65536
+    return m * (8 + 8 + 4 + 8) + n_agents * n * (4 + 4 + 4) + n * 8 + (1 << 20)
 
 
 class Server:
@@ -78,10 +84,25 @@ class Server:
         return self.matrices[k]
 
     def _matrix_estimate(self, r):
-        # nnz ~ pixels * views * (1 + 4/pi) for square pixels on channels of the
-        # same pitch; (index, value) per entry plus padding
+        # per (pixel, view): a header byte and two values, and for about 27 %
+        # of them a third value with its 2-byte list entry; 16-byte column
+        # padding; offsets and band descriptors
         vb = 4 if self.dtype == "f32" else 2
-        return int(r.nx * r.ny * r.n_views * 2.3 * (2 + vb) * 1.1)
+        n = r.nx * r.ny
+        return int(n * r.n_views * (1 + 2 * vb + 0.3 * (2 + vb)) * 1.05 + n * r.n_agents * 12)
+
+    def _params(self, r):
+        return make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
+
+    def _state_need(self, r):
+        """(bytes to admit, bytes held while active) of request r's state: the
+        library's count when its matrix is resident, else the estimate."""
+        k = self._key(r)
+        if k in self.matrices:
+            persistent, peak = mace_state_bytes(self.matrices[k], self._params(r), batch=1)
+            return peak, persistent
+        est = state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)
+        return est + self._matrix_estimate(r), est
 
     def run(self, requests, serial=False, now=time.perf_counter):
         """Serve `requests` (arrival times in seconds from the start).  With
@@ -101,9 +122,7 @@ class Server:
             limit = 1 if serial else self.max_active
             while pending and pending[0].arrival <= t and len(active) < limit:
                 r = pending[0]
-                new_matrix = self._key(r) not in self.matrices
-                need = state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)
-                need += self._matrix_estimate(r) if new_matrix else 0
+                need, _ = self._state_need(r)
                 held = self._resident() + sum(a["bytes"] for a in active)
                 if held + need > self.budget and active:
                     break
@@ -112,7 +131,7 @@ class Server:
                 try:
                     sm = self._matrix(r)
                     stream = torch.cuda.Stream()
-                    prm = make_params(sigma_x=r.sigma_x, max_iter=self.max_iter, **self.params)
+                    prm = self._params(r)
                     st = mace_init(sm, r.y, r.lam, prm, stream=stream)
                     # first chunk, its status copy, and the next chunk behind it
                     st.launch(self.chunk)
@@ -126,7 +145,7 @@ class Server:
                         st.close()
                     continue
                 active.append(dict(req=r, st=st, stream=stream, start=now() - t0, seen=seen,
-                                   bytes=state_bytes(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents)))
+                                   bytes=self._state_need(r)[1]))
             if not active:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (now() - t0))))

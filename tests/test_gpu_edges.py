@@ -114,3 +114,76 @@ def test_geometry_limits(gpu_lib):
     with pytest.raises(mace.MaceError) as ei:
         mace.mace_build_sysmatrix(16, 16, 0, 23, 1)
     assert ei.value.code == mace.MACE_EINVAL
+
+
+@pytest.mark.parametrize("chains", [1, 2])
+def test_many_views_per_agent(gpu_lib, chains):
+    """Agents with more views than four rounds of lanes (here 150 views per
+    agent) run the sweep variant that decodes each column as it is used: one
+    pass at concurrency 1 equals Algorithm 2 in the library's order, and the
+    converged image equals the oracle's MAP image (relative RMSE 1e-4)."""
+    mace = gpu_lib
+    n, V, D, N = 40, 300, 59, 2
+    E = synth.ellipses(37, n, 0.02 * 64 / n)
+    p = synth.sinogram(E, V, D)
+    y, lam = synth.measurements(p, 2e4, synth.CounterRNG(137))
+    sx = synth.prior_sigma_x(lam, V, frac=1.0)
+    P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior="qggmrf", sigma_x=sx)
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=4)
+    batch = chains
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=0.5, sigma_mode=1, concurrency=1, chains=chains)
+    st = mace.mace_init(sm, np.stack([y] * batch), np.stack([lam] * batch), prm, batch=batch)
+    assert st.stats()["chains"] == chains
+    rng = np.random.default_rng(3)
+    xs, _, _ = P.central_icd(max_sweeps=20000, tol=1e-13)
+    X0 = (xs[None, None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((batch, N, n * n))).astype(np.float32)
+    v = (xs[None, None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((batch, N, n * n))).astype(np.float32)
+    st.set_state(X0.copy(), X0.copy())
+    st.prox_pass(v)
+    _, Xg = st.get_state()
+    Xg = Xg.reshape(batch, N, n * n)
+    sigma = st.stats()["sigma_abs"]
+    order = st.visit_order()
+    for b in range(batch):
+        for g in range(N):
+            x = X0[b, g].astype(np.float64)
+            e = P.error_sinogram(g, x)
+            P.icd_sweep(g, x, e, v=v[b, g].astype(np.float64), sigma=sigma, order=order)
+            assert nrmse(Xg[b, g], x) < 2e-5, (b, g)
+    st.close()
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=0.5, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
+                           symmetric=True, recompute_every=10, max_iter=4000, tol=1e-7, concurrency=4, chains=chains)
+    st = mace.mace_init(sm, np.stack([y] * batch), np.stack([lam] * batch), prm, batch=batch)
+    x, iters, r, conv = st.reconstruct()
+    st.close()
+    sm.close()
+    assert conv
+    for b in range(batch):
+        err = nrmse(np.asarray(x).reshape(batch, -1)[b], xs)
+        print("150 views per agent, chains %d: iters %d, NRMSE vs oracle %.2e" % (chains, iters, err))
+        assert err < 1e-4
+
+
+def test_state_bytes_matches_device_usage(gpu_lib):
+    """mace_state_bytes (the server's admission count) against the device
+    memory mace_init actually takes (cudaMemGetInfo around it): the
+    persistent bytes, up to the allocator's rounding."""
+    import torch
+    mace = gpu_lib
+    n, V, D, N, B = 256, 360, 363, 16, 2
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=4)
+    prm = mace.make_params(prior="qggmrf", sigma_x=1.0, sigma=0.1, concurrency=-1, chains=2)
+    persistent, peak = mace.mace_state_bytes(sm, prm, batch=B)
+    assert peak > persistent > 0
+    y = np.ones((B, V, D), np.float32)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st = mace.mace_init(sm, y, y, prm, batch=B)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    print("state bytes: library %d, measured %d" % (persistent, used))
+    assert persistent <= used + (2 << 20)
+    assert used <= persistent + (32 << 20)
+    st.close()
+    sm.close()

@@ -122,6 +122,25 @@ def test_slots_and_budget_limit_admission(fake_server):
     assert active["max"] == 2          # the budget holds two states
 
 
+def test_admission_uses_the_library_footprint(fake_server, monkeypatch):
+    """Once a geometry's matrix is resident, admission counts the library's
+    own footprint of a state (mace_state_bytes: the peak during mace_init to
+    admit, the persistent bytes while active)."""
+    make, active = fake_server
+    calls = []
+
+    def fake_state_bytes(sm, prm, batch=1, inputs_on_device=False):
+        calls.append(batch)
+        return 1000, 1500
+    monkeypatch.setattr(serve, "mace_state_bytes", fake_state_bytes)
+    srv = make(max_active=8, budget=2 * 1000 + 1500 - 1)
+    reqs = _requests([20] * 5)
+    srv.matrices[srv._key(reqs[0])] = object()
+    out = srv.run(reqs)
+    assert len(out["results"]) == 5 and calls
+    assert active["max"] == 2          # 1000 + 1000 held, a third needs 1500 more
+
+
 def test_serial_mode_is_one_at_a_time_in_arrival_order(fake_server):
     make, active = fake_server
     srv = make(max_active=4)
