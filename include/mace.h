@@ -138,7 +138,19 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   and the changes are summed in 64-bit fixed point, so every run, alone or
  *   beside other work, eagerly or from a captured graph, gives the same bits.
  *   The e recompute and the initial normalisation are order-independent in
- *   both modes. */
+ *   both modes.
+ *   schedule: how warps get super-voxels.  0 (fixed) = C warps per
+ *   (reconstruction, agent) pair, every one resident for the whole pass,
+ *   warp c taking the c-th of every C super-voxels of its pair's order (C
+ *   from concurrency, capped so that every pair fits on the GPU at once);
+ *   1 (work queue) = a persistent grid of every resident warp takes work
+ *   items from a counter, an item being one of `concurrency` interleaved
+ *   shares of one pair's order (0 or -1: one per row of super-voxels), so
+ *   any number of pairs runs, a warp that finishes early takes more work,
+ *   and slices of a volume (neighbourhood 26) are swept even ones first,
+ *   then odd ones, each reading neighbour slices that are not being
+ *   updated.  Schedule 1 runs one chain per warp and the free mode
+ *   (deterministic 0). */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -157,6 +169,7 @@ typedef struct {
     int32_t pnp;
     int32_t forward_geometry;
     int32_t deterministic;
+    int32_t schedule;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */
@@ -307,6 +320,28 @@ int mace_recompute_error(mace_state *st);
  * reconstructions one warp updates together. */
 int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
                    double *last_residual, int32_t *concurrency, int32_t *chains);
+
+/* Groups: the Mann iterations of several states (different scans,
+ * geometries and parameters; params.schedule = 1, neighbourhood 8, one
+ * stored value type) advanced together, the ICD passes of all of them in
+ * one queue-fed launch per pass, so a small reconstruction does not hold
+ * the GPU alone and warps that finish one state's work take another's.
+ * mace_group_create takes the member states (not owned; each must outlive
+ * the group and belong to no group launch in flight on another stream)
+ * and the CUDA stream (NULL = legacy default) the group enqueues on.
+ * mace_group_launch enqueues n_iters Mann iterations of every member
+ * (Algorithm 1 per member; each member's iterates are those of
+ * mace_launch on it alone, up to the order of float additions); the group's
+ * stream first waits for each member's stream, and each member's stream
+ * then waits for the group's, so mace_poll / mace_poll_async /
+ * mace_consensus on a member see the group's iterations.  Returns without
+ * waiting.  mace_group_free releases the group's descriptors (not the
+ * members).  Errors: MACE_EINVAL (schedule 0 or volume members, a member
+ * twice, mixed value types), MACE_ENOMEM, MACE_ECUDA. */
+typedef struct mace_group mace_group;
+int mace_group_create(mace_state *const *members, int32_t n, void *cuda_stream, mace_group **out);
+int mace_group_launch(mace_group *group, int32_t n_iters);
+int mace_group_free(mace_group *group);
 
 /* CUDA-event timing of the ICD sweep launches on the state's stream:
  * mace_set_timing(st, 1, max_launches) starts recording (up to max_launches

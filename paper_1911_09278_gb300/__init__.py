@@ -37,6 +37,7 @@ EXPORTS = [
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
+    "mace_group_create", "mace_group_launch", "mace_group_free",
 ]
 
 
@@ -67,7 +68,8 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32),
                 ("chains", ctypes.c_int32), ("pnp", ctypes.c_int32),
-                ("forward_geometry", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
+                ("forward_geometry", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -123,13 +125,17 @@ def load(path=LIB_PATH):
     L.mace_free_sysmatrix.argtypes = [vp]
     L.mace_free_sysmatrix.restype = None
     L.mace_last_error.restype = ctypes.c_char_p
+    L.mace_group_create.argtypes = [ctypes.POINTER(vp), i32, vp, pp]
+    L.mace_group_launch.argtypes = [vp, i32]
+    L.mace_group_free.argtypes = [vp]
     for name in ("mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
                  "mace_get_visit_order",
                  "mace_init", "mace_iterate", "mace_launch", "mace_poll", "mace_poll_async", "mace_poll_ready",
-    "mace_reconstruct", "mace_consensus",
-    "mace_set_timing", "mace_get_timing",
+                 "mace_reconstruct", "mace_consensus",
+                 "mace_set_timing", "mace_get_timing",
                  "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
-                 "mace_recompute_error", "mace_get_stats"):
+                 "mace_recompute_error", "mace_get_stats",
+                 "mace_group_create", "mace_group_launch", "mace_group_free"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -230,14 +236,17 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
                 max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0, pnp=False,
-                forward_geometry=None, deterministic=False):
+                forward_geometry=None, deterministic=False, schedule=0):
     """forward_geometry: None = the library's default (the geometry-evaluated
     e recompute for BF16/FP16 stored values), True = always from the
-    geometry, False = always from the stored values."""
+    geometry, False = always from the stored values.  schedule: 0 = fixed
+    warps per (reconstruction, agent) pair, 1 = a persistent grid fed from
+    a work queue."""
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
                   max_iter, tol, concurrency, sv_order, chains, int(bool(pnp)),
-                  0 if forward_geometry is None else (1 if forward_geometry else 2), int(bool(deterministic)))
+                  0 if forward_geometry is None else (1 if forward_geometry else 2), int(bool(deterministic)),
+                  int(schedule))
 
 
 class State:
@@ -413,6 +422,38 @@ def mace_init(sm, y, weights, params, w0=None, stream=None, batch=None):
     _check(load().mace_init(sm.handle, batch, py, pl, dy, ctypes.byref(params), pw, _stream_handle(stream),
                             ctypes.byref(h)))
     return State(h, sm, params, batch)
+
+
+class Group:
+    """Several states advanced together (mace_group_create): their ICD
+    passes share one queue-fed launch per pass.  The members are borrowed
+    and must outlive the group."""
+
+    def __init__(self, states, stream=None):
+        self.states = list(states)
+        arr = (ctypes.c_void_p * len(self.states))(*[st.handle for st in self.states])
+        h = ctypes.c_void_p()
+        _check(load().mace_group_create(arr, len(self.states), _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, n_iters):
+        """Enqueue n_iters Mann iterations of every member (no wait)."""
+        _check(load().mace_group_launch(self.handle, n_iters))
+
+    def close(self):
+        if self.handle:
+            load().mace_group_free(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mace_group_create(states, stream=None):
+    return Group(states, stream=stream)
 
 
 def mace_wait_selftest(spin_limit=1000, stream=None):

@@ -574,6 +574,16 @@ static constexpr int64_t kNoAllocFloats = (int64_t)1 << 20;
 static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
 
 
+// One configuration of the queue-fed sweep for a set of matrices (one state,
+// or the states of a group): the kernel for the most views per agent, and a
+// shared-memory layout large enough for every one of them.
+struct QueueLaunch {
+    sweep_queue_fn fn = nullptr;
+    int vpad = 0, wmax = 0, col_stride = 16, S = 4;
+    int wpb = 1, blocks = 0;
+    size_t smem = 0;
+};
+
 struct mace_state {
     const mace_sysmatrix *M;
     mace_params P;
@@ -618,6 +628,13 @@ struct mace_state {
     int iters = 0;
     double last_resid = INFINITY;
     int sweep_warps = 0, sweep_wpb = 0, concurrency = 0, chains = 1;
+    // work-queue schedule: descriptors (forward, backward, explicit v),
+    // item offsets per z parity ([0, items] twice), item counter
+    SweepArgs *d_qtab = nullptr;
+    int *d_qoff = nullptr;
+    unsigned *d_qcnt = nullptr;
+    int q_items[2] = {0, 0};
+    QueueLaunch q;
     size_t sweep_smem = 0, warp_smem = 0;
 };
 
@@ -1102,7 +1119,9 @@ static sweep_fn sweep_kernel_ptr(const mace_sysmatrix *M, int K, bool nb26, bool
     }
 }
 
-static int launch_sweep(mace_state *st, int backward, const float *vexp)
+// The sweep's arguments for this state (one pass, forward or backward, with
+// v formed from the consensus or given explicitly).
+static SweepArgs sweep_args(const mace_state *st, int backward, const float *vexp)
 {
     const mace_sysmatrix *M = st->M;
     SweepArgs A;
@@ -1152,9 +1171,20 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     A.b26[0] = (float)(1.0 / b3);
     A.b26[1] = (float)(1.0 / std::sqrt(2.0) / b3);
     A.b26[2] = (float)(1.0 / std::sqrt(3.0) / b3);
-    A.nwarps = st->sweep_warps;
+    // the fixed schedule's warp count; the work queue's rows per pair
+    A.nwarps = st->P.schedule == 1 ? st->concurrency : st->sweep_warps;
     A.phase = st->d_phase;
     A.dacc = st->d_dacc;
+    return A;
+}
+
+static int launch_sweep_queue(mace_state *st, int backward, const float *vexp);
+
+static int launch_sweep(mace_state *st, int backward, const float *vexp)
+{
+    if (st->P.schedule == 1) return launch_sweep_queue(st, backward, vexp);
+    const mace_sysmatrix *M = st->M;
+    const SweepArgs A = sweep_args(st, backward, vexp);
     dim3 grid((st->sweep_warps + st->sweep_wpb - 1) / st->sweep_wpb), block(32 * st->sweep_wpb);
     const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
     if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
@@ -1190,7 +1220,161 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
     return MACE_OK;
 }
 
-static int configure_sweep(mace_state *st)
+// --- work-queue launches ------------------------------------------------------
+static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26)
+{
+    switch (dt) {
+    case MACE_F32: return mace_sweep_queue_kernel_f32(max_views, nb26);
+    case MACE_BF16: return mace_sweep_queue_kernel_bf16(max_views, nb26);
+    default: return mace_sweep_queue_kernel_f16(max_views, nb26);
+    }
+}
+
+static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, QueueLaunch *L)
+{
+    int max_views = 1;
+    for (int k = 0; k < n; ++k) {
+        const mace_sysmatrix *M = Ms[k];
+        if (M->dtype != Ms[0]->dtype) return fail(MACE_EINVAL, "a queue-fed launch needs one stored value type");
+        if (M->bytes_cols >= ((int64_t)1 << 36)) return fail(MACE_EINVAL, "stored matrix larger than 64 GiB");
+        max_views = std::max(max_views, M->max_views);
+        L->vpad = std::max(L->vpad, M->vpad);
+        L->wmax = std::max(L->wmax, M->wmax);
+        L->col_stride = std::max(L->col_stride, (M->max_col_bytes + 15) & ~15);
+        L->S = std::max(L->S, M->S);
+    }
+    int dev = 0, nsm = 0, max_smem = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t per_warp = warp_smem_layout(L->vpad, L->wmax, L->col_stride, L->S, 1, nb26).total +
+                            ((sizeof(SweepArgs) + 15) & ~(size_t)15);
+    if (per_warp > (size_t)max_smem)
+        return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
+    // the kernel with enough rounds of views per lane for every matrix; the
+    // generic one (decoding each column as it is used) when a column's
+    // three-channel list is longer than that kernel's rounds hold
+    const int R = sweep_rounds(max_views, 1);
+    if (R <= 4)
+        for (int k = 0; k < n; ++k)
+            if (Ms[k]->max_n3 > sweep_ovf_rounds(R, 1) * 32) max_views = 5 * 32 + 1;
+    L->fn = queue_kernel_ptr(Ms[0]->dtype, max_views, nb26);
+    if (!L->fn) return fail(MACE_EINVAL, "no queue-fed sweep kernel for this matrix");
+    CUDA_TRY(cudaFuncSetAttribute(L->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    int best = 0;
+    for (int w = 1; w <= 8; ++w) {
+        if (per_warp * w > (size_t)max_smem) break;
+        int b = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, L->fn, 32 * w, per_warp * w));
+        if (b * w > best) { best = b * w; L->wpb = w; L->blocks = b * nsm; }
+    }
+    if (best < 1) return fail(MACE_EINVAL, "the queue-fed sweep cannot be resident");
+    L->smem = per_warp * L->wpb;
+    return MACE_OK;
+}
+
+// One queue-fed launch over the items of a table of requests: every resident
+// warp takes items until none is left (counter zeroed first, on the stream)
+static int queue_run(const QueueLaunch &L, const SweepArgs *d_table, const int *d_off, unsigned *d_cnt, int nreq,
+                     int total, int zpar, cudaStream_t s)
+{
+    if (total <= 0) return MACE_OK;
+    CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s));
+    QueueArgs Q;
+    Q.table = d_table;
+    Q.offsets = d_off;
+    Q.counter = d_cnt;
+    Q.nreq = nreq;
+    Q.total = total;
+    Q.zpar = zpar;
+    Q.vpad = L.vpad;
+    Q.wmax = L.wmax;
+    Q.col_stride = L.col_stride;
+    Q.S = L.S;
+    L.fn<<<L.blocks, 32 * L.wpb, L.smem, s>>>(Q);
+    CUDA_TRY(cudaGetLastError());
+    return MACE_OK;
+}
+
+// items of one state for z parity p (volumes) or all groups (p < 0)
+static int queue_items(const mace_state *st, int p)
+{
+    const int groups = p < 0 ? st->B : (st->B - p + 1) / 2;
+    return groups * st->M->N * st->concurrency;
+}
+
+static int launch_sweep_queue(mace_state *st, int backward, const float *vexp)
+{
+    const QueueLaunch &L = st->q;
+    const bool nb26 = st->P.neighbourhood == 26;
+    int rc = MACE_OK;
+    const SweepArgs *tab = st->d_qtab + (backward ? 1 : 0);
+    if (vexp) {
+        // an explicit v (the single-pass entry point): its own descriptor,
+        // written in stream order (the pageable source is staged at the call)
+        const SweepArgs A = sweep_args(st, backward, vexp);
+        CUDA_TRY(cudaMemcpyAsync(st->d_qtab + 2, &A, sizeof(SweepArgs), cudaMemcpyHostToDevice, st->stream));
+        tab = st->d_qtab + 2;
+    }
+    const bool rec = st->timing && st->ev_used + 2 <= (int)st->ev.size();
+    if (rec) CUDA_TRY(cudaEventRecord(st->ev[st->ev_used], st->stream));
+    if (nb26) {
+        // even slices, then odd: a slice's 26-neighbourhood is fixed while it
+        // is updated (z-parity phases)
+        for (int p = 0; p < 2 && rc == MACE_OK; ++p)
+            rc = queue_run(L, tab, st->d_qoff + 2 * p, st->d_qcnt, 1, st->q_items[p], p, st->stream);
+    } else {
+        rc = queue_run(L, tab, st->d_qoff, st->d_qcnt, 1, st->q_items[0], -1, st->stream);
+    }
+    if (rc) return rc;
+    if (rec) {
+        CUDA_TRY(cudaEventRecord(st->ev[st->ev_used + 1], st->stream));
+        st->ev_used += 2;
+    }
+    return MACE_OK;
+}
+
+// Set-up of the queue-fed schedule for one state: the launch configuration
+// and the rows of super-voxels per (reconstruction, agent) pair
+static int configure_queue(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    if (st->P.deterministic) return fail(MACE_EINVAL, "the deterministic mode runs the fixed schedule (schedule 0)");
+    const mace_sysmatrix *Ms[1] = {M};
+    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, &st->q);
+    if (rc) return rc;
+    st->chains = 1;
+    // items per pair: `concurrency` rows (0 or -1: one per super-voxel row)
+    int64_t C = st->P.concurrency > 0 ? st->P.concurrency : M->nsvy;
+    C = std::max<int64_t>(1, std::min<int64_t>(C, M->nsv));
+    st->concurrency = (int)C;
+    st->sweep_warps = (int)std::min<int64_t>((int64_t)st->q.blocks * st->q.wpb, (int64_t)st->B * M->N * C);
+    st->sweep_wpb = st->q.wpb;
+    st->sweep_smem = st->q.smem;
+    return MACE_OK;
+}
+
+// The queue's descriptors (forward and backward pass) and item offsets, in
+// device memory; written once the super-voxel order is resident
+static int queue_tables(mace_state *st)
+{
+    if (!st->d_qtab && (cudaMalloc(&st->d_qtab, 3 * sizeof(SweepArgs)) != cudaSuccess ||
+                        cudaMalloc(&st->d_qoff, 4 * sizeof(int)) != cudaSuccess ||
+                        cudaMalloc(&st->d_qcnt, sizeof(unsigned)) != cudaSuccess))
+        return fail(MACE_ENOMEM, "cudaMalloc queue descriptors");
+    const bool nb26 = st->P.neighbourhood == 26;
+    st->q_items[0] = queue_items(st, nb26 ? 0 : -1);
+    st->q_items[1] = nb26 ? queue_items(st, 1) : 0;
+    const int off[4] = {0, st->q_items[0], 0, st->q_items[1]};
+    const SweepArgs tab[2] = {sweep_args(st, 0, nullptr), sweep_args(st, 1, nullptr)};
+    CUDA_TRY(cudaMemcpy(st->d_qoff, off, sizeof(off), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(st->d_qtab, tab, sizeof(tab), cudaMemcpyHostToDevice));
+    return MACE_OK;
+}
+
+// Set-up of the fixed schedule: chains per warp, the kernel, the block size
+// and C warps per (batch group, agent) pair, all resident
+static int configure_fixed(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
     int dev = 0;
@@ -1198,9 +1382,7 @@ static int configure_sweep(mace_state *st)
     int nsm = 0, max_smem = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    int col_stride = (M->max_col_bytes + 15) & ~15;
-    // the sweep addresses columns in 16-byte units with 32 bits
-    if (M->bytes_cols >= ((int64_t)1 << 36)) return fail(MACE_EINVAL, "stored matrix larger than 64 GiB");
+    const int col_stride = (M->max_col_bytes + 15) & ~15;
     // chains per warp: reconstructions of the batch that share each column
     // load (two when asked and the batch is even; volumes run one)
     const bool nb26 = st->P.neighbourhood == 26;
@@ -1246,6 +1428,18 @@ static int configure_sweep(mace_state *st)
     st->sweep_smem = st->warp_smem * w;
     st->sweep_warps = (int)warps;
     st->concurrency = (int)C;
+    return MACE_OK;
+}
+
+static int configure_sweep(mace_state *st)
+{
+    const mace_sysmatrix *M = st->M;
+    // the sweep addresses columns in 16-byte units with 32 bits
+    if (M->bytes_cols >= ((int64_t)1 << 36)) return fail(MACE_EINVAL, "stored matrix larger than 64 GiB");
+    const bool queue = st->P.schedule == 1;
+    int rc = queue ? configure_queue(st) : configure_fixed(st);
+    if (rc) return rc;
+    const int64_t C = st->concurrency;
     // super-voxel visiting order.  sv_order 0: the raster list of
     // super-voxels cut into C contiguous bands, interleaved so the C in flight
     // come from different bands (plain raster when C = 1); 1: a stride
@@ -1270,7 +1464,7 @@ static int configure_sweep(mace_state *st)
         return fail(MACE_ENOMEM, "cudaMalloc sv order");
     CUDA_TRY(cudaMemcpyAsync(st->d_sv_order, st->sv_order.data(), sizeof(int32_t) * M->nsv, cudaMemcpyHostToDevice,
                              st->stream));
-    return MACE_OK;
+    return queue ? queue_tables(st) : MACE_OK;
 }
 
 static int check_params(const mace_params *P)
@@ -1297,6 +1491,9 @@ static int check_params(const mace_params *P)
     if (P->forward_geometry < 0 || P->forward_geometry > 2)
         return fail(MACE_EINVAL, "forward_geometry must be 0, 1 or 2");
     if (P->deterministic != 0 && P->deterministic != 1) return fail(MACE_EINVAL, "deterministic must be 0 or 1");
+    if (P->schedule != 0 && P->schedule != 1) return fail(MACE_EINVAL, "schedule must be 0 or 1");
+    if (P->schedule == 1 && P->deterministic)
+        return fail(MACE_EINVAL, "the deterministic mode runs the fixed schedule (schedule 0)");
     if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
         return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
@@ -1319,6 +1516,9 @@ extern "C" void mace_free_state(mace_state *st)
     cudaFree(st->d_hbuf);
     cudaFree(st->d_status);
     cudaFree(st->d_sv_order);
+    cudaFree(st->d_qtab);
+    cudaFree(st->d_qoff);
+    cudaFree(st->d_qcnt);
     for (cudaEvent_t e : st->ev) cudaEventDestroy(e);
     if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
     if (st->poll_ev) cudaEventDestroy(st->poll_ev);
@@ -1550,7 +1750,8 @@ extern "C" int mace_state_bytes(const mace_sysmatrix *M, int32_t batch, const ma
     const int64_t m = B * (int64_t)M->V * M->geo.D, NN = B * M->N * n;
     const int64_t per = (int64_t)M->N * n;
     const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(std::max(1, nsm * 4 / batch), (per + 255) / 256));
-    const int K = (params->chains >= 2 && batch % 2 == 0 && params->neighbourhood != 26) ? 2 : 1;
+    const int K = (params->chains >= 2 && batch % 2 == 0 && params->neighbourhood != 26 && params->schedule == 0)
+                      ? 2 : 1;
     int64_t p = m * (8 + 8 + 4)                 // (e, Lambda), changes of e, y
                 + NN * 4 * 3                    // w, X, theta2
                 + B * n * 8 + B * 3 * 8 + 4     // consensus, residuals, status
@@ -1558,6 +1759,7 @@ extern "C" int mace_state_bytes(const mace_sysmatrix *M, int32_t batch, const ma
                 + (int64_t)M->nsv * 4;          // super-voxel order
     if (params->pnp) p += 2 * B * n * 8;
     if (params->deterministic) p += (B / K) * M->N * 4;
+    if (params->schedule == 1) p += 3 * (int64_t)sizeof(SweepArgs) + 4 * 4 + 4;   // queue descriptors
     // transient during mace_init: input staging, the view map, theta2 partials
     const int64_t t = (ptr_is_device ? 0 : 2 * m * 4) + (int64_t)M->V * 4 + (B * M->N * M->nsv + 1) * 8;
     *persistent = p;
@@ -1565,15 +1767,14 @@ extern "C" int mace_state_bytes(const mace_sysmatrix *M, int32_t batch, const ma
     return MACE_OK;
 }
 
-static int run_iteration(mace_state *st)
+// The two halves of a Mann iteration around its ICD passes (Algorithm 1):
+// the consensus G(w) before them; the Mann update, its residual and the
+// periodic e recompute after them
+static int iteration_pre(mace_state *st) { return apply_consensus(st, nullptr); }
+
+static int iteration_post(mace_state *st)
 {
     const mace_sysmatrix *M = st->M;
-    int rc0 = apply_consensus(st, nullptr);
-    if (rc0) return rc0;
-    for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
-        int rc = launch_sweep(st, st->P.symmetric ? (k & 1) : 0, nullptr);
-        if (rc) return rc;
-    }
     mann_kernel<<<dim3(st->nblk_mann, st->B), 256, 0, st->stream>>>(st->d_w, st->d_X, st->d_wbar, M->N, st->n,
                                                                     (float)st->P.rho, st->d_part);
     residual_kernel<<<st->B, 256, 0, st->stream>>>(st->d_part, st->nblk_mann, st->B, st->d_resid);
@@ -1581,6 +1782,17 @@ static int run_iteration(mace_state *st)
     st->iters++;
     if (st->P.recompute_every > 0 && st->iters % st->P.recompute_every == 0) return launch_forward(st);
     return MACE_OK;
+}
+
+static int run_iteration(mace_state *st)
+{
+    int rc = iteration_pre(st);
+    if (rc) return rc;
+    for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
+        rc = launch_sweep(st, st->P.symmetric ? (k & 1) : 0, nullptr);
+        if (rc) return rc;
+    }
+    return iteration_post(st);
 }
 
 // largest relative Mann residual over the batch from a host copy of d_resid
@@ -1734,6 +1946,133 @@ extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_ou
     int rc = mace_launch(st, n_iters);
     if (rc) return rc;
     return mace_poll(st, residual_out, converged_out);
+}
+
+// --- groups: several states' ICD passes in one queue-fed launch -------------
+struct mace_group {
+    std::vector<mace_state *> members;
+    cudaStream_t stream = nullptr;
+    QueueLaunch q;
+    int npass = 0;                       // largest sweeps_per_iter of the members
+    SweepArgs *d_tab = nullptr;          // [npass][n] descriptors of each pass's requests
+    int *d_off = nullptr;                // [npass][n + 1] first item of each request
+    unsigned *d_cnt = nullptr;
+    std::vector<int> nreq, total;        // per pass
+    cudaEvent_t done = nullptr;          // the group's work, for the members' streams
+    std::vector<cudaEvent_t> ready;      // each member's earlier work, for the group's stream
+};
+
+static void group_free(mace_group *G)
+{
+    cudaFree(G->d_tab);
+    cudaFree(G->d_off);
+    cudaFree(G->d_cnt);
+    if (G->done) cudaEventDestroy(G->done);
+    for (cudaEvent_t e : G->ready)
+        if (e) cudaEventDestroy(e);
+    delete G;
+}
+
+extern "C" int mace_group_create(mace_state *const *members, int32_t n, void *cuda_stream, mace_group **out)
+{
+    if (!members || !out) return fail(MACE_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1 || n > 65536) return fail(MACE_EINVAL, "a group has 1 to 65536 members");
+    std::vector<const mace_sysmatrix *> Ms(n);
+    for (int k = 0; k < n; ++k) {
+        const mace_state *st = members[k];
+        if (!st) return fail(MACE_EINVAL, "NULL member");
+        for (int j = 0; j < k; ++j)
+            if (members[j] == st) return fail(MACE_EINVAL, "a state appears twice in the group");
+        if (st->P.schedule != 1) return fail(MACE_EINVAL, "group members run the work-queue schedule (schedule 1)");
+        if (st->P.neighbourhood == 26) return fail(MACE_EINVAL, "volumes (neighbourhood 26) are not grouped");
+        Ms[k] = st->M;
+    }
+    mace_group *G = new mace_group();
+    G->members.assign(members, members + n);
+    G->stream = (cudaStream_t)cuda_stream;
+    int rc = queue_configure(Ms.data(), n, false, &G->q);
+    if (rc) { group_free(G); return rc; }
+    for (const mace_state *st : G->members) G->npass = std::max(G->npass, st->P.sweeps_per_iter);
+    // pass p: the members with more than p passes per iteration, each in
+    // its own direction (every second pass backward when symmetric)
+    std::vector<SweepArgs> tab((size_t)G->npass * n);
+    std::vector<int> off((size_t)G->npass * (n + 1), 0);
+    G->nreq.assign(G->npass, 0);
+    G->total.assign(G->npass, 0);
+    for (int p = 0; p < G->npass; ++p) {
+        int r = 0, t = 0;
+        for (const mace_state *st : G->members) {
+            if (st->P.sweeps_per_iter <= p) continue;
+            tab[(size_t)p * n + r] = sweep_args(st, st->P.symmetric ? (p & 1) : 0, nullptr);
+            off[(size_t)p * (n + 1) + r] = t;
+            t += queue_items(st, -1);
+            ++r;
+        }
+        off[(size_t)p * (n + 1) + r] = t;
+        G->nreq[p] = r;
+        G->total[p] = t;
+    }
+    if (cudaMalloc(&G->d_tab, sizeof(SweepArgs) * tab.size()) != cudaSuccess ||
+        cudaMalloc(&G->d_off, sizeof(int) * off.size()) != cudaSuccess ||
+        cudaMalloc(&G->d_cnt, sizeof(unsigned)) != cudaSuccess) {
+        group_free(G);
+        return fail(MACE_ENOMEM, "cudaMalloc group descriptors");
+    }
+    if (cudaMemcpy(G->d_tab, tab.data(), sizeof(SweepArgs) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(G->d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess) {
+        group_free(G);
+        return fail(MACE_ECUDA, "group set-up");
+    }
+    G->ready.assign(n, nullptr);
+    for (int k = 0; k < n; ++k)
+        if (cudaEventCreateWithFlags(&G->ready[k], cudaEventDisableTiming) != cudaSuccess) {
+            group_free(G);
+            return fail(MACE_ECUDA, "group events");
+        }
+    *out = G;
+    return MACE_OK;
+}
+
+extern "C" int mace_group_launch(mace_group *G, int32_t n_iters)
+{
+    if (!G) return fail(MACE_EINVAL, "group is NULL");
+    if (n_iters < 0) return fail(MACE_EINVAL, "n_iters must be >= 0");
+    if (n_iters == 0) return MACE_OK;
+    const int n = (int)G->members.size();
+    // the group's stream follows every member's earlier work
+    for (int k = 0; k < n; ++k) {
+        CUDA_TRY(cudaEventRecord(G->ready[k], G->members[k]->stream));
+        CUDA_TRY(cudaStreamWaitEvent(G->stream, G->ready[k], 0));
+    }
+    // members enqueue on the group's stream for the length of the call
+    std::vector<cudaStream_t> own(n);
+    for (int k = 0; k < n; ++k) {
+        own[k] = G->members[k]->stream;
+        G->members[k]->stream = G->stream;
+    }
+    int rc = MACE_OK;
+    for (int it = 0; it < n_iters && rc == MACE_OK; ++it) {
+        for (int k = 0; k < n && rc == MACE_OK; ++k) rc = iteration_pre(G->members[k]);
+        for (int p = 0; p < G->npass && rc == MACE_OK; ++p)
+            rc = queue_run(G->q, G->d_tab + (size_t)p * n, G->d_off + (size_t)p * (n + 1), G->d_cnt, G->nreq[p],
+                           G->total[p], -1, G->stream);
+        for (int k = 0; k < n && rc == MACE_OK; ++k) rc = iteration_post(G->members[k]);
+    }
+    for (int k = 0; k < n; ++k) G->members[k]->stream = own[k];
+    if (rc) return rc;
+    // and every member's later work follows the group's
+    CUDA_TRY(cudaEventRecord(G->done, G->stream));
+    for (int k = 0; k < n; ++k) CUDA_TRY(cudaStreamWaitEvent(G->members[k]->stream, G->done, 0));
+    return MACE_OK;
+}
+
+extern "C" int mace_group_free(mace_group *G)
+{
+    if (!G) return MACE_OK;
+    group_free(G);
+    return MACE_OK;
 }
 
 extern "C" int mace_set_timing(mace_state *st, int32_t enable, int32_t max_launches)

@@ -196,10 +196,25 @@ struct ColRaw {
 // the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
 // z-stack of one volume, 26-neighbourhood prior (K = 1).  DET: deterministic
 // mode (lock-step phases, fixed-point changes of e).
-template <typename T, int K, int R, int RO, bool NB26, bool DET>
-__global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
+// Per-warp set-up shared by the launches: ring barriers, and the band at
+// zero (entries outside a super-voxel's band are only ever read and written
+// with matrix value 0, so they stay finite whatever a previous super-voxel
+// left there).
+__device__ __forceinline__ void sweep_warp_init(uint8_t *base, const WarpSmem &Ly, int nband, int lane)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t *bars = (uint64_t *)(base + Ly.bars);
+    float2 *band = (float2 *)(base + Ly.band);
+    if (lane == 0)
+        for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
+    for (int f = lane; f <= nband; f += 32) band[f] = make_float2(0.f, 0.f);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+}
+
+template <typename T, int K, int R, int RO, bool NB26, bool DET, class ARGS>
+__device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem &Ly, const int grp, const int g,
+                                           const int cidx, const int Cw, uint32_t &dec, uint32_t &issued)
+{
     static_assert(K == 1 || K == 2, "one or two chains per warp");
     static_assert(!NB26 || K == 1, "volumes run one chain per warp");
     static_assert((kRing & (kRing - 1)) == 0 && kRing >= 3, "ring size is a power of two >= 4");
@@ -211,9 +226,6 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     const int S = A.S, S2 = S * S, TS = S + 2, TA = TS * TS;
     const int lS = 31 - __clz(S);               // S is a power of two
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const WarpSmem Ly = warp_smem_layout(A.vpad, A.wmax, A.col_stride, S, K, NB26);
-    uint8_t *base = smem + wib * Ly.total;
     uint8_t *ring = base + Ly.ring;
     uint64_t *bars = (uint64_t *)(base + Ly.bars);
     uint32_t *bdesc2 = (uint32_t *)(base + Ly.bdesc);
@@ -229,26 +241,11 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
 
     const int vpad = A.vpad, wmax = A.wmax;
     const int nrow = wmax * vpad;               // band entries of one chain
-    if (lane == 0)
-        for (int k = 0; k < kRing; ++k) mbar_init(&bars[k], 1);
-    // the whole band starts at zero: entries outside a super-voxel's band
-    // (spares) are only ever read and written with matrix value 0, so they
-    // stay finite whatever a previous super-voxel left there
-    for (int f = lane; f <= nrow * K; f += 32) band[f] = make_float2(0.f, 0.f);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    __syncwarp();
-
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = (int64_t)A.nx * A.ny;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (gw >= A.nwarps) return;
-    const int G = A.B / K;                      // batch groups
-    const int pair = gw % (G * A.N);            // (group, agent)
-    const int cidx = gw / (G * A.N);            // this warp's place among the C serving the pair
-    const int grp = pair / A.N, g = pair - grp * A.N;
+    const int pair = grp * A.N + g;             // (group, agent)
     const int v0 = A.view_off[g], Vg = A.view_off[g + 1] - v0;
-    const int Cw = A.nwarps / (G * A.N);
 
     // lane roles in the pixel loop: chain h, index hl inside the chain's lanes
     const int h = K == 2 ? (lane >> 4) : 0;
@@ -360,7 +357,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     if (sv < 0) {
         if (DET && lane == 0)
             for (int p = 0; p < 2 * ((A.nsv + Cw - 1) / Cw); ++p) phase_arrive(A.phase + pair);
-        return;
+        return true;
     }
     // first super-voxel: metadata with plain loads
     {
@@ -372,13 +369,13 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     }
     int count = build_list(sv, scoff, pl2, cl2);
     // The warp's columns form one sequence (its super-voxels' visiting lists
-    // one after the other).  dec: columns decoded; issued: columns whose copy
-    // has been started; seq0: sequence number of the current super-voxel's
-    // first column.  A slot is refilled one column late: when column d is
+    // one after the other, over all its work items).  dec: columns decoded;
+    // issued: columns whose copy has been started; seq0: sequence number of
+    // the current super-voxel's first column.  A slot is refilled one column late: when column d is
     // decoded, the data of column d-1 has been used by the stores of the
     // pixel before, so its slot is free; at most kRing - 1 copies are in
     // flight beside the column held in registers.
-    uint32_t issued = 0, dec = 0, seq0 = 0;
+    uint32_t seq0 = dec;      // (issued == dec: the previous item's columns are all decoded)
     int count_n = 0;
     int cur = 0;
     auto col_src = [&](uint2 c) { return A.cols + ((uint64_t)c.x << 4); };
@@ -481,7 +478,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             if (!__shfl_sync(FULL, ok ? 1 : 0, 0)) {
                 if (lane == 0) atomicExch(A.status, kStatusTimeout);
                 drain();
-                return;
+                return false;
             }
             __threadfence();
         }
@@ -604,10 +601,10 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         if (status_seen != 0) {
             // another warp gave up: drain this warp's copies in flight and stop
             drain();
-            return;
+            return false;
         }
         if (R > 0 && !have_cur && count > 0) {
-            if (!wait_column()) return;
+            if (!wait_column()) return false;
             ColRaw<RR, RRO> w0;
             col_load(w0);
             col_finish(w0, cc, cl, cl_n);
@@ -765,22 +762,22 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
         int q = 0;
         if constexpr (R == 0) {
             for (; q < count; ++q)
-                if (!pixel_any(q)) return;
+                if (!pixel_any(q)) return false;
         } else if constexpr (R <= 3) {
             // two pixels per trip, the decoded columns alternating between
             // cc and cn (no register copy)
             for (; q + 1 < count; q += 2) {
-                if (!pixel(q, cc, cn)) return;
-                if (!pixel(q + 1, cn, cc)) return;
+                if (!pixel(q, cc, cn)) return false;
+                if (!pixel(q + 1, cn, cc)) return false;
             }
         } else {
             for (; q + 1 < count; ++q) {
-                if (!pixel(q, cc, cn)) return;
+                if (!pixel(q, cc, cn)) return false;
                 cc = cn;
             }
         }
         if (R > 0 && q < count) {
-            if (!pixel(q, cc, cn)) return;
+            if (!pixel(q, cc, cn)) return false;
             cc = cn;
         }
         // the next super-voxel's first column is decoded already when the
@@ -795,7 +792,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             if (!__shfl_sync(FULL, ok ? 1 : 0, 0)) {
                 if (lane == 0) atomicExch(A.status, kStatusTimeout);
                 drain();
-                return;
+                return false;
             }
         }
         // --- write back: X tiles and the change of e ---------------------------
@@ -846,6 +843,76 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
             }
         }
     }
+    return true;
+}
+
+// One warp per (group, agent, row of super-voxels), fixed at launch: the
+// C warps of a pair are warps pair, pair + G N, pair + 2 G N, ...
+template <typename T, int K, int R, int RO, bool NB26, bool DET>
+__global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const WarpSmem Ly = warp_smem_layout(A.vpad, A.wmax, A.col_stride, A.S, K, NB26);
+    uint8_t *base = smem + (threadIdx.x >> 5) * Ly.total;
+    sweep_warp_init(base, Ly, A.wmax * A.vpad * K, lane);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= A.nwarps) return;
+    const int G = A.B / K;
+    const int pair = gw % (G * A.N);
+    uint32_t dec = 0, issued = 0;
+    sweep_work<T, K, R, RO, NB26, DET, SweepArgs>(A, base, Ly, pair / A.N, pair % A.N, gw / (G * A.N),
+                                                  A.nwarps / (G * A.N), dec, issued);
+}
+
+// Work queue over (request, group, agent, row of super-voxels): every resident
+// warp takes the next item from a counter until none is left, copies the
+// item's request descriptor into its shared memory and runs the row.  Items
+// are numbered row-fastest within a (group, agent) pair, so the C rows of a
+// pair are taken by warps at about the same time, as in the fixed schedule,
+// and a warp that finishes early takes more work (agents of uneven size).
+// zpar >= 0: only the groups (slices) of that parity.
+struct QueueArgs {
+    const SweepArgs *table;     // per request, in device memory
+    const int *offsets;         // [nreq + 1] first item of each request
+    unsigned *counter;          // zero at launch
+    int nreq, total, zpar;
+    int vpad, wmax, col_stride, S;   // shared-memory layout: the largest of the requests
+};
+
+template <typename T, int K, int R, int RO, bool NB26>
+__global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_queue_kernel(QueueArgs Q)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const WarpSmem Ly = warp_smem_layout(Q.vpad, Q.wmax, Q.col_stride, Q.S, K, NB26);
+    const size_t per_warp = Ly.total + ((sizeof(SweepArgs) + 15) & ~(size_t)15);
+    uint8_t *base = smem + (threadIdx.x >> 5) * per_warp;
+    SweepArgs *args = (SweepArgs *)(base + Ly.total);
+    sweep_warp_init(base, Ly, Q.wmax * Q.vpad * K, lane);
+    uint32_t dec = 0, issued = 0;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(Q.counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int)item >= Q.total) return;
+        int r = 0;
+        while (r + 1 < Q.nreq && (int)item >= Q.offsets[r + 1]) ++r;
+        // this item's request descriptor, word by word
+        const uint32_t *src = (const uint32_t *)(Q.table + r);
+        for (int k = lane; k < (int)(sizeof(SweepArgs) / 4); k += 32) ((uint32_t *)args)[k] = src[k];
+        __syncwarp();
+        const SweepArgs &A = *args;
+        const int local = (int)item - Q.offsets[r];
+        const int Cw = A.nwarps;                 // rows of a pair in flight (the request's concurrency)
+        const int pl = local / Cw, cidx = local - pl * Cw;
+        int grp = pl / A.N;
+        const int g = pl - grp * A.N;
+        if (Q.zpar >= 0) grp = 2 * grp + Q.zpar;
+        if (!sweep_work<T, K, R, RO, NB26, false, const SweepArgs &>(A, base, Ly, grp, g, cidx, Cw, dec, issued))
+            return;
+        __syncwarp();
+    }
 }
 
 // Rounds of views per lane and of the three-channel list for an agent of at
@@ -882,6 +949,32 @@ static sweep_fn sweep_lookup(int max_views, int K, bool nb26, bool det)
     return nullptr;
 }
 
+typedef void (*sweep_queue_fn)(QueueArgs);
+
+template <typename T, bool NB26>
+static sweep_queue_fn sweep_queue_lookup_r(int R)
+{
+    switch (R) {
+    case 1: return icd_sweep_queue_kernel<T, 1, 1, 1, NB26>;
+    case 2: return icd_sweep_queue_kernel<T, 1, 2, 1, NB26>;
+    case 3: return icd_sweep_queue_kernel<T, 1, 3, 2, NB26>;
+    case 4: return icd_sweep_queue_kernel<T, 1, 4, 2, NB26>;
+    default: return icd_sweep_queue_kernel<T, 1, 0, 1, NB26>;
+    }
+}
+
+// The queue-fed sweep (one chain per warp) for agents of at most max_views
+// views and the 8- or 26-neighbourhood.
+template <typename T>
+static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26)
+{
+    const int R = sweep_rounds(max_views, 1);
+    return nb26 ? sweep_queue_lookup_r<T, true>(R) : sweep_queue_lookup_r<T, false>(R);
+}
+
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26, bool det);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f32(int max_views, bool nb26);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_bf16(int max_views, bool nb26);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f16(int max_views, bool nb26);
