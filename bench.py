@@ -14,6 +14,7 @@ cores).  Under torchrun every rank runs its own independent batch (replicas;
 no collective on the data path).
 """
 import argparse
+import collections
 import json
 import math
 import os
@@ -411,17 +412,20 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "recons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-SERVE_SIZES = [(128, 180, 183), (256, 360, 363)]    # (n, views, channels)
-SERVE_AGENTS = [4, 8, 16]
+SERVE_SIZES = [(128, 180, 183), (256, 360, 363), (512, 720, 725), (1024, 1440, 1449)]   # (n, views, channels)
+SERVE_AGENTS = [4, 8, 16, 32]
 
 
 def run_serve(args):
-    """Continuous batching against one-at-a-time service, on one GPU: a seeded
-    stream of 2D requests (sizes and agent counts drawn from SERVE_SIZES and
-    SERVE_AGENTS, BF16 matrices, FP32 state) with Poisson arrivals at
-    args.serve_load times the rate one-at-a-time service sustains (above what
-    either mode can serve, so recons/s measures capacity).  Both modes see
-    the same arrivals; latency is arrival to image in host memory."""
+    """Serving on one GPU: a seeded stream of 2D requests, sizes and agent
+    counts drawn uniformly from SERVE_SIZES and SERVE_AGENTS (BF16 matrices,
+    FP32 state, Q-GGMRF 8-neighbour).  First the grouped server's capacity is
+    measured with every request waiting at time 0; then Poisson arrivals at
+    args.serve_load times that capacity are served three ways on the same
+    stream: grouped (all active requests in one group, their ICD passes in
+    one queue-fed launch per pass), one stream per request (each with its
+    own fixed-grid sweeps), and one request at a time.  Latency is arrival
+    to image in host memory."""
     import torch
     import synth
     from paper_1911_09278_gb300 import build as gbuild
@@ -445,40 +449,53 @@ def run_serve(args):
                        max_iter=args.max_iter)
     for r in reqs:                      # matrices resident before any timing
         srv._matrix(r)
-    srv.run(reqs[:2], serial=True)      # warm-up
+    small = sorted(reqs, key=lambda r: r.nx)[:2]
+    srv.run(small, grouped=True)        # warm-up
+    srv.run(small)
     torch.cuda.synchronize()
-    back = srv.run(reqs, serial=True)   # back-to-back, for the service time
-    service = back["makespan"] / len(reqs)
-    rate = args.serve_load / service
+    calib = srv.run(reqs, grouped=True)     # every request waiting at time 0: capacity
+    capacity = len(calib["results"]) / max(1e-9, calib["makespan"])
+    rate = args.serve_load * capacity
     gaps = -np.log(1.0 - rng.uniform(12, np.arange(len(reqs)))) / rate
     t = np.cumsum(gaps) - gaps[0]
     timed = [r._replace(arrival=float(t[k])) for k, r in enumerate(reqs)]
-    serial = srv.run(timed, serial=True)
-    served = srv.run(timed)
+    runs = {"grouped": srv.run(timed, grouped=True), "streams": srv.run(timed)}
+    if not args.no_serial:
+        runs["one_at_a_time"] = srv.run(timed, serial=True)
+    ref = runs.get("one_at_a_time", runs["streams"])
     worst = 0.0
     for r in reqs:
-        if r.rid not in served["results"] or r.rid not in serial["results"]:
+        if r.rid not in runs["grouped"]["results"] or r.rid not in ref["results"]:
             continue      # failed in one of the modes: counted below
-        a, b = served["results"][r.rid]["x"], serial["results"][r.rid]["x"]
+        a, b = runs["grouped"]["results"][r.rid]["x"], ref["results"][r.rid]["x"]
         worst = max(worst, float(np.linalg.norm(a - b) / max(1e-30, np.linalg.norm(b))))
-    conv = all(d["converged"] for d in served["results"].values())
+    g = runs["grouped"]
+    conv = all(d["converged"] for d in g["results"].values())
     srv.close()
-    return {
-        "metric": "served recons/sec (continuous batching) with p50/p99 latency",
-        "value": served["recons_per_s"], "unit": "recons/s", "n_gpus": 1, "higher_is_better": True,
-        "p50_s": served["p50"], "p99_s": served["p99"],
-        "serial": {"value": serial["recons_per_s"], "unit": "recons/s", "p50_s": serial["p50"],
-                   "p99_s": serial["p99"]},
-        "speedup_vs_serial": served["recons_per_s"] / serial["recons_per_s"],
-        "max_nrmse_served_vs_serial": worst, "converged": conv,
-        "failed": {"served": len(served["failed"]), "one_at_a_time": len(serial["failed"])},
+    mix = collections.Counter((r.nx, r.n_agents) for r in reqs)
+
+    def brief(o):
+        return {"value": o["recons_per_s"], "unit": "recons/s", "p50_s": o["p50"], "p99_s": o["p99"],
+                "completed": len(o["results"]), "failed": len(o["failed"])}
+    out = {
+        "metric": "served recons/sec (grouped continuous batching) with p50/p99 latency",
+        "value": g["recons_per_s"], "unit": "recons/s", "n_gpus": 1, "higher_is_better": True,
+        "p50_s": g["p50"], "p99_s": g["p99"],
+        "modes": {k: brief(v) for k, v in runs.items()},
+        "capacity_all_at_once": capacity,
+        "max_nrmse_grouped_vs_%s" % ("one_at_a_time" if "one_at_a_time" in runs else "streams"): worst,
+        "converged": conv, "failed": len(g["failed"]),
         "dtype": args.serve_dtype + "-A/f32", "data": "synthetic",
-        "config": {"workload": "stream of %d 2D requests, sizes %s, agents %s, Poisson arrivals at %.2f/s "
-                               "(%gx one-at-a-time capacity)" % (len(reqs), SERVE_SIZES, SERVE_AGENTS, rate,
-                                                                 args.serve_load),
+        "config": {"workload": "stream of %d 2D requests, sizes %s, agents %s, Poisson arrivals at %.3f/s "
+                               "(%gx the grouped capacity)" % (len(reqs), SERVE_SIZES, SERVE_AGENTS, rate,
+                                                               args.serve_load),
+                   "mix": {"%dx%d/%d agents" % (k[0], k[0], k[1]): v for k, v in sorted(mix.items())},
                    "max_active": args.max_active, "concurrency_per_agent": args.serve_concurrency,
                    "sv_size": 8, "sigma_normalised": args.serve_sigma, "tol": args.serve_tol},
     }
+    if "one_at_a_time" in runs:
+        out["speedup_vs_one_at_a_time"] = g["recons_per_s"] / runs["one_at_a_time"]["recons_per_s"]
+    return out
 
 
 def run_volume(args):
@@ -604,8 +621,10 @@ def build_parser():
     # serving and the 3D stack run 8x8 super-voxels, stable up to sigma about 0.14
     ap.add_argument("--serve-sigma", dest="serve_sigma", type=float, default=0.13)
     ap.add_argument("--serve-tol", dest="serve_tol", type=float, default=6.5e-7)
-    ap.add_argument("--serve-load", dest="serve_load", type=float, default=8.0,
-                    help="arrival rate as a multiple of one-at-a-time capacity")
+    ap.add_argument("--serve-load", dest="serve_load", type=float, default=0.8,
+                    help="arrival rate as a multiple of the grouped server's capacity")
+    ap.add_argument("--no-serial", dest="no_serial", action="store_true",
+                    help="serving: skip the one-at-a-time run")
     ap.add_argument("--volume", action="store_true",
                     help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
     ap.add_argument("--slices", type=int, default=64)

@@ -335,11 +335,16 @@ int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
  * stream first waits for each member's stream, and each member's stream
  * then waits for the group's, so mace_poll / mace_poll_async /
  * mace_consensus on a member see the group's iterations.  Returns without
- * waiting.  mace_group_free releases the group's descriptors (not the
- * members).  Errors: MACE_EINVAL (schedule 0 or volume members, a member
- * twice, mixed value types), MACE_ENOMEM, MACE_ECUDA. */
+ * waiting.  mace_group_update replaces the members (a server admitting and
+ * retiring requests): stream-ordered, it neither waits for the group's work
+ * in flight nor synchronises the device; on error the group keeps its
+ * previous members.  mace_group_free releases the group's descriptors (not
+ * the members).  Errors: MACE_EINVAL (schedule 0 or volume members, a
+ * member twice, mixed value types, n outside [1, 65536]), MACE_ENOMEM,
+ * MACE_ECUDA. */
 typedef struct mace_group mace_group;
 int mace_group_create(mace_state *const *members, int32_t n, void *cuda_stream, mace_group **out);
+int mace_group_update(mace_group *group, mace_state *const *members, int32_t n);
 int mace_group_launch(mace_group *group, int32_t n_iters);
 int mace_group_free(mace_group *group);
 

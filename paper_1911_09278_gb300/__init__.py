@@ -37,7 +37,7 @@ EXPORTS = [
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
-    "mace_group_create", "mace_group_launch", "mace_group_free",
+    "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free",
 ]
 
 
@@ -126,6 +126,7 @@ def load(path=LIB_PATH):
     L.mace_free_sysmatrix.restype = None
     L.mace_last_error.restype = ctypes.c_char_p
     L.mace_group_create.argtypes = [ctypes.POINTER(vp), i32, vp, pp]
+    L.mace_group_update.argtypes = [vp, ctypes.POINTER(vp), i32]
     L.mace_group_launch.argtypes = [vp, i32]
     L.mace_group_free.argtypes = [vp]
     for name in ("mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
@@ -135,7 +136,7 @@ def load(path=LIB_PATH):
                  "mace_set_timing", "mace_get_timing",
                  "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
                  "mace_recompute_error", "mace_get_stats",
-                 "mace_group_create", "mace_group_launch", "mace_group_free"):
+                 "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -435,6 +436,13 @@ class Group:
         h = ctypes.c_void_p()
         _check(load().mace_group_create(arr, len(self.states), _stream_handle(stream), ctypes.byref(h)))
         self.handle = h
+
+    def update(self, states):
+        """Replace the members (stream-ordered; no wait)."""
+        states = list(states)
+        arr = (ctypes.c_void_p * len(states))(*[st.handle for st in states])
+        _check(load().mace_group_update(self.handle, arr, len(states)))
+        self.states = states
 
     def launch(self, n_iters):
         """Enqueue n_iters Mann iterations of every member (no wait)."""

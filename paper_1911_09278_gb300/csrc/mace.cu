@@ -1502,6 +1502,9 @@ static int check_params(const mace_params *P)
 extern "C" void mace_free_state(mace_state *st)
 {
     if (!st) return;
+    // work on the state's stream (and, through its event waits, the group
+    // launches it took part in) ends before its memory goes
+    cudaStreamSynchronize(st->stream);
     cudaFree(st->d_eL);
     cudaFree(st->d_dacc);
     cudaFree(st->d_phase);
@@ -1949,6 +1952,10 @@ extern "C" int mace_iterate(mace_state *st, int32_t n_iters, double *residual_ou
 }
 
 // --- groups: several states' ICD passes in one queue-fed launch -------------
+// Membership changes (mace_group_update) are stream-ordered: the new
+// descriptors go through pinned staging (two slots, so the host does not
+// wait for the upload it just queued) into device tables that later launches
+// on the group's stream read; nothing synchronises the device.
 struct mace_group {
     std::vector<mace_state *> members;
     cudaStream_t stream = nullptr;
@@ -1956,27 +1963,40 @@ struct mace_group {
     int npass = 0;                       // largest sweeps_per_iter of the members
     SweepArgs *d_tab = nullptr;          // [npass][n] descriptors of each pass's requests
     int *d_off = nullptr;                // [npass][n + 1] first item of each request
+    size_t cap_tab = 0, cap_off = 0;     // entries allocated
     unsigned *d_cnt = nullptr;
     std::vector<int> nreq, total;        // per pass
     cudaEvent_t done = nullptr;          // the group's work, for the members' streams
     std::vector<cudaEvent_t> ready;      // each member's earlier work, for the group's stream
+    uint8_t *h_stage[2] = {nullptr, nullptr};
+    size_t cap_stage[2] = {0, 0};
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    bool staged_used[2] = {false, false};
+    int slot = 0;
 };
 
 static void group_free(mace_group *G)
 {
-    cudaFree(G->d_tab);
-    cudaFree(G->d_off);
-    cudaFree(G->d_cnt);
+    for (int k = 0; k < 2; ++k) {
+        if (G->staged_used[k]) cudaEventSynchronize(G->staged[k]);
+        if (G->h_stage[k]) cudaFreeHost(G->h_stage[k]);
+        if (G->staged[k]) cudaEventDestroy(G->staged[k]);
+    }
+    if (G->d_tab) cudaFreeAsync(G->d_tab, G->stream);
+    if (G->d_off) cudaFreeAsync(G->d_off, G->stream);
+    if (G->d_cnt) cudaFreeAsync(G->d_cnt, G->stream);
     if (G->done) cudaEventDestroy(G->done);
     for (cudaEvent_t e : G->ready)
         if (e) cudaEventDestroy(e);
     delete G;
 }
 
-extern "C" int mace_group_create(mace_state *const *members, int32_t n, void *cuda_stream, mace_group **out)
+// Replace the members: check them, configure the launch, build the
+// per-pass descriptor tables and queue their upload on the group's stream.
+// On error the group keeps its previous members.
+static int group_set(mace_group *G, mace_state *const *members, int n)
 {
-    if (!members || !out) return fail(MACE_EINVAL, "NULL argument");
-    *out = nullptr;
+    if (!members) return fail(MACE_EINVAL, "NULL argument");
     if (n < 1 || n > 65536) return fail(MACE_EINVAL, "a group has 1 to 65536 members");
     std::vector<const mace_sysmatrix *> Ms(n);
     for (int k = 0; k < n; ++k) {
@@ -1988,51 +2008,106 @@ extern "C" int mace_group_create(mace_state *const *members, int32_t n, void *cu
         if (st->P.neighbourhood == 26) return fail(MACE_EINVAL, "volumes (neighbourhood 26) are not grouped");
         Ms[k] = st->M;
     }
-    mace_group *G = new mace_group();
-    G->members.assign(members, members + n);
-    G->stream = (cudaStream_t)cuda_stream;
-    int rc = queue_configure(Ms.data(), n, false, &G->q);
-    if (rc) { group_free(G); return rc; }
-    for (const mace_state *st : G->members) G->npass = std::max(G->npass, st->P.sweeps_per_iter);
+    QueueLaunch q;
+    int rc = queue_configure(Ms.data(), n, false, &q);
+    if (rc) return rc;
+    int npass = 0;
+    for (int k = 0; k < n; ++k) npass = std::max(npass, members[k]->P.sweeps_per_iter);
     // pass p: the members with more than p passes per iteration, each in
     // its own direction (every second pass backward when symmetric)
-    std::vector<SweepArgs> tab((size_t)G->npass * n);
-    std::vector<int> off((size_t)G->npass * (n + 1), 0);
-    G->nreq.assign(G->npass, 0);
-    G->total.assign(G->npass, 0);
-    for (int p = 0; p < G->npass; ++p) {
+    const size_t ntab = (size_t)npass * n, noff = (size_t)npass * (n + 1);
+    const size_t tab_bytes = sizeof(SweepArgs) * ntab, bytes = tab_bytes + sizeof(int) * noff;
+    std::vector<int> nreq(npass, 0), total(npass, 0);
+    // staging slot: the one not used by the last update; its previous
+    // upload (two updates ago) has long been queued
+    const int slot = G->slot ^ 1;
+    if (G->staged_used[slot]) CUDA_TRY(cudaEventSynchronize(G->staged[slot]));
+    if (G->cap_stage[slot] < bytes) {
+        if (G->h_stage[slot]) cudaFreeHost(G->h_stage[slot]);
+        G->h_stage[slot] = nullptr;
+        G->cap_stage[slot] = 0;
+        if (cudaMallocHost(&G->h_stage[slot], bytes) != cudaSuccess) {
+            G->h_stage[slot] = nullptr;
+            return fail(MACE_ENOMEM, "cudaMallocHost group staging");
+        }
+        G->cap_stage[slot] = bytes;
+    }
+    SweepArgs *tab = (SweepArgs *)G->h_stage[slot];
+    int *off = (int *)(G->h_stage[slot] + tab_bytes);
+    for (int p = 0; p < npass; ++p) {
         int r = 0, t = 0;
-        for (const mace_state *st : G->members) {
+        for (int k = 0; k < n; ++k) {
+            const mace_state *st = members[k];
             if (st->P.sweeps_per_iter <= p) continue;
             tab[(size_t)p * n + r] = sweep_args(st, st->P.symmetric ? (p & 1) : 0, nullptr);
             off[(size_t)p * (n + 1) + r] = t;
             t += queue_items(st, -1);
             ++r;
         }
-        off[(size_t)p * (n + 1) + r] = t;
-        G->nreq[p] = r;
-        G->total[p] = t;
+        for (int k = r; k <= n; ++k) off[(size_t)p * (n + 1) + k] = t;
+        nreq[p] = r;
+        total[p] = t;
     }
-    if (cudaMalloc(&G->d_tab, sizeof(SweepArgs) * tab.size()) != cudaSuccess ||
-        cudaMalloc(&G->d_off, sizeof(int) * off.size()) != cudaSuccess ||
-        cudaMalloc(&G->d_cnt, sizeof(unsigned)) != cudaSuccess) {
+    // device tables, grown in stream order (launches before this point
+    // still read the old ones)
+    if (G->cap_tab < ntab) {
+        if (G->d_tab) CUDA_TRY(cudaFreeAsync(G->d_tab, G->stream));
+        G->d_tab = nullptr;
+        G->cap_tab = 0;
+        if (cudaMallocAsync((void **)&G->d_tab, sizeof(SweepArgs) * ntab, G->stream) != cudaSuccess)
+            return fail(MACE_ENOMEM, "cudaMallocAsync group descriptors");
+        G->cap_tab = ntab;
+    }
+    if (G->cap_off < noff) {
+        if (G->d_off) CUDA_TRY(cudaFreeAsync(G->d_off, G->stream));
+        G->d_off = nullptr;
+        G->cap_off = 0;
+        if (cudaMallocAsync((void **)&G->d_off, sizeof(int) * noff, G->stream) != cudaSuccess)
+            return fail(MACE_ENOMEM, "cudaMallocAsync group offsets");
+        G->cap_off = noff;
+    }
+    if (!G->d_cnt && cudaMallocAsync((void **)&G->d_cnt, sizeof(unsigned), G->stream) != cudaSuccess)
+        return fail(MACE_ENOMEM, "cudaMallocAsync group counter");
+    CUDA_TRY(cudaMemcpyAsync(G->d_tab, tab, tab_bytes, cudaMemcpyHostToDevice, G->stream));
+    CUDA_TRY(cudaMemcpyAsync(G->d_off, off, sizeof(int) * noff, cudaMemcpyHostToDevice, G->stream));
+    if (!G->staged[slot]) CUDA_TRY(cudaEventCreateWithFlags(&G->staged[slot], cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(G->staged[slot], G->stream));
+    G->staged_used[slot] = true;
+    G->slot = slot;
+    while ((int)G->ready.size() < n) {
+        cudaEvent_t e = nullptr;
+        CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        G->ready.push_back(e);
+    }
+    G->members.assign(members, members + n);
+    G->q = q;
+    G->npass = npass;
+    G->nreq = nreq;
+    G->total = total;
+    return MACE_OK;
+}
+
+extern "C" int mace_group_create(mace_state *const *members, int32_t n, void *cuda_stream, mace_group **out)
+{
+    if (!members || !out) return fail(MACE_EINVAL, "NULL argument");
+    *out = nullptr;
+    mace_group *G = new mace_group();
+    G->stream = (cudaStream_t)cuda_stream;
+    int rc = MACE_OK;
+    if (cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess) rc = fail(MACE_ECUDA, "group event");
+    if (rc == MACE_OK) rc = group_set(G, members, n);
+    if (rc) {
         group_free(G);
-        return fail(MACE_ENOMEM, "cudaMalloc group descriptors");
+        return rc;
     }
-    if (cudaMemcpy(G->d_tab, tab.data(), sizeof(SweepArgs) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(G->d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming) != cudaSuccess) {
-        group_free(G);
-        return fail(MACE_ECUDA, "group set-up");
-    }
-    G->ready.assign(n, nullptr);
-    for (int k = 0; k < n; ++k)
-        if (cudaEventCreateWithFlags(&G->ready[k], cudaEventDisableTiming) != cudaSuccess) {
-            group_free(G);
-            return fail(MACE_ECUDA, "group events");
-        }
     *out = G;
     return MACE_OK;
+}
+
+extern "C" int mace_group_update(mace_group *G, mace_state *const *members, int32_t n)
+{
+    if (!G) return fail(MACE_EINVAL, "group is NULL");
+    return group_set(G, members, n);
 }
 
 extern "C" int mace_group_launch(mace_group *G, int32_t n_iters)

@@ -53,6 +53,26 @@ def test_served_equals_alone(gpu_lib):
     srv.close()
 
 
+def test_grouped_serving_equals_alone(gpu_lib):
+    """Grouped serving (all active requests in one group, their ICD passes
+    in one queue-fed launch per pass): every image equals the request
+    reconstructed alone in grouped mode, and the iteration counts agree."""
+    from paper_1911_09278_gb300 import serve
+    specs = [(64, 90, 95, 4), (48, 72, 71, 8), (64, 90, 95, 16), (32, 48, 47, 4), (48, 72, 71, 8), (64, 90, 95, 4)]
+    reqs = _requests(serve, specs, rate=200.0)
+    srv = serve.Server(PARAMS, dtype="f32", sv_size=8, max_active=4, max_iter=6000)
+    mixed = srv.run(reqs, grouped=True)
+    assert not mixed["failed"]
+    for r in reqs:
+        one = srv.run([r._replace(arrival=0.0)], grouped=True)["results"][r.rid]
+        got = mixed["results"][r.rid]
+        assert got["converged"], r.rid
+        assert got["iters"] == one["iters"], (r.rid, got["iters"], one["iters"])
+        assert np.array_equal(got["x"], one["x"]), r.rid
+    print("grouped: %.2f recons/s, p50 %.3f s, p99 %.3f s" % (mixed["recons_per_s"], mixed["p50"], mixed["p99"]))
+    srv.close()
+
+
 def test_admission_respects_budget(gpu_lib):
     """With a budget that holds one request at a time the server still
     finishes every request, one after another."""

@@ -174,3 +174,60 @@ def test_failed_requests_are_retired_and_the_rest_served(fake_server):
     for rid in (0, 2, 4):
         assert out["results"][rid]["converged"]
     assert active["now"] == 0          # every state that was made is closed
+
+
+class FakeGroup:
+    log = []
+
+    def __init__(self, states, stream=None):
+        self.states = list(states)
+        self.closed = False
+        FakeGroup.log.append(("create", [st.rid for st in self.states]))
+
+    def update(self, states):
+        assert not self.closed
+        self.states = list(states)
+        FakeGroup.log.append(("update", [st.rid for st in self.states]))
+
+    def launch(self, k):
+        assert not self.closed
+        for st in self.states:
+            assert not st.closed, "a retired state is still a member"
+            st.launch(k)
+
+    def close(self):
+        self.closed = True
+
+
+@pytest.fixture
+def grouped(fake_server, monkeypatch):
+    FakeGroup.log = []
+    monkeypatch.setattr(serve, "mace_group_create", lambda states, stream=None: FakeGroup(states, stream))
+    return fake_server
+
+
+def test_grouped_mode_retires_one_chunk_after_convergence(grouped):
+    """Grouped serving: every request is served, its image read one chunk
+    after the status that showed convergence, never more than max_active at
+    once, and no retired state stays in the group."""
+    make, active = grouped
+    srv = make(max_active=3, chunk=10)
+    conv = [30, 50, 20, 40, 10, 60]
+    out = srv.run(_requests(conv), grouped=True)
+    assert sorted(out["results"]) == list(range(len(conv)))
+    for rid, c in enumerate(conv):
+        d = out["results"][rid]
+        assert d["converged"] and d["iters"] == c + 10, (rid, d["iters"])
+        assert float(d["x"][0, 0]) == rid
+    assert active["max"] == 3
+    sizes = [len(m) for kind, m in FakeGroup.log]
+    assert max(sizes) <= 3 and FakeGroup.log[0][0] == "create"
+
+
+def test_grouped_mode_retires_a_diverged_request_alone(grouped):
+    make, active = grouped
+    srv = make(max_active=4, chunk=10)
+    out = srv.run(_requests([20, -1, 30]), grouped=True)
+    assert sorted(out["results"]) == [0, 2]
+    assert list(out["failed"]) == [1] and out["failed"][1]["code"] == -6
+    assert active["now"] == 0
