@@ -150,7 +150,15 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   and slices of a volume (neighbourhood 26) are swept even ones first,
  *   then odd ones, each reading neighbour slices that are not being
  *   updated.  Schedule 1 runs one chain per warp and the free mode
- *   (deterministic 0). */
+ *   (deterministic 0).
+ *   warps_per_voxel (schedule 1, neighbourhood 8): 1, 2 or 4 warps of one
+ *   block sweep the same super-voxels together, each holding its share of
+ *   the agent's views (views 32 (w + W j) + lane of warp w) and its share of
+ *   the error-sinogram band; a pixel's theta1 is the sum of the warps'
+ *   partial sums, added in warp order through shared memory, so every warp
+ *   takes the same step (Algorithm 2 is unchanged).  For agents with many
+ *   views: fewer views per warp and more warps per agent.  0 = automatic:
+ *   1 up to 128 views per agent, else 2 up to 192, else 4. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;
@@ -170,6 +178,7 @@ typedef struct {
     int32_t forward_geometry;
     int32_t deterministic;
     int32_t schedule;
+    int32_t warps_per_voxel;
 } mace_params;
 
 /* Sizes of a built system matrix (for memory accounting, Table 3). */
@@ -320,6 +329,11 @@ int mace_recompute_error(mace_state *st);
  * reconstructions one warp updates together. */
 int mace_get_stats(const mace_state *st, int32_t *iters, double *sigma_abs,
                    double *last_residual, int32_t *concurrency, int32_t *chains);
+
+/* The sweep's launch configuration: params.schedule, the warps per
+ * super-voxel in use (1 for schedule 0) and the warps the sweep launches
+ * (schedule 0) or keeps resident (schedule 1).  Any pointer may be NULL. */
+int mace_get_launch_info(const mace_state *st, int32_t *schedule, int32_t *warps_per_voxel, int32_t *warps);
 
 /* Groups: the Mann iterations of several states (different scans,
  * geometries and parameters; params.schedule = 1, neighbourhood 8, one

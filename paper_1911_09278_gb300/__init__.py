@@ -37,7 +37,7 @@ EXPORTS = [
     "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
     "mace_error_size", "mace_recompute_error", "mace_get_stats",
     "mace_free_state", "mace_free_sysmatrix", "mace_last_error",
-    "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free",
+    "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free", "mace_get_launch_info",
 ]
 
 
@@ -69,7 +69,7 @@ class Params(ctypes.Structure):
                 ("concurrency", ctypes.c_int32), ("sv_order", ctypes.c_int32),
                 ("chains", ctypes.c_int32), ("pnp", ctypes.c_int32),
                 ("forward_geometry", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("schedule", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("warps_per_voxel", ctypes.c_int32)]
 
 
 class SysmatrixInfo(ctypes.Structure):
@@ -127,6 +127,7 @@ def load(path=LIB_PATH):
     L.mace_last_error.restype = ctypes.c_char_p
     L.mace_group_create.argtypes = [ctypes.POINTER(vp), i32, vp, pp]
     L.mace_group_update.argtypes = [vp, ctypes.POINTER(vp), i32]
+    L.mace_get_launch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.mace_group_launch.argtypes = [vp, i32]
     L.mace_group_free.argtypes = [vp]
     for name in ("mace_build_sysmatrix", "mace_sysmatrix_get_info", "mace_sysmatrix_column",
@@ -136,7 +137,8 @@ def load(path=LIB_PATH):
                  "mace_set_timing", "mace_get_timing",
                  "mace_get_state", "mace_set_state", "mace_prox_pass", "mace_get_error",
                  "mace_recompute_error", "mace_get_stats",
-                 "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free"):
+                 "mace_group_create", "mace_group_update", "mace_group_launch", "mace_group_free",
+                 "mace_get_launch_info"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -237,17 +239,18 @@ def mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=None,
 def make_params(prior="qggmrf", beta=1.0, sigma_x=1.0, p=2.0, q=1.2, T=1.0, sigma=0.1,
                 sigma_mode=1, rho=0.8, sweeps_per_iter=1, symmetric=False, recompute_every=0,
                 max_iter=1000, tol=1e-5, concurrency=0, neighbourhood=8, sv_order=0, chains=0, pnp=False,
-                forward_geometry=None, deterministic=False, schedule=0):
+                forward_geometry=None, deterministic=False, schedule=0, warps_per_voxel=0):
     """forward_geometry: None = the library's default (the geometry-evaluated
     e recompute for BF16/FP16 stored values), True = always from the
     geometry, False = always from the stored values.  schedule: 0 = fixed
     warps per (reconstruction, agent) pair, 1 = a persistent grid fed from
-    a work queue."""
+    a work queue.  warps_per_voxel: warps sweeping one super-voxel together
+    (schedule 1; 0 = automatic by views per agent)."""
     return Params(0 if prior == "quadratic" else 1, neighbourhood, beta, sigma_x, p, q, T, sigma,
                   sigma_mode, rho, sweeps_per_iter, int(bool(symmetric)), recompute_every,
                   max_iter, tol, concurrency, sv_order, chains, int(bool(pnp)),
                   0 if forward_geometry is None else (1 if forward_geometry else 2), int(bool(deterministic)),
-                  int(schedule))
+                  int(schedule), int(warps_per_voxel))
 
 
 class State:
@@ -370,8 +373,10 @@ class State:
         k = ctypes.c_int32()
         _check(load().mace_get_stats(self.handle, ctypes.byref(it), ctypes.byref(s), ctypes.byref(r),
                                      ctypes.byref(c), ctypes.byref(k)))
+        sc, wpv, nw = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().mace_get_launch_info(self.handle, ctypes.byref(sc), ctypes.byref(wpv), ctypes.byref(nw)))
         return dict(iters=it.value, sigma_abs=s.value, last_residual=r.value, concurrency=c.value,
-                    chains=k.value)
+                    chains=k.value, schedule=sc.value, warps_per_voxel=wpv.value, warps=nw.value)
 
     def close(self):
         if self.handle:

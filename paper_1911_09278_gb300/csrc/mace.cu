@@ -579,6 +579,7 @@ static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
 // shared-memory layout large enough for every one of them.
 struct QueueLaunch {
     sweep_queue_fn fn = nullptr;
+    int W = 1;                           // warps per super-voxel (a team)
     int vpad = 0, wmax = 0, col_stride = 16, S = 4;
     int wpb = 1, blocks = 0;
     size_t smem = 0;
@@ -635,6 +636,7 @@ struct mace_state {
     unsigned *d_qcnt = nullptr;
     int q_items[2] = {0, 0};
     QueueLaunch q;
+    int wpv = 1;                            // warps per super-voxel (the queue-fed sweep)
     size_t sweep_smem = 0, warp_smem = 0;
 };
 
@@ -1221,17 +1223,29 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
 }
 
 // --- work-queue launches ------------------------------------------------------
-static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26)
+static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26, int W)
 {
     switch (dt) {
-    case MACE_F32: return mace_sweep_queue_kernel_f32(max_views, nb26);
-    case MACE_BF16: return mace_sweep_queue_kernel_bf16(max_views, nb26);
-    default: return mace_sweep_queue_kernel_f16(max_views, nb26);
+    case MACE_F32: return mace_sweep_queue_kernel_f32(max_views, nb26, W);
+    case MACE_BF16: return mace_sweep_queue_kernel_bf16(max_views, nb26, W);
+    default: return mace_sweep_queue_kernel_f16(max_views, nb26, W);
     }
 }
 
-static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, QueueLaunch *L)
+// Warps per super-voxel of the queue-fed sweep: the caller's choice, else
+// one while a warp's lanes hold the agent's views in at most four rounds
+// (the kernels that decode one column ahead), else the smallest team that
+// leaves a warp at most 96 views
+static int resolve_wpv(const mace_params &P, const mace_sysmatrix *M)
 {
+    if (P.warps_per_voxel > 0) return P.warps_per_voxel;
+    if (P.schedule != 1 || P.neighbourhood == 26 || M->max_views <= 128) return 1;
+    return M->max_views <= 2 * 96 ? 2 : 4;
+}
+
+static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L)
+{
+    L->W = W;
     int max_views = 1;
     for (int k = 0; k < n; ++k) {
         const mace_sysmatrix *M = Ms[k];
@@ -1247,7 +1261,7 @@ static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, Qu
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t per_warp = warp_smem_layout(L->vpad, L->wmax, L->col_stride, L->S, 1, nb26).total +
+    const size_t per_warp = warp_smem_layout(L->vpad, L->wmax, L->col_stride, L->S, 1, nb26, W).total +
                             ((sizeof(SweepArgs) + 15) & ~(size_t)15);
     if (per_warp > (size_t)max_smem)
         return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
@@ -1258,11 +1272,12 @@ static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, Qu
     if (R <= 4)
         for (int k = 0; k < n; ++k)
             if (Ms[k]->max_n3 > sweep_ovf_rounds(R, 1) * 32) max_views = 5 * 32 + 1;
-    L->fn = queue_kernel_ptr(Ms[0]->dtype, max_views, nb26);
-    if (!L->fn) return fail(MACE_EINVAL, "no queue-fed sweep kernel for this matrix");
+    L->fn = queue_kernel_ptr(Ms[0]->dtype, max_views, nb26, W);
+    if (!L->fn) return fail(MACE_EINVAL, "no queue-fed sweep kernel for this matrix and warps per voxel");
     CUDA_TRY(cudaFuncSetAttribute(L->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    // blocks of whole teams (at most 8 warps: team barriers 1..8)
     int best = 0;
-    for (int w = 1; w <= 8; ++w) {
+    for (int w = W; w <= 8; w += W) {
         if (per_warp * w > (size_t)max_smem) break;
         int b = 0;
         CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, L->fn, 32 * w, per_warp * w));
@@ -1341,14 +1356,16 @@ static int configure_queue(mace_state *st)
     const mace_sysmatrix *M = st->M;
     if (st->P.deterministic) return fail(MACE_EINVAL, "the deterministic mode runs the fixed schedule (schedule 0)");
     const mace_sysmatrix *Ms[1] = {M};
-    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, &st->q);
+    st->wpv = resolve_wpv(st->P, M);
+    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, st->wpv, &st->q);
     if (rc) return rc;
     st->chains = 1;
     // items per pair: `concurrency` rows (0 or -1: one per super-voxel row)
     int64_t C = st->P.concurrency > 0 ? st->P.concurrency : M->nsvy;
     C = std::max<int64_t>(1, std::min<int64_t>(C, M->nsv));
     st->concurrency = (int)C;
-    st->sweep_warps = (int)std::min<int64_t>((int64_t)st->q.blocks * st->q.wpb, (int64_t)st->B * M->N * C);
+    st->sweep_warps = (int)std::min<int64_t>((int64_t)st->q.blocks * st->q.wpb,
+                                             (int64_t)st->B * M->N * C * st->wpv);
     st->sweep_wpb = st->q.wpb;
     st->sweep_smem = st->q.smem;
     return MACE_OK;
@@ -1494,6 +1511,10 @@ static int check_params(const mace_params *P)
     if (P->schedule != 0 && P->schedule != 1) return fail(MACE_EINVAL, "schedule must be 0 or 1");
     if (P->schedule == 1 && P->deterministic)
         return fail(MACE_EINVAL, "the deterministic mode runs the fixed schedule (schedule 0)");
+    if (P->warps_per_voxel != 0 && P->warps_per_voxel != 1 && P->warps_per_voxel != 2 && P->warps_per_voxel != 4)
+        return fail(MACE_EINVAL, "warps_per_voxel must be 0 (automatic), 1, 2 or 4");
+    if (P->warps_per_voxel > 1 && (P->schedule != 1 || P->neighbourhood == 26))
+        return fail(MACE_EINVAL, "teams of warps per super-voxel run the 2D work-queue schedule (schedule 1)");
     if (P->pnp && (P->prior != 0 || P->neighbourhood != 8))
         return fail(MACE_EINVAL, "pnp needs the quadratic prior and the 8-neighbourhood");
     return MACE_OK;
@@ -2008,8 +2029,11 @@ static int group_set(mace_group *G, mace_state *const *members, int n)
         if (st->P.neighbourhood == 26) return fail(MACE_EINVAL, "volumes (neighbourhood 26) are not grouped");
         Ms[k] = st->M;
     }
+    // one team size for the launch: the largest the members resolved
+    int W = 1;
+    for (int k = 0; k < n; ++k) W = std::max(W, members[k]->wpv);
     QueueLaunch q;
-    int rc = queue_configure(Ms.data(), n, false, &q);
+    int rc = queue_configure(Ms.data(), n, false, W, &q);
     if (rc) return rc;
     int npass = 0;
     for (int k = 0; k < n; ++k) npass = std::max(npass, members[k]->P.sweeps_per_iter);
@@ -2336,6 +2360,16 @@ extern "C" int mace_wait_selftest(uint32_t spin_limit, void *cuda_stream)
     cudaFree(d);
     if (ce != cudaSuccess) return fail(MACE_ECUDA, std::string("wait self test: ") + cudaGetErrorString(ce));
     if (h == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+    return MACE_OK;
+}
+
+extern "C" int mace_get_launch_info(const mace_state *st, int32_t *schedule, int32_t *warps_per_voxel,
+                                    int32_t *warps)
+{
+    if (!st) return fail(MACE_EINVAL, "state is NULL");
+    if (schedule) *schedule = st->P.schedule;
+    if (warps_per_voxel) *warps_per_voxel = st->P.schedule == 1 ? st->wpv : 1;
+    if (warps) *warps = st->sweep_warps;
     return MACE_OK;
 }
 

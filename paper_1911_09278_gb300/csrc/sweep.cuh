@@ -85,18 +85,28 @@ typedef void (*sweep_fn)(SweepArgs);
 //                                       | pixel offset in the super-voxel << 20
 //   cl:     2 * S^2 * 8                 per visited pixel: (column offset in 16-byte units, bytes)
 //   halo:   2 * (S+2)^2 * 4             X tiles of the slices below and above (volumes only)
-//   band:   (wmax vpad K + 1) * 8       (e, Lambda), chains interleaved; the last entry is a
+//   band:   (wmax bw K + 1) * 8         (e, Lambda), chains interleaved; the last entry is a
 //                                       sink that idle lanes read and write with value 0
-//   snap:   K wmax vpad * 4             e of the band when the super-voxel began
+//   snap:   K wmax bw * 4               e of the band when the super-voxel began
 //   xt:     K (S+2)^2 * 4               X tiles with a one-pixel halo
 //   vt2:    K S^2 * 8                   per visited pixel (v / sigma^2, theta2 + 1 / sigma^2)
+//   xch:    32                          a team's exchange slots (partial sums, flags, work items)
+// bw: band row width, vpad for one warp per voxel; with W warps per voxel a
+// warp keeps only its own views' entries, 32 ceil(vpad / 32 W) of them.
 struct WarpSmem {
-    size_t ring, bars, bdesc, coff, pl, cl, halo, band, snap, xt, vt2;
+    size_t ring, bars, bdesc, coff, pl, cl, halo, band, snap, xt, vt2, xch;
     size_t total;
 };
 
-__host__ __device__ inline WarpSmem warp_smem_layout(int vpad, int wmax, int col_stride, int S, int K, bool halo)
+__host__ __device__ inline int band_width(int vpad, int W)
 {
+    return W == 1 ? vpad : 32 * ((vpad + 32 * W - 1) / (32 * W));
+}
+
+__host__ __device__ inline WarpSmem warp_smem_layout(int vpad, int wmax, int col_stride, int S, int K, bool halo,
+                                                     int W = 1)
+{
+    const int bw = band_width(vpad, W);
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t S2 = (size_t)S * S, TA = (size_t)(S + 2) * (S + 2);
     WarpSmem L;
@@ -108,10 +118,11 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int vpad, int wmax, int col
     L.pl = o;    o += r16(2 * S2 * 4);
     L.cl = o;    o += r16(2 * S2 * 8);
     L.halo = o;  o += halo ? r16(2 * TA * 4) : 0;
-    L.band = o;  o += r16(((size_t)wmax * vpad * K + 1) * 8);
-    L.snap = o;  o += r16((size_t)K * wmax * vpad * 4);
+    L.band = o;  o += r16(((size_t)wmax * bw * K + 1) * 8);
+    L.snap = o;  o += r16((size_t)K * wmax * bw * 4);
     L.xt = o;    o += r16((size_t)K * TA * 4);
     L.vt2 = o;   o += r16((size_t)K * S2 * 8);
+    L.xch = o;   o += 32;
     L.total = o;
     return L;
 }
@@ -196,6 +207,27 @@ struct ColRaw {
 // the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
 // z-stack of one volume, 26-neighbourhood prior (K = 1).  DET: deterministic
 // mode (lock-step phases, fixed-point changes of e).
+// A team of W warps of one block sweeping the same super-voxels, the
+// agent's views split between them (warp wi owns views 32 (wi + W j) + lane):
+// each warp keeps its own views' band, the partial sums of a pixel's theta1
+// are added in a fixed order through shared memory, so every warp of the
+// team computes the same step and the same X tile.  xch0: shared address of
+// the team's first warp's exchange slots; stride: bytes between the warps'
+// regions; bar: the team's named barrier (1 + team index in the block).
+struct TeamCtx {
+    int wi, bar;
+    uint32_t xch0, stride;
+};
+
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void team_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Per-warp set-up shared by the launches: ring barriers, and the band at
 // zero (entries outside a super-voxel's band are only ever read and written
 // with matrix value 0, so they stay finite whatever a previous super-voxel
@@ -211,14 +243,18 @@ __device__ __forceinline__ void sweep_warp_init(uint8_t *base, const WarpSmem &L
     __syncwarp();
 }
 
-template <typename T, int K, int R, int RO, bool NB26, bool DET, class ARGS>
+template <typename T, int K, int R, int RO, bool NB26, bool DET, int W, class ARGS>
 __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem &Ly, const int grp, const int g,
-                                           const int cidx, const int Cw, uint32_t &dec, uint32_t &issued)
+                                           const int cidx, const int Cw, uint32_t &dec, uint32_t &issued,
+                                           const TeamCtx &tm)
 {
     static_assert(K == 1 || K == 2, "one or two chains per warp");
     static_assert(!NB26 || K == 1, "volumes run one chain per warp");
+    static_assert(W == 1 || (W == 2 || W == 4) && K == 1 && R == 0 && !DET && !NB26,
+                  "teams of 2 or 4 warps run the 2D decode-at-use sweep, one chain, free mode");
     static_assert((kRing & (kRing - 1)) == 0 && kRing >= 3, "ring size is a power of two >= 4");
     constexpr int LPC = 32 / K;                 // lanes per chain
+    constexpr int LPCV = LPC * W;               // stride between a lane's views
     // R = 0: any number of views, each column decoded from its ring slot at
     // use (RR, RRO size the prefetch registers of the R > 0 kernels)
     constexpr int RR = R > 0 ? R : 1, RRO = RO > 0 ? RO : 1;
@@ -240,7 +276,8 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     float2 *vt20 = (float2 *)(base + Ly.vt2);
 
     const int vpad = A.vpad, wmax = A.wmax;
-    const int nrow = wmax * vpad;               // band entries of one chain
+    const int bw = band_width(vpad, W);         // band row width (this warp's views)
+    const int nrow = wmax * bw;                 // band entries of one chain
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = (int64_t)A.nx * A.ny;
@@ -250,13 +287,14 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     // lane roles in the pixel loop: chain h, index hl inside the chain's lanes
     const int h = K == 2 ? (lane >> 4) : 0;
     const int hl = K == 2 ? (lane & 15) : lane;
+    const int hl_v = (W > 1 ? tm.wi * LPC : 0) + hl;     // this lane's first view
     const uint32_t band_s = smem_u32(band);
     const uint32_t sink_s = band_s + (uint32_t)nrow * K * 8u;
-    const uint32_t tstr = (uint32_t)vpad * K * 8u;      // bytes between band rows
+    const uint32_t tstr = (uint32_t)bw * K * 8u;        // bytes between band rows
     const int v01 = col_v01(Vg), ovc = col_ovc(Vg, vb);
     const uint32_t bdesc_s = smem_u32(bdesc2);
     const uint32_t snap0 = smem_u32(snap) + (uint32_t)(h * nrow + hl) * 4u;   // snapshot of entry (0, hl)
-    const uint32_t sstr = (uint32_t)vpad * 4u;          // bytes between snapshot rows
+    const uint32_t sstr = (uint32_t)bw * 4u;            // bytes between snapshot rows
     // round j: view hl + LPC j, so the round's shared address and column
     // offsets are the first round's plus a constant (a lane past the agent's
     // views reads bytes of its ring slot or of the warp's next region, and
@@ -457,6 +495,30 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     };
 
     int status_seen = 0;
+    // team exchange: every warp adds its value and flag; returns the OR of
+    // the flags and the sum over the team's warps in warp order (the same
+    // bits in every warp).  Slots alternate, so one barrier per exchange
+    // keeps a slot from being rewritten before every warp has read it.
+    uint32_t xpar = 0;
+    auto team_sum = [&](float val, int flag, float &tot) -> int {
+        const uint32_t mine = tm.xch0 + (uint32_t)tm.wi * tm.stride + xpar * 8u;
+        if (lane == 0) {
+            sts_f32(mine, val);
+            sts_u32(mine + 4u, (uint32_t)flag);
+        }
+        team_barrier(tm.bar, 32 * W);
+        float sum = 0.f;
+        uint32_t any = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t a = tm.xch0 + (uint32_t)w * tm.stride + xpar * 8u;
+            sum += lds_f32(a);
+            any |= lds_u32(a + 4u);
+        }
+        xpar ^= 1u;
+        tot = sum;
+        return (int)any;
+    };
     ColRegs<RR, RRO> cc, cn;
     bool have_cur = false;    // cc holds the current super-voxel's first column
 
@@ -488,11 +550,11 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         // global entry in every super-voxel, so a flushed change is seen by
         // the next load of that entry); e also goes into the snapshot
         // (deterministic mode: once the accumulated changes are added)
-        for (int v = hl; v < Vg; v += LPC) {
+        for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
             const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
             const int len = (int)(d >> 16);
             const float2 *src = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
-            uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+            uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
             for (int t = 0; t < len; ++t) {
                 cp_async8_s(ds, src + t);
                 if (!DET) cp_async4_s(ss, src + t);
@@ -569,11 +631,11 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         if (DET) {
             // e = e at launch + the changes accumulated so far; snapshot;
             // then this warp's reads of the phase are done
-            for (int v = hl; v < Vg; v += LPC) {
+            for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
                 const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
                 const int len = (int)(d >> 16);
                 const unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
-                uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+                uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
 #pragma unroll 4
                 for (int t = 0; t < len; ++t) {
                     const float e = lds_f32(ds) + efix_value(__ldcg(da + t));
@@ -598,7 +660,12 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             for (int q = lane; q < count; q += 32) vt2[q].y += A.inv_s2;
         }
         __syncwarp();
-        if (status_seen != 0) {
+        int stop = status_seen != 0;
+        if constexpr (W > 1) {
+            float unused;
+            stop = team_sum(0.f, stop, unused);     // the team stops together
+        }
+        if (stop) {
             // another warp gave up: drain this warp's copies in flight and stop
             drain();
             return false;
@@ -687,8 +754,27 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         // used (views and list entries in run-time rounds, re-read for the
         // update); the slot of the column before is refilled at the start
         const uint32_t pl_s = smem_u32(pl);
+        // three-channel list entry's band address; with a team, whether the
+        // entry's view is this warp's
+        auto ovf_addr = [&](uint32_t code, bool &own) -> uint32_t {
+            if constexpr (W == 1) {
+                own = true;
+                return band_s + (code * K + h) * 8u;
+            } else {
+                const uint32_t row = code / (uint32_t)vpad, v = code - row * (uint32_t)vpad;
+                own = ((v >> 5) & (uint32_t)(W - 1)) == (uint32_t)tm.wi;
+                return band_s + (row * (uint32_t)bw + (((v >> 5) / (uint32_t)W) << 5 | (v & 31u))) * 8u;
+            }
+        };
         auto pixel_any = [&](int q) {
-            if (!wait_column()) return false;
+            const bool okc = wait_column();
+            if (!okc) {
+                if constexpr (W > 1) {
+                    float unused;
+                    team_sum(0.f, 1, unused);    // tell the team at this pixel's exchange
+                }
+                return false;
+            }
             const uint32_t col = ring_s + (dec & (kRing - 1)) * (uint32_t)A.col_stride;
             const int n3 = (int)lds_u16(col);
             const uint32_t ovv = col + (uint32_t)((ovc + 2 * n3 + 3) & ~3);
@@ -715,10 +801,11 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
                 for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
                 pr2 = __shfl_sync(FULL, pr2, lane & ~(LPC - 1));
             }
-            const int nr = (Vg + LPC - 1) / LPC, nro = (n3 + LPC - 1) / LPC;
-            float pa = pr1, pc = 0.f;
+            const int nr = (Vg + LPCV - 1) / LPCV, nro = (n3 + LPC - 1) / LPC;
+            // the prior's gradient enters once per team
+            float pa = (W == 1 || tm.wi == 0) ? pr1 : 0.f, pc = 0.f;
             for (int j = 0; j < nr; ++j) {
-                const int v = hl + LPC * j;
+                const int v = hl_v + LPCV * j;
                 if (v < Vg) {
                     const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
                     const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
@@ -730,17 +817,28 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             for (int o = 0; o < nro; ++o) {
                 const int i = hl + LPC * o;
                 if (i < n3) {
-                    const uint32_t ad = band_s + (lds_u16(col + ovc + 2u * i) * K + h) * 8u;
-                    const float2 e2 = lds_f2(ad);
-                    pa = fmaf(-lds_val<T>(ovv + vb * i) * e2.y, e2.x, pa);
+                    bool own;
+                    const uint32_t ad = ovf_addr(lds_u16(col + ovc + 2u * i), own);
+                    if (own) {
+                        const float2 e2 = lds_f2(ad);
+                        pa = fmaf(-lds_val<T>(ovv + vb * i) * e2.y, e2.x, pa);
+                    }
                 }
             }
             float p1 = pa + pc;
 #pragma unroll
             for (int o = LPC / 2; o > 0; o >>= 1) p1 += __shfl_xor_sync(FULL, p1, o);
+            if constexpr (W > 1) {
+                float tot;
+                if (team_sum(p1, 0, tot)) {
+                    drain();
+                    return false;
+                }
+                p1 = tot;
+            }
             const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
             for (int j = 0; j < nr; ++j) {
-                const int v = hl + LPC * j;
+                const int v = hl_v + LPCV * j;
                 if (v < Vg) {
                     const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
                     const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
@@ -751,8 +849,9 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             for (int o = 0; o < nro; ++o) {
                 const int i = hl + LPC * o;
                 if (i < n3) {
-                    const uint32_t ad = band_s + (lds_u16(col + ovc + 2u * i) * K + h) * 8u;
-                    sts_f(ad, fmaf(-lds_val<T>(ovv + vb * i), alpha, lds_f32(ad)));
+                    bool own;
+                    const uint32_t ad = ovf_addr(lds_u16(col + ovc + 2u * i), own);
+                    if (own) sts_f(ad, fmaf(-lds_val<T>(ovv + vb * i), alpha, lds_f32(ad)));
                 }
             }
             sts_f32(xth_s + tc4, xs + alpha);
@@ -795,9 +894,9 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
                 return false;
             }
         }
-        // --- write back: X tiles and the change of e ---------------------------
+        // --- write back: X tiles (once per team) and the change of e ----------
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < ((W == 1 || tm.wi == 0) ? K : 0); ++k) {
             const float *xt = xt0 + k * TA;
             float *Xg = Xk(k);
             for (int p = lane; p < S2; p += 32) {
@@ -806,11 +905,11 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
                     Xg[(int64_t)(i0 + ti) * A.nx + j0 + tj] = xt[(ti + 1) * TS + tj + 1];
             }
         }
-        for (int v = hl; v < Vg; v += LPC) {
+        for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
             const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
             const int len = (int)(d >> 16);
             float2 *eg = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
-            uint32_t ds = lbase0 + (uint32_t)(v - hl) * K * 8u, ss = snap0 + (uint32_t)(v - hl) * 4u;
+            uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
             unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
             for (int t = 0; t < len; ++t) {
                 const float de = lds_f32(ds) - lds_f32(ss);
@@ -861,8 +960,9 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     const int G = A.B / K;
     const int pair = gw % (G * A.N);
     uint32_t dec = 0, issued = 0;
-    sweep_work<T, K, R, RO, NB26, DET, SweepArgs>(A, base, Ly, pair / A.N, pair % A.N, gw / (G * A.N),
-                                                  A.nwarps / (G * A.N), dec, issued);
+    const TeamCtx solo = {0, 0, 0u, 0u};
+    sweep_work<T, K, R, RO, NB26, DET, 1, SweepArgs>(A, base, Ly, pair / A.N, pair % A.N, gw / (G * A.N),
+                                                     A.nwarps / (G * A.N), dec, issued, solo);
 }
 
 // Work queue over (request, group, agent, row of super-voxels): every resident
@@ -880,21 +980,37 @@ struct QueueArgs {
     int vpad, wmax, col_stride, S;   // shared-memory layout: the largest of the requests
 };
 
-template <typename T, int K, int R, int RO, bool NB26>
+template <typename T, int K, int R, int RO, bool NB26, int W>
 __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_queue_kernel(QueueArgs Q)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    const int lane = threadIdx.x & 31;
-    const WarpSmem Ly = warp_smem_layout(Q.vpad, Q.wmax, Q.col_stride, Q.S, K, NB26);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WarpSmem Ly = warp_smem_layout(Q.vpad, Q.wmax, Q.col_stride, Q.S, K, NB26, W);
     const size_t per_warp = Ly.total + ((sizeof(SweepArgs) + 15) & ~(size_t)15);
-    uint8_t *base = smem + (threadIdx.x >> 5) * per_warp;
+    uint8_t *base = smem + warp * per_warp;
     SweepArgs *args = (SweepArgs *)(base + Ly.total);
-    sweep_warp_init(base, Ly, Q.wmax * Q.vpad * K, lane);
+    sweep_warp_init(base, Ly, Q.wmax * band_width(Q.vpad, W) * K, lane);
+    // a team: W consecutive warps of the block; its first warp takes the
+    // items and hands them over through its exchange slots (two, used in turn)
+    TeamCtx tm;
+    tm.wi = warp % W;
+    tm.bar = 1 + warp / W;
+    tm.stride = (uint32_t)per_warp;
+    tm.xch0 = smem_u32(smem + (warp - tm.wi) * per_warp + Ly.xch);
+    const uint32_t item_slot = tm.xch0 + 16u;
+    uint32_t ipar = 0;
     uint32_t dec = 0, issued = 0;
     for (;;) {
         unsigned item = 0;
-        if (lane == 0) item = atomicAdd(Q.counter, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        if (lane == 0 && tm.wi == 0) item = atomicAdd(Q.counter, 1u);
+        if constexpr (W > 1) {
+            if (lane == 0 && tm.wi == 0) sts_u32(item_slot + 4u * ipar, item);
+            team_barrier(tm.bar, 32 * W);
+            item = lds_u32(item_slot + 4u * ipar);
+            ipar ^= 1u;
+        } else {
+            item = __shfl_sync(0xffffffffu, item, 0);
+        }
         if ((int)item >= Q.total) return;
         int r = 0;
         while (r + 1 < Q.nreq && (int)item >= Q.offsets[r + 1]) ++r;
@@ -909,7 +1025,8 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_queue_kernel(QueueArgs
         int grp = pl / A.N;
         const int g = pl - grp * A.N;
         if (Q.zpar >= 0) grp = 2 * grp + Q.zpar;
-        if (!sweep_work<T, K, R, RO, NB26, false, const SweepArgs &>(A, base, Ly, grp, g, cidx, Cw, dec, issued))
+        if (!sweep_work<T, K, R, RO, NB26, false, W, const SweepArgs &>(A, base, Ly, grp, g, cidx, Cw, dec, issued,
+                                                                          tm))
             return;
         __syncwarp();
     }
@@ -955,19 +1072,23 @@ template <typename T, bool NB26>
 static sweep_queue_fn sweep_queue_lookup_r(int R)
 {
     switch (R) {
-    case 1: return icd_sweep_queue_kernel<T, 1, 1, 1, NB26>;
-    case 2: return icd_sweep_queue_kernel<T, 1, 2, 1, NB26>;
-    case 3: return icd_sweep_queue_kernel<T, 1, 3, 2, NB26>;
-    case 4: return icd_sweep_queue_kernel<T, 1, 4, 2, NB26>;
-    default: return icd_sweep_queue_kernel<T, 1, 0, 1, NB26>;
+    case 1: return icd_sweep_queue_kernel<T, 1, 1, 1, NB26, 1>;
+    case 2: return icd_sweep_queue_kernel<T, 1, 2, 1, NB26, 1>;
+    case 3: return icd_sweep_queue_kernel<T, 1, 3, 2, NB26, 1>;
+    case 4: return icd_sweep_queue_kernel<T, 1, 4, 2, NB26, 1>;
+    default: return icd_sweep_queue_kernel<T, 1, 0, 1, NB26, 1>;
     }
 }
 
 // The queue-fed sweep (one chain per warp) for agents of at most max_views
-// views and the 8- or 26-neighbourhood.
+// views and the 8- or 26-neighbourhood; W = 2 or 4: teams of W warps per
+// super-voxel (2D, decoding each column as it is used).
 template <typename T>
-static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26)
+static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26, int W)
 {
+    if (W == 2 && !nb26) return icd_sweep_queue_kernel<T, 1, 0, 1, false, 2>;
+    if (W == 4 && !nb26) return icd_sweep_queue_kernel<T, 1, 0, 1, false, 4>;
+    if (W != 1) return nullptr;
     const int R = sweep_rounds(max_views, 1);
     return nb26 ? sweep_queue_lookup_r<T, true>(R) : sweep_queue_lookup_r<T, false>(R);
 }
@@ -975,6 +1096,6 @@ static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26)
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26, bool det);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f32(int max_views, bool nb26);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_bf16(int max_views, bool nb26);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f16(int max_views, bool nb26);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f32(int max_views, bool nb26, int W);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_bf16(int max_views, bool nb26, int W);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f16(int max_views, bool nb26, int W);

@@ -207,3 +207,77 @@ def test_queue_more_pairs_than_resident_warps(gpu_lib):
         errs = [nrmse(x[b], xs) for b in range(k, B, 2)]
         print("scan %d: %d reconstructions, worst NRMSE vs oracle %.2e (iters %d)" % (k, len(errs), max(errs), iters))
         assert max(errs) < 1e-4
+
+
+@functools.lru_cache(maxsize=None)
+def wide_case():
+    """40 x 40 pixels, 300 views over 2 agents: 150 views per agent."""
+    n, V, D, N = 40, 300, 59, 2
+    E = synth.ellipses(37, n, 0.02 * 64 / n)
+    p = synth.sinogram(E, V, D)
+    y, lam = synth.measurements(p, 2e4, synth.CounterRNG(137))
+    sx = synth.prior_sigma_x(lam, V, frac=1.0)
+    P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior="qggmrf", sigma_x=sx)
+    return dict(nx=n, ny=n, V=V, D=D, N=N, va=None, y=y[None], lam=lam[None], sx=sx, P=[P])
+
+
+@pytest.mark.parametrize("case,W", [("wide", 2), ("wide", 4), ("ragged", 4)])
+def test_warp_team_one_pass_matches_algorithm2(gpu_lib, case, W):
+    """Teams of W warps per super-voxel (each warp holding a share of the
+    agent's views and of the band, theta1 summed across the team): one pass
+    at concurrency 1 is still Algorithm 2 for every agent.  The ragged case
+    has 10-16 views per agent, so all but one warp of a team of four own no
+    view at all."""
+    mace = gpu_lib
+    c = wide_case() if case == "wide" else ragged_case(1)
+    N, n = c["N"], c["nx"] * c["ny"]
+    sm = mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], N, view_agent=c["va"], sv_size=4)
+    P = c["P"][0]
+    xs = _map(P)
+    rng = np.random.default_rng(11)
+    sc = 0.3 * np.abs(xs).mean()
+    X0 = (xs[None, :] + sc * rng.standard_normal((N, n))).astype(np.float32)
+    v = (xs[None, :] + sc * rng.standard_normal((N, n))).astype(np.float32)
+    for backward in (0, 1):
+        prm = mace.make_params(prior="qggmrf", sigma_x=c["sx"], sigma=0.5, sigma_mode=1, concurrency=1, schedule=1,
+                               warps_per_voxel=W)
+        st = mace.mace_init(sm, c["y"][:1], c["lam"][:1], prm)
+        assert st.stats()["warps_per_voxel"] == W
+        st.set_state(X0.copy(), X0)
+        st.prox_pass(v, backward=bool(backward))
+        _, Xg = st.get_state()
+        Xg = Xg.reshape(N, n)
+        sigma = st.stats()["sigma_abs"]
+        order = st.visit_order()
+        st.close()
+        if backward:
+            order = order[::-1].copy()
+        for g in range(N):
+            x = X0[g].astype(np.float64)
+            e = P.error_sinogram(g, x)
+            P.icd_sweep(g, x, e, v=v[g].astype(np.float64), sigma=sigma, order=order)
+            assert nrmse(Xg[g], x) < 2e-5, (backward, g)
+    sm.close()
+
+
+def test_warp_teams_converge_to_map(gpu_lib):
+    """150 views per agent: the automatic choice is a team of two warps;
+    rows of super-voxels in flight; the image converges to the oracle's MAP
+    image, as with one warp per super-voxel."""
+    mace = gpu_lib
+    c = wide_case()
+    sm = mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], c["N"], sv_size=4)
+    xs = _map(c["P"][0])
+    for W in (0, 1):
+        prm = mace.make_params(prior="qggmrf", sigma_x=c["sx"], sigma=0.3, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
+                               symmetric=True, recompute_every=10, tol=1e-7, max_iter=6000, concurrency=-1,
+                               schedule=1, warps_per_voxel=W)
+        st = mace.mace_init(sm, c["y"], c["lam"], prm)
+        stats = st.stats()
+        assert stats["warps_per_voxel"] == (2 if W == 0 else 1)
+        x, iters, r, conv = st.reconstruct()
+        st.close()
+        err = nrmse(np.asarray(x).ravel(), xs)
+        print("warps per voxel %d: iters %d, NRMSE vs oracle %.2e" % (stats["warps_per_voxel"], iters, err))
+        assert conv and err < 1e-4
+    sm.close()
