@@ -421,11 +421,12 @@ def run_serve(args):
     counts drawn uniformly from SERVE_SIZES and SERVE_AGENTS (BF16 matrices,
     FP32 state, Q-GGMRF 8-neighbour).  First the grouped server's capacity is
     measured with every request waiting at time 0; then Poisson arrivals at
-    args.serve_load times that capacity are served three ways on the same
-    stream: grouped (all active requests in one group, their ICD passes in
-    one queue-fed launch per pass), one stream per request (each with its
-    own fixed-grid sweeps), and one request at a time.  Latency is arrival
-    to image in host memory."""
+    args.serve_load times that capacity are served on the same stream
+    grouped (all active requests in one group, their ICD passes in one
+    queue-fed launch per pass) and one request at a time (and, with
+    --serve-streams, with one stream per request running its own fixed-grid
+    sweeps).  Every mode stops a request at the same Mann residual
+    (args.serve_tol).  Latency is arrival to image in host memory."""
     import torch
     import synth
     from paper_1911_09278_gb300 import build as gbuild
@@ -451,7 +452,7 @@ def run_serve(args):
         srv._matrix(r)
     small = sorted(reqs, key=lambda r: r.nx)[:2]
     srv.run(small, grouped=True)        # warm-up
-    srv.run(small)
+    srv.run(small, serial=True)
     torch.cuda.synchronize()
     calib = srv.run(reqs, grouped=True)     # every request waiting at time 0: capacity
     capacity = len(calib["results"]) / max(1e-9, calib["makespan"])
@@ -459,10 +460,12 @@ def run_serve(args):
     gaps = -np.log(1.0 - rng.uniform(12, np.arange(len(reqs)))) / rate
     t = np.cumsum(gaps) - gaps[0]
     timed = [r._replace(arrival=float(t[k])) for k, r in enumerate(reqs)]
-    runs = {"grouped": srv.run(timed, grouped=True), "streams": srv.run(timed)}
+    runs = {"grouped": srv.run(timed, grouped=True)}
+    if args.serve_streams:
+        runs["streams"] = srv.run(timed)
     if not args.no_serial:
         runs["one_at_a_time"] = srv.run(timed, serial=True)
-    ref = runs.get("one_at_a_time", runs["streams"])
+    ref = runs.get("one_at_a_time", runs.get("streams", runs["grouped"]))
     worst = 0.0
     for r in reqs:
         if r.rid not in runs["grouped"]["results"] or r.rid not in ref["results"]:
@@ -483,7 +486,7 @@ def run_serve(args):
         "p50_s": g["p50"], "p99_s": g["p99"],
         "modes": {k: brief(v) for k, v in runs.items()},
         "capacity_all_at_once": capacity,
-        "max_nrmse_grouped_vs_%s" % ("one_at_a_time" if "one_at_a_time" in runs else "streams"): worst,
+        "max_nrmse_grouped_vs_one_at_a_time": worst if "one_at_a_time" in runs else None,
         "converged": conv, "failed": len(g["failed"]),
         "dtype": args.serve_dtype + "-A/f32", "data": "synthetic",
         "config": {"workload": "stream of %d 2D requests, sizes %s, agents %s, Poisson arrivals at %.3f/s "
@@ -502,9 +505,13 @@ def run_volume(args):
     """A 3D stack: args.slices slices of 512^2 sharing one 2D matrix (960
     views over 180 deg, 725 channels), 32 agents with uneven view subsets
     (16-40 views each, spread over the half circle), 26-neighbourhood
-    Q-GGMRF coupling the slices; all slices and agents in one sweep launch.
-    Times Mann iterations (the iteration count to tolerance is not measured
-    at this size): value = Mann iterations per second of the whole volume."""
+    Q-GGMRF coupling the slices.  Schedule 1 (default): a persistent grid fed
+    from a work queue of (slice, agent, row of super-voxels) items, even
+    slices first, then odd ones; schedule 0: one fixed warp per (slice,
+    agent) pair.  Times args.steps Mann iterations (value = Mann iterations
+    per second of the whole volume); with --volume-tol > 0 it then runs on
+    to that residual (at most args.max_iter iterations) and reports the
+    iterations and the time to get there."""
     import torch
     import synth
     import paper_1911_09278_gb300 as mace
@@ -518,16 +525,16 @@ def run_volume(args):
     va = synth.uneven_partition(204, V, N, 16, 40)
     sx = synth.prior_sigma_x(c["lam"], V, frac=1.0)
     stream = torch.cuda.Stream()
-    # 8x8 super-voxels: with one warp per (slice, agent) the larger tile
-    # amortises the per-super-voxel work better (measured)
-    sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=8, dtype=args.dtype, stream=stream)
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=args.volume_sv, dtype=args.dtype,
+                                   stream=stream)
     info = sm.info()
-    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.serve_sigma, sigma_mode=1, rho=args.rho,
-                           sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter, tol=0.0,
-                           concurrency=args.concurrency, neighbourhood=26)
+    prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.volume_sigma, sigma_mode=1, rho=args.rho,
+                           sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
+                           tol=args.volume_tol, concurrency=args.concurrency, neighbourhood=26,
+                           schedule=args.volume_schedule)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, stream=stream, batch=nz)
     st.iterate(args.warmup)
-    st.set_timing(True, max_launches=2 * args.steps + 8)
+    st.set_timing(True, max_launches=4 * args.steps + 8)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -536,26 +543,43 @@ def run_volume(args):
     stream.synchronize()
     el = ev0.elapsed_time(ev1) / 1000.0
     ms, nl = st.get_timing()
+    st.set_timing(False)
     stats = st.stats()
-    st.close()
-    updates = nz * n * n * N
-    return {
+    r_now, _ = st.poll()
+    out = {
         "metric": "Mann iterations / s of a 3D stack (all slices and agents)", "value": args.steps / el,
         "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "dtype": args.dtype,
         "data": "synthetic (seeded ellipsoid phantom, analytic sinograms, Poisson counts)",
-        "sweep_ms": ms / max(1, nl), "voxel_updates_per_s": updates / (ms / max(1, nl) / 1000.0),
-        "concurrency_per_agent": stats["concurrency"],
+        "sweep_ms": ms / max(1, nl), "voxel_updates_per_s": nz * n * n * N / (ms / max(1, nl) / 1000.0),
+        "residual_after_timed": r_now,
+        "schedule": stats["schedule"], "concurrency_per_agent": stats["concurrency"], "warps": stats["warps"],
         "config": {"workload": "3D %dx%dx%d, 960 views, 725 channels, 32 agents with 16-40 views, "
                                "26-neighbour Q-GGMRF" % (n, n, nz),
-                   "matrix_gb": info["bytes_columns"] / 1e9, "sigma_normalised": args.serve_sigma, "rho": args.rho},
+                   "matrix_gb": info["bytes_columns"] / 1e9, "sv_size": args.volume_sv,
+                   "sigma_normalised": args.volume_sigma, "rho": args.rho},
     }
+    if args.volume_tol > 0:
+        t0 = time.perf_counter()
+        conv, r = False, r_now
+        while not conv and stats["iters"] < args.max_iter:
+            st.launch(50)
+            r, conv = st.poll()
+            stats = st.stats()
+        out["to_tolerance"] = {"tol": args.volume_tol, "converged": conv, "iters": stats["iters"],
+                               "residual": r, "seconds_after_timed": time.perf_counter() - t0,
+                               "seconds_est_total": stats["iters"] * el / args.steps}
+    st.close()
+    sm.close()
+    return out
 
 
 def run_autotune(args):
-    """The sweep-configuration autotuner on the benchmark's scans: for each
-    (super-voxel size, chains) a short probe of Mann iterations, timed, and
-    the iterations to tolerance extrapolated from the residual's rate."""
+    """The sweep-configuration autotuner on the benchmark's scans (or, with
+    --size and --agents, a scan of that size and agent count): for each
+    candidate (super-voxel size, chains, schedule, warps per super-voxel) a
+    short probe of Mann iterations, timed, and the iterations to tolerance
+    extrapolated from the residual's rate."""
     import torch
     import synth
     import paper_1911_09278_gb300 as mace
@@ -564,21 +588,26 @@ def run_autotune(args):
 
     gbuild.build()
     torch.cuda.set_device(0)
+    if args.agents:
+        WORKLOAD["n_agents"] = args.agents
     y, lam = make_inputs(args.batch, 0)
     sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
     params = dict(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
                   symmetric=True, recompute_every=args.recompute_every, max_iter=args.max_iter, tol=args.tol,
                   concurrency=args.concurrency, sv_order=0, forward_geometry=forward_param(args))
+    cands = autotune.candidates_for(-(-WORKLOAD["n_views"] // WORKLOAD["n_agents"]))
     best, table = autotune.tune(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"],
                                 WORKLOAD["n_agents"], y, lam, params, batch=args.batch, dtype=args.dtype,
-                                probe_iters=args.probe_iters)
+                                candidates=cands, probe_iters=args.probe_iters)
     for row in table:
         row.pop("trajectory", None)
         for k, v in row.items():
             if isinstance(v, float) and not math.isfinite(v):
                 row[k] = None     # did not contract within the probe
-    pick = None if best is None else {"sv_size": best["sv_size"], "chains": best["chains"]}
-    return {"mode": "autotune", "workload": WORKLOAD["name"], "batch": args.batch, "sigma_normalised": args.sigma,
+    pick = None if best is None else {k: best[k] for k in ("sv_size", "chains", "schedule", "warps_per_voxel",
+                                                           "concurrency")}
+    return {"mode": "autotune", "workload": "%s (%d agents)" % (WORKLOAD["name"], WORKLOAD["n_agents"]),
+            "batch": args.batch, "sigma_normalised": args.sigma,
             "rho": args.rho, "tol": args.tol, "probe_iters": args.probe_iters, "best": pick, "candidates": table}
 
 
@@ -614,13 +643,16 @@ def build_parser():
                          "(the same geometry family, smaller), instead of the 512^2 workload")
     ap.add_argument("--serve", action="store_true",
                     help="continuous batching vs one-at-a-time service on a request stream (its own JSON line)")
-    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--max-active", dest="max_active", type=int, default=16)
     ap.add_argument("--serve-concurrency", dest="serve_concurrency", type=int, default=-1)
     ap.add_argument("--serve-dtype", dest="serve_dtype", default="bf16", choices=["f32", "bf16", "f16"])
-    # serving and the 3D stack run 8x8 super-voxels, stable up to sigma about 0.14
-    ap.add_argument("--serve-sigma", dest="serve_sigma", type=float, default=0.13)
-    ap.add_argument("--serve-tol", dest="serve_tol", type=float, default=6.5e-7)
+    # serving runs 8x8 super-voxels, one row per item; sigma 0.1 is stable over
+    # the whole size and agent mix (0.13 diverged for 256^2 with 32 agents)
+    ap.add_argument("--serve-sigma", dest="serve_sigma", type=float, default=0.1)
+    ap.add_argument("--serve-tol", dest="serve_tol", type=float, default=1e-5)
+    ap.add_argument("--serve-streams", dest="serve_streams", action="store_true",
+                    help="serving: also run one stream per request (fixed-grid sweeps)")
     ap.add_argument("--serve-load", dest="serve_load", type=float, default=0.8,
                     help="arrival rate as a multiple of the grouped server's capacity")
     ap.add_argument("--no-serial", dest="no_serial", action="store_true",
@@ -628,16 +660,26 @@ def build_parser():
     ap.add_argument("--volume", action="store_true",
                     help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
     ap.add_argument("--slices", type=int, default=64)
+    ap.add_argument("--volume-schedule", dest="volume_schedule", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--volume-sv", dest="volume_sv", type=int, default=8)
+    ap.add_argument("--volume-sigma", dest="volume_sigma", type=float, default=0.13)
+    ap.add_argument("--volume-tol", dest="volume_tol", type=float, default=0.0,
+                    help="volume: after the timed iterations, run on to this Mann residual")
     ap.add_argument("--autotune", action="store_true",
                     help="rank super-voxel sizes and chains on the workload by estimated time to tolerance "
                          "(its own JSON line)")
     ap.add_argument("--probe-iters", dest="probe_iters", type=int, default=100)
+    ap.add_argument("--agents", type=int, default=0, help="autotune: agents of the scan (default 16)")
     return ap
 
 
 def main():
     args = build_parser().parse_args()
     if args.autotune:
+        if args.size:
+            n = args.size
+            WORKLOAD.update(n=n, n_views=int(round(1.40625 * n)), n_channels=int(math.ceil(math.sqrt(2.0) * n)),
+                            name="parallel-beam 2D %dx%d, %d views, Q-GGMRF" % (n, n, int(round(1.40625 * n))))
         print(json.dumps(run_autotune(args)))
         return
     if args.volume:

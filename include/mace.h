@@ -157,8 +157,10 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   the error-sinogram band; a pixel's theta1 is the sum of the warps'
  *   partial sums, added in warp order through shared memory, so every warp
  *   takes the same step (Algorithm 2 is unchanged).  For agents with many
- *   views: fewer views per warp and more warps per agent.  0 = automatic:
- *   1 up to 128 views per agent, else 2 up to 192, else 4. */
+ *   views: fewer views per warp, but more shared memory per view, so fewer
+ *   super-voxels at a time.  0 = automatic: 1 up to 128 views per agent,
+ *   else the largest team (4, then 2) of which the GPU holds one for every
+ *   work item at once, else 1.  A group runs the smallest of its members'. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;

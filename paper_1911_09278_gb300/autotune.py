@@ -1,12 +1,17 @@
 """Autotuner for the sweep configuration of one scan geometry.
 
-Two settings trade sweep speed against convergence:
+Four settings trade sweep speed against convergence:
 - the super-voxel size S, the side of the tile one warp updates. It sets the
   warp's working set and how stale concurrent updates are.
 - the chains per warp, the reconstructions of a batch that share each column
   load. With two chains each half-warp serves one reconstruction.
+- the schedule (fixed warps per pair, or a persistent grid fed from a work
+  queue) and, with the queue, the warps per super-voxel: a team of 2 or 4
+  warps splitting an agent's views, for agents with many views.
+- the concurrency, the super-voxels of one agent in flight (rows of
+  super-voxels by default).
 
-The fixed point depends on neither (Theorem 1), so both are chosen by
+The fixed point depends on none of them (Theorem 1), so they are chosen by
 measurement. For each candidate the tuner:
 1. builds the system matrix (once per S);
 2. runs a short probe of Mann iterations on the caller's scans, timed on the
@@ -28,10 +33,23 @@ import numpy as np
 
 from . import MACE_ENUMERIC, MaceError, mace_build_sysmatrix, mace_init, make_params
 
-Candidate = collections.namedtuple("Candidate", "sv_size chains")
+# schedule, warps_per_voxel: as make_params; concurrency None keeps the
+# caller's
+Candidate = collections.namedtuple("Candidate", "sv_size chains schedule warps_per_voxel concurrency",
+                                   defaults=(0, 0, None))
 # the sizes and chain counts the GPU tests cover; 16 x 16 super-voxels (one
 # chain) are built by the library and may be passed explicitly
 DEFAULT_CANDIDATES = tuple(Candidate(s, k) for s in (4, 8) for k in (1, 2))
+
+
+def candidates_for(views_per_agent):
+    """The default candidates plus the work-queue schedule (one chain), and
+    for agents of more than 128 views teams of 2 and 4 warps per
+    super-voxel."""
+    out = list(DEFAULT_CANDIDATES) + [Candidate(s, 1, 1, 1) for s in (4, 8)]
+    if views_per_agent > 128:
+        out += [Candidate(s, 1, 1, w) for s in (4, 8) for w in (2, 4)]
+    return tuple(out)
 
 
 def estimate_iterations(traj, tol, tail=0.5):
@@ -80,7 +98,10 @@ def tune(nx, ny, n_views, n_channels, n_agents, y, lam, params, batch=1, candida
     matrices = {}
     try:
         for c in candidates:
-            row = dict(sv_size=c.sv_size, chains_asked=c.chains)
+            row = dict(sv_size=c.sv_size, chains_asked=c.chains, schedule=c.schedule,
+                       warps_per_voxel_asked=c.warps_per_voxel)
+            if c.concurrency is not None:
+                row["concurrency_asked"] = c.concurrency
             table.append(row)
             st = None
             try:
@@ -89,10 +110,15 @@ def tune(nx, ny, n_views, n_channels, n_agents, y, lam, params, batch=1, candida
                     sm = mace_build_sysmatrix(nx, ny, n_views, n_channels, n_agents, view_agent=view_agent,
                                               dtype=dtype, sv_size=c.sv_size, stream=stream)
                     matrices[c.sv_size] = sm
-                st = mace_init(sm, y, lam, make_params(**dict(params, chains=c.chains)), stream=stream,
-                               batch=batch)
-                row["chains"] = st.stats()["chains"]
-                key = (c.sv_size, row["chains"])
+                kw = dict(params, chains=c.chains, schedule=c.schedule, warps_per_voxel=c.warps_per_voxel)
+                if c.concurrency is not None:
+                    kw["concurrency"] = c.concurrency
+                st = mace_init(sm, y, lam, make_params(**kw), stream=stream, batch=batch)
+                info = st.stats()
+                row["chains"] = info["chains"]
+                row["warps_per_voxel"] = info.get("warps_per_voxel", 1)
+                row["concurrency"] = info.get("concurrency")
+                key = (c.sv_size, row["chains"], c.schedule, row["warps_per_voxel"], row["concurrency"])
                 if key in seen:
                     row["duplicate_of"] = seen[key]
                     continue

@@ -1232,15 +1232,25 @@ static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26, 
     }
 }
 
-// Warps per super-voxel of the queue-fed sweep: the caller's choice, else
-// one while a warp's lanes hold the agent's views in at most four rounds
-// (the kernels that decode one column ahead), else the smallest team that
-// leaves a warp at most 96 views
-static int resolve_wpv(const mace_params &P, const mace_sysmatrix *M)
+static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L);
+
+// Warps per super-voxel of the queue-fed sweep for `items` work items: the
+// caller's choice, else one while a warp's lanes hold the agent's views in
+// at most four rounds (the kernels that decode one column ahead), else the
+// largest team (4, 2) of which the GPU holds one per item at once: a team
+// shortens each item's chain of pixel steps, but its warps hold more shared
+// memory, so fewer items run at a time (measured on the 512^2 and 1024^2
+// serving sizes)
+static int resolve_wpv(const mace_params &P, const mace_sysmatrix *M, int64_t items)
 {
     if (P.warps_per_voxel > 0) return P.warps_per_voxel;
     if (P.schedule != 1 || P.neighbourhood == 26 || M->max_views <= 128) return 1;
-    return M->max_views <= 2 * 96 ? 2 : 4;
+    for (int W = 4; W >= 2; W /= 2) {
+        QueueLaunch L;
+        const mace_sysmatrix *Ms[1] = {M};
+        if (queue_configure(Ms, 1, false, W, &L) == MACE_OK && (int64_t)L.blocks * L.wpb / W >= items) return W;
+    }
+    return 1;
 }
 
 static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L)
@@ -1356,14 +1366,14 @@ static int configure_queue(mace_state *st)
     const mace_sysmatrix *M = st->M;
     if (st->P.deterministic) return fail(MACE_EINVAL, "the deterministic mode runs the fixed schedule (schedule 0)");
     const mace_sysmatrix *Ms[1] = {M};
-    st->wpv = resolve_wpv(st->P, M);
-    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, st->wpv, &st->q);
-    if (rc) return rc;
-    st->chains = 1;
     // items per pair: `concurrency` rows (0 or -1: one per super-voxel row)
     int64_t C = st->P.concurrency > 0 ? st->P.concurrency : M->nsvy;
     C = std::max<int64_t>(1, std::min<int64_t>(C, M->nsv));
     st->concurrency = (int)C;
+    st->wpv = resolve_wpv(st->P, M, (int64_t)st->B * M->N * C);
+    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, st->wpv, &st->q);
+    if (rc) return rc;
+    st->chains = 1;
     st->sweep_warps = (int)std::min<int64_t>((int64_t)st->q.blocks * st->q.wpb,
                                              (int64_t)st->B * M->N * C * st->wpv);
     st->sweep_wpb = st->q.wpb;
@@ -2029,9 +2039,10 @@ static int group_set(mace_group *G, mace_state *const *members, int n)
         if (st->P.neighbourhood == 26) return fail(MACE_EINVAL, "volumes (neighbourhood 26) are not grouped");
         Ms[k] = st->M;
     }
-    // one team size for the launch: the largest the members resolved
-    int W = 1;
-    for (int k = 0; k < n; ++k) W = std::max(W, members[k]->wpv);
+    // one team size for the launch: the smallest the members resolved (a
+    // team runs the decode-at-use sweep, slower for agents of few views)
+    int W = 4;
+    for (int k = 0; k < n; ++k) W = std::min(W, members[k]->wpv);
     QueueLaunch q;
     int rc = queue_configure(Ms.data(), n, false, W, &q);
     if (rc) return rc;

@@ -67,7 +67,9 @@ class FakeLib:
 
     def init(self, sm, y, lam, prm, stream=None, batch=1):
         chains = prm["chains"] if batch % max(1, prm["chains"]) == 0 else 1
-        sec, q = self.cfg[(sm.sv, chains)]
+        wpv = prm.get("warps_per_voxel", 0) or 1
+        key = (sm.sv, chains) if prm.get("schedule", 0) == 0 else (sm.sv, chains, 1, wpv)
+        sec, q = self.cfg[key]
         lib = self
         lib.open_st += 1
 
@@ -75,7 +77,7 @@ class FakeLib:
             it = 0
 
             def stats(self):
-                return dict(chains=chains)
+                return dict(chains=chains, warps_per_voxel=wpv, concurrency=7)
 
             def iterate(self, k):
                 self.it += k
@@ -160,3 +162,19 @@ def test_tune_rejects_a_probe_shorter_than_two_chunks(fake):
     fake({})
     with pytest.raises(ValueError):
         autotune.tune(8, 8, 4, 5, 1, None, None, dict(tol=1e-6), probe_iters=10, chunk=10)
+
+
+def test_tune_ranks_schedules_and_warp_teams(fake):
+    """Wide agents: the queue-fed schedule with teams of warps per
+    super-voxel competes with the fixed schedule; the fastest to tolerance
+    wins and the row records the team size the library used."""
+    cands = autotune.candidates_for(180)
+    assert autotune.Candidate(4, 1, 1, 4) in cands and autotune.Candidate(8, 1, 1, 2) in cands
+    assert autotune.Candidate(4, 1, 1, 4) not in autotune.candidates_for(45)
+    cfg = {k[:2] if k.schedule == 0 else (k.sv_size, k.chains, 1, k.warps_per_voxel): (2e-3, 0.9) for k in cands}
+    cfg[(4, 1, 1, 4)] = (1e-3, 0.9)
+    lib, clock = fake(cfg)
+    best, table = autotune.tune(64, 64, 720, 95, 4, None, None, dict(tol=1e-6), batch=1, candidates=cands,
+                                clock=clock)
+    assert (best["sv_size"], best["schedule"], best["warps_per_voxel"]) == (4, 1, 4)
+    assert lib.open_sm == 0 and lib.open_st == 0

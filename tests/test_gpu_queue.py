@@ -261,9 +261,9 @@ def test_warp_team_one_pass_matches_algorithm2(gpu_lib, case, W):
 
 
 def test_warp_teams_converge_to_map(gpu_lib):
-    """150 views per agent: the automatic choice is a team of two warps;
-    rows of super-voxels in flight; the image converges to the oracle's MAP
-    image, as with one warp per super-voxel."""
+    """150 views per agent and 20 rows of super-voxels: the automatic choice
+    is a team of four warps (the GPU holds a team for every row); the image
+    converges to the oracle's MAP image, as with one warp per super-voxel."""
     mace = gpu_lib
     c = wide_case()
     sm = mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], c["N"], sv_size=4)
@@ -274,7 +274,7 @@ def test_warp_teams_converge_to_map(gpu_lib):
                                schedule=1, warps_per_voxel=W)
         st = mace.mace_init(sm, c["y"], c["lam"], prm)
         stats = st.stats()
-        assert stats["warps_per_voxel"] == (2 if W == 0 else 1)
+        assert stats["warps_per_voxel"] == (4 if W == 0 else 1)
         x, iters, r, conv = st.reconstruct()
         st.close()
         err = nrmse(np.asarray(x).ravel(), xs)
