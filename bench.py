@@ -562,12 +562,14 @@ def run_volume(args):
     if args.volume_tol > 0:
         t0 = time.perf_counter()
         conv, r = False, r_now
+        traj = []
         while not conv and stats["iters"] < args.max_iter:
             st.launch(50)
             r, conv = st.poll()
             stats = st.stats()
+            traj.append([stats["iters"], r])
         out["to_tolerance"] = {"tol": args.volume_tol, "converged": conv, "iters": stats["iters"],
-                               "residual": r, "seconds_after_timed": time.perf_counter() - t0,
+                               "residual": r, "trajectory": traj, "seconds_after_timed": time.perf_counter() - t0,
                                "seconds_est_total": stats["iters"] * el / args.steps}
     st.close()
     sm.close()
