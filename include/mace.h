@@ -158,9 +158,8 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   partial sums, added in warp order through shared memory, so every warp
  *   takes the same step (Algorithm 2 is unchanged).  For agents with many
  *   views: fewer views per warp, but more shared memory per view, so fewer
- *   super-voxels at a time.  0 = automatic: 1 up to 128 views per agent,
- *   else the largest team (4, then 2) of which the GPU holds one for every
- *   work item at once, else 1.  A group runs the smallest of its members'. */
+ *   super-voxels at a time; which wins depends on the scan (the autotuner
+ *   measures it).  0 = 1.  A group runs the smallest of its members'. */
 typedef struct {
     int32_t prior;
     int32_t neighbourhood;

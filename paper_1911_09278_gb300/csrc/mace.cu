@@ -1232,25 +1232,14 @@ static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26, 
     }
 }
 
-static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L);
-
-// Warps per super-voxel of the queue-fed sweep for `items` work items: the
-// caller's choice, else one while a warp's lanes hold the agent's views in
-// at most four rounds (the kernels that decode one column ahead), else the
-// largest team (4, 2) of which the GPU holds one per item at once: a team
-// shortens each item's chain of pixel steps, but its warps hold more shared
-// memory, so fewer items run at a time (measured on the 512^2 and 1024^2
-// serving sizes)
-static int resolve_wpv(const mace_params &P, const mace_sysmatrix *M, int64_t items)
+// Warps per super-voxel of the queue-fed sweep: the caller's choice, else
+// one.  (A team shortens each item's chain of pixel steps, but its warps hold
+// more shared memory per view, so fewer items run at once: on the 512^2 and
+// 1024^2 scans with 4 to 8 agents it won in some configurations and lost in
+// others, so the choice is left to the caller and the autotuner.)
+static int resolve_wpv(const mace_params &P)
 {
-    if (P.warps_per_voxel > 0) return P.warps_per_voxel;
-    if (P.schedule != 1 || P.neighbourhood == 26 || M->max_views <= 128) return 1;
-    for (int W = 4; W >= 2; W /= 2) {
-        QueueLaunch L;
-        const mace_sysmatrix *Ms[1] = {M};
-        if (queue_configure(Ms, 1, false, W, &L) == MACE_OK && (int64_t)L.blocks * L.wpb / W >= items) return W;
-    }
-    return 1;
+    return P.warps_per_voxel > 0 ? P.warps_per_voxel : 1;
 }
 
 static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L)
@@ -1370,7 +1359,7 @@ static int configure_queue(mace_state *st)
     int64_t C = st->P.concurrency > 0 ? st->P.concurrency : M->nsvy;
     C = std::max<int64_t>(1, std::min<int64_t>(C, M->nsv));
     st->concurrency = (int)C;
-    st->wpv = resolve_wpv(st->P, M, (int64_t)st->B * M->N * C);
+    st->wpv = resolve_wpv(st->P);
     int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, st->wpv, &st->q);
     if (rc) return rc;
     st->chains = 1;

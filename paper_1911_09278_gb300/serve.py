@@ -55,9 +55,11 @@ class Server:
     """Host-side scheduler; see the module docstring.
 
     params: keyword arguments for make_params (sigma_x comes per request).
-    max_active: requests on the GPU at once.  budget: device bytes the
-    server may hold (system matrices + states).  chunk: iterations enqueued
-    per request between polls."""
+    sv_size: super-voxel side, or "auto": 4 for agents of more than 64 views
+    (more, smaller items in flight: faster for the wide agents of large
+    scans with few agents, measured), else 8.  max_active: requests on the
+    GPU at once.  budget: device bytes the server may hold (system matrices
+    + states).  chunk: iterations enqueued per request between polls."""
 
     def __init__(self, params, dtype="bf16", sv_size=8, max_active=8, budget=64 << 30,
                  chunk=10, max_iter=4000):
@@ -73,9 +75,14 @@ class Server:
         self.matrices = {}      # geometry key -> Sysmatrix
         self.matrix_bytes = {}
 
+    def _sv(self, r):
+        if self.sv_size != "auto":
+            return self.sv_size
+        return 4 if r.n_views > 64 * r.n_agents else 8
+
     def _key(self, r):
         va = None if r.view_agent is None else bytes(np.asarray(r.view_agent, np.int32))
-        return (r.nx, r.ny, r.n_views, r.n_channels, r.n_agents, va)
+        return (r.nx, r.ny, r.n_views, r.n_channels, r.n_agents, va, self._sv(r))
 
     def _resident(self):
         return sum(self.matrix_bytes.values())
@@ -84,7 +91,7 @@ class Server:
         k = self._key(r)
         if k not in self.matrices:
             sm = mace_build_sysmatrix(r.nx, r.ny, r.n_views, r.n_channels, r.n_agents,
-                                      view_agent=r.view_agent, dtype=self.dtype, sv_size=self.sv_size)
+                                      view_agent=r.view_agent, dtype=self.dtype, sv_size=self._sv(r))
             info = sm.info()
             self.matrices[k] = sm
             self.matrix_bytes[k] = info["bytes_columns"] + info["bytes_meta"]

@@ -261,20 +261,20 @@ def test_warp_team_one_pass_matches_algorithm2(gpu_lib, case, W):
 
 
 def test_warp_teams_converge_to_map(gpu_lib):
-    """150 views per agent and 20 rows of super-voxels: the automatic choice
-    is a team of four warps (the GPU holds a team for every row); the image
-    converges to the oracle's MAP image, as with one warp per super-voxel."""
+    """150 views per agent, rows of super-voxels in flight: with teams of
+    two and four warps the image converges to the oracle's MAP image, as
+    with one warp per super-voxel (the default, 0)."""
     mace = gpu_lib
     c = wide_case()
     sm = mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], c["N"], sv_size=4)
     xs = _map(c["P"][0])
-    for W in (0, 1):
+    for W in (0, 2, 4):
         prm = mace.make_params(prior="qggmrf", sigma_x=c["sx"], sigma=0.3, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
                                symmetric=True, recompute_every=10, tol=1e-7, max_iter=6000, concurrency=-1,
                                schedule=1, warps_per_voxel=W)
         st = mace.mace_init(sm, c["y"], c["lam"], prm)
         stats = st.stats()
-        assert stats["warps_per_voxel"] == (4 if W == 0 else 1)
+        assert stats["warps_per_voxel"] == max(W, 1)
         x, iters, r, conv = st.reconstruct()
         st.close()
         err = nrmse(np.asarray(x).ravel(), xs)
