@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmace.so")
+# MACE_DEBUG=1: the build with device-side bounds checks (build(debug=True))
+LIB_PATH = os.path.join(HERE, "libmace_debug.so" if os.environ.get("MACE_DEBUG") == "1" else "libmace.so")
 
 MACE_OK = 0
 MACE_EINVAL = -1

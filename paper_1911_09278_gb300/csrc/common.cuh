@@ -19,6 +19,23 @@ static constexpr int kMaxViews = 4096;     // per geometry
 static constexpr int kRing = MACE_RING;
 static constexpr uint32_t kSpinLimit = 1u << 26;  // bounded device waits
 static constexpr int kStatusTimeout = 1;
+static constexpr int kStatusBounds = 2;      // a MACE_DEBUG bounds check failed
+
+// MACE_DEBUG builds check the indices the kernels read from stored data
+// (run headers, three-channel list codes, band descriptors, column sizes)
+// against the buffers they address; a failed check sets the device status
+// word to kStatusBounds (the host returns an error) and the access is
+// redirected to a safe location instead of being made.
+#ifdef MACE_DEBUG
+static constexpr bool kDebug = true;
+#else
+static constexpr bool kDebug = false;
+#endif
+__device__ __forceinline__ bool debug_ok(bool cond, int *status)
+{
+    if (kDebug && !cond) atomicExch(status, kStatusBounds);
+    return !kDebug || cond;
+}
 
 // --- stored column format ----------------------------------------------------
 // Column of one pixel for one agent with Vg views: the per-view runs (first

@@ -29,8 +29,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "sweep.cuh"
+
+// NVTX range over a host call (shown by Nsight Systems and ncu's NVTX
+// filters; without a tool attached a push or pop costs a few nanoseconds)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // error handling
@@ -288,6 +299,7 @@ extern "C" int mace_build_sysmatrix(const mace_geometry *geom, const mace_partit
                                     mace_dtype dtype, int32_t sv_size, void *cuda_stream,
                                     mace_sysmatrix **out)
 {
+    NvtxRange nvtx_range("mace_build_sysmatrix");
     if (!out) return fail(MACE_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = check_geometry(geom);
@@ -1085,6 +1097,7 @@ static void launch_forward_t(mace_state *st, unsigned blocks)
 // e_i = y_i - A_i X_i for every reconstruction and agent
 static int launch_forward(mace_state *st)
 {
+    NvtxRange nvtx_range("e recompute");
     const mace_sysmatrix *M = st->M;
     int64_t items = (int64_t)st->B * M->N * M->nsv;
     unsigned blocks = (unsigned)((items * 32 + 255) / 256);
@@ -1184,6 +1197,7 @@ static int launch_sweep_queue(mace_state *st, int backward, const float *vexp);
 
 static int launch_sweep(mace_state *st, int backward, const float *vexp)
 {
+    NvtxRange nvtx_range("ICD sweep");
     if (st->P.schedule == 1) return launch_sweep_queue(st, backward, vexp);
     const mace_sysmatrix *M = st->M;
     const SweepArgs A = sweep_args(st, backward, vexp);
@@ -1568,6 +1582,7 @@ static int copy_out(void *dst, const void *src, size_t bytes, int is_dev, cudaSt
 // the mean; x_out (device, optional) receives it in FP32.
 static int apply_consensus(mace_state *st, float *x_out)
 {
+    NvtxRange nvtx_range("consensus");
     const mace_sysmatrix *M = st->M;
     const int64_t Bn = (int64_t)st->B * st->n;
     const unsigned blocks = (unsigned)((Bn + 255) / 256);
@@ -1604,6 +1619,7 @@ extern "C" int mace_init(const mace_sysmatrix *M, int32_t batch, const float *y,
                          int32_t ptr_is_device, const mace_params *params, const float *w0, void *cuda_stream,
                          mace_state **out)
 {
+    NvtxRange nvtx_range("mace_init");
     if (!out) return fail(MACE_EINVAL, "out is NULL");
     *out = nullptr;
     if (!M || !y || !weights) return fail(MACE_EINVAL, "NULL sysmatrix, y or weights");
@@ -1809,6 +1825,7 @@ static int iteration_post(mace_state *st)
 
 static int run_iteration(mace_state *st)
 {
+    NvtxRange nvtx_range("Mann iteration");
     int rc = iteration_pre(st);
     if (rc) return rc;
     for (int k = 0; k < st->P.sweeps_per_iter; ++k) {
@@ -1823,6 +1840,8 @@ static int run_iteration(mace_state *st)
 static int parse_status(mace_state *st, const double *h, int status, double *r)
 {
     if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+    if (status == kStatusBounds)
+        return fail(MACE_ECUDA, "a device-side bounds check failed (MACE_DEBUG build): stored matrix or state inconsistent");
     double worst = 0.0;
     for (int b = 0; b < st->B; ++b) {
         double rb = h[3 * b + 2];
@@ -2136,6 +2155,7 @@ extern "C" int mace_group_update(mace_group *G, mace_state *const *members, int3
 
 extern "C" int mace_group_launch(mace_group *G, int32_t n_iters)
 {
+    NvtxRange nvtx_range("group launch");
     if (!G) return fail(MACE_EINVAL, "group is NULL");
     if (n_iters < 0) return fail(MACE_EINVAL, "n_iters must be >= 0");
     if (n_iters == 0) return MACE_OK;
@@ -2249,6 +2269,7 @@ extern "C" int mace_consensus_noalloc(mace_state *st, float *x_out, int32_t ptr_
 extern "C" int mace_reconstruct(mace_state *st, float *x_out, int32_t ptr_is_device, int32_t *iters_out,
                                 double *residual_out)
 {
+    NvtxRange nvtx_range("mace_reconstruct");
     if (!st || !x_out) return fail(MACE_EINVAL, "NULL argument");
     const int check = 10;
     double r = st->last_resid;
@@ -2305,6 +2326,8 @@ extern "C" int mace_prox_pass(mace_state *st, const float *v, int32_t ptr_is_dev
         CUDA_TRY(cudaMemcpyAsync(&status, st->d_status, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
         CUDA_TRY(cudaStreamSynchronize(st->stream));
         if (status == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+        if (status == kStatusBounds)
+            return fail(MACE_ECUDA, "a device-side bounds check failed (MACE_DEBUG build): stored matrix or state inconsistent");
     }
     return rc;
 }
@@ -2360,6 +2383,8 @@ extern "C" int mace_wait_selftest(uint32_t spin_limit, void *cuda_stream)
     cudaFree(d);
     if (ce != cudaSuccess) return fail(MACE_ECUDA, std::string("wait self test: ") + cudaGetErrorString(ce));
     if (h == kStatusTimeout) return fail(MACE_ETIMEOUT, "a device-side wait timed out");
+    if (h == kStatusBounds)
+        return fail(MACE_ECUDA, "a device-side bounds check failed (MACE_DEBUG build): stored matrix or state inconsistent");
     return MACE_OK;
 }
 

@@ -388,6 +388,8 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     const uint64_t stream_policy = l2_evict_first_policy();
     auto issue = [&](uint32_t idx, const uint8_t *src, uint32_t bytes) {
         const uint32_t stg = idx & (kRing - 1);
+        if (kDebug && !debug_ok(bytes >= 16 && bytes <= (uint32_t)A.col_stride && (bytes & 15u) == 0, A.status))
+            bytes = 16;     // a safe copy: the column's first 16 bytes
         tma_load_1d_lane0(ring + (size_t)stg * A.col_stride, src, bytes, &bars[stg], lane, stream_policy);
     };
 
@@ -475,14 +477,16 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     auto col_finish = [&](const ColRaw<RR, RRO> &w, ColRegs<RR, RRO> &c, const uint2 *cl, const uint2 *cl_n) {
 #pragma unroll
         for (int j = 0; j < RR; ++j) {
-            const bool ok = (vokm >> j) & 1u;
+            bool ok = (vokm >> j) & 1u;
+            if (kDebug && ok) ok = debug_ok((w.hb[j] & 63u) + 1u < (uint32_t)wmax, A.status);
             c.addr[j] = ok ? lbase0 + 256u * j + (w.hb[j] & 63u) * tstr : sink_s - tstr;
             c.a0[j] = ok ? w.a[j].x : 0.f;
             c.a1[j] = ok ? w.a[j].y : 0.f;
         }
 #pragma unroll
         for (int o = 0; o < RRO; ++o) {
-            const bool ok = hl + LPC * o < w.n3;
+            bool ok = hl + LPC * o < w.n3;
+            if (kDebug && ok) ok = debug_ok(w.code[o] < (uint32_t)(wmax * vpad), A.status);
             c.oaddr[o] = ok ? band_s + (w.code[o] * K + h) * 8u : sink_s;
             c.a2[o] = ok ? w.a2[o] : 0.f;
         }
@@ -552,7 +556,8 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         // (deterministic mode: once the accumulated changes are added)
         for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
             const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
-            const int len = (int)(d >> 16);
+            int len = (int)(d >> 16);
+            if (kDebug && !debug_ok(len <= wmax && (int)(d & 0xFFFFu) + len <= A.D, A.status)) len = 0;
             const float2 *src = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
             uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
             for (int t = 0; t < len; ++t) {
@@ -633,7 +638,8 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             // then this warp's reads of the phase are done
             for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
                 const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
-                const int len = (int)(d >> 16);
+                int len = (int)(d >> 16);
+            if (kDebug && !debug_ok(len <= wmax && (int)(d & 0xFFFFu) + len <= A.D, A.status)) len = 0;
                 const unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
                 uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
 #pragma unroll 4
@@ -757,6 +763,10 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         // three-channel list entry's band address; with a team, whether the
         // entry's view is this warp's
         auto ovf_addr = [&](uint32_t code, bool &own) -> uint32_t {
+            if (kDebug && !debug_ok(code < (uint32_t)(wmax * vpad), A.status)) {
+                own = false;
+                return sink_s;
+            }
             if constexpr (W == 1) {
                 own = true;
                 return band_s + (code * K + h) * 8u;
@@ -806,7 +816,7 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             float pa = (W == 1 || tm.wi == 0) ? pr1 : 0.f, pc = 0.f;
             for (int j = 0; j < nr; ++j) {
                 const int v = hl_v + LPCV * j;
-                if (v < Vg) {
+                if (v < Vg && debug_ok((lds_u8(col + 2u + v) & 63u) + 1u < (uint32_t)wmax, A.status)) {
                     const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
                     const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
                     const float2 e0 = lds_f2(ad), e1 = lds_f2(ad + tstr);
@@ -839,7 +849,7 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             const float alpha = -(p1 + prox) * rcp_approx(vq.y + pr2);
             for (int j = 0; j < nr; ++j) {
                 const int v = hl_v + LPCV * j;
-                if (v < Vg) {
+                if (v < Vg && (!kDebug || (lds_u8(col + 2u + v) & 63u) + 1u < (uint32_t)wmax)) {
                     const float2 a = lds_pair<T>(col + v01 + 2u * vb * v);
                     const uint32_t ad = lbase0 + 256u * j + (lds_u8(col + 2u + v) & 63u) * tstr;
                     sts_f(ad, fmaf(-a.x, alpha, lds_f32(ad)));
@@ -907,7 +917,8 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
         }
         for (int v = hl_v, jj = 0; v < Vg; v += LPCV, ++jj) {
             const uint32_t d = lds_u32(bdesc_s + cur * vpad * 4u + 4u * v);
-            const int len = (int)(d >> 16);
+            int len = (int)(d >> 16);
+            if (kDebug && !debug_ok(len <= wmax && (int)(d & 0xFFFFu) + len <= A.D, A.status)) len = 0;
             float2 *eg = eLh + (int64_t)v * A.D + (d & 0xFFFFu);
             uint32_t ds = lbase0 + (uint32_t)jj * 256u, ss = snap0 + (uint32_t)(jj * LPC) * 4u;
             unsigned long long *da = dacch + (int64_t)v * A.D + (d & 0xFFFFu);
