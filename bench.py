@@ -142,13 +142,13 @@ def make_inputs(batch, rank):
     return y, lam
 
 
-def oracle_match(x, y, lam, dtype="f32"):
-    """Relative RMSE of the first reconstruction of the batch against the
-    oracle's stored MAP image of the same scan (written by
+def oracle_match(x, y, lam, dtype="f32", sx=None, name="cfg2"):
+    """Relative RMSE of a reconstruction against the oracle's stored MAP image
+    of the same scan (tests/golden/<name>_reference.npz, written by
     tests/golden/make_reference.py from the oracle alone), when the stored
-    image's input digest matches."""
+    image's input digest and prior scale match."""
     import hashlib
-    path = os.path.join(ROOT, "tests", "golden", "cfg2_reference.npz")
+    path = os.path.join(ROOT, "tests", "golden", "%s_reference.npz" % name)
     if not os.path.exists(path):
         return {"nrmse_vs_oracle": None, "why": "no stored oracle image"}
     d = np.load(path)
@@ -157,6 +157,8 @@ def oracle_match(x, y, lam, dtype="f32"):
     h.update(np.ascontiguousarray(lam, np.float32).tobytes())
     if str(d["digest"]) != h.hexdigest():
         return {"nrmse_vs_oracle": None, "why": "stored oracle image is of other inputs"}
+    if sx is not None and abs(float(d["sigma_x"]) - sx) > 1e-6 * abs(sx):
+        return {"nrmse_vs_oracle": None, "why": "stored oracle image is of another prior scale"}
     ref = d["x"].reshape(x.shape)
     err = float(np.sqrt(np.mean((x.astype(np.float64) - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
     return {"nrmse_vs_oracle": err, "bound": 1e-4 if dtype == "f32" else 1e-3, "oracle_kkt": float(d["kkt"]),
@@ -196,7 +198,7 @@ def run_mace(args, rank, world):
         dist.init_process_group("nccl")
     B = args.batch
     y, lam = make_inputs(B, rank)
-    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=args.prior_frac)
     stream = torch.cuda.Stream()
     sm = mace.mace_build_sysmatrix(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"],
                                    WORKLOAD["n_agents"], sv_size=args.sv, dtype=args.dtype, stream=stream)
@@ -264,7 +266,10 @@ def run_mace(args, rank, world):
     el, clocks = timed(True, True, args.warmup)
     iters_main = [it for it, _, _ in iters_seen[-args.steps:]]
     conv_main = all(c for _, _, c in iters_seen[-args.steps:])
-    accuracy = oracle_match(d_x[0].cpu().numpy(), y[0], lam[0], args.dtype)
+    accuracy = oracle_match(d_x[0].cpu().numpy(), y[0], lam[0], args.dtype, sx)
+    if B > 1:
+        accuracy = {"scan0": accuracy,
+                    "scan1": oracle_match(d_x[1].cpu().numpy(), y[1], lam[1], args.dtype, sx, name="cfg2_scan1")}
     el_e2e, _ = timed(False, False, 1)
     recons = B * args.steps * world
     value = recons / el
@@ -335,6 +340,7 @@ def run_mace(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, int(np.mean(iters_main)),
                                            seconds=args.cpu_seconds)
+        out["cpu_baseline"]["config1_to_tolerance"] = config1_to_tolerance()
     if dist:
         dist.destroy_process_group()
     return out
@@ -377,6 +383,50 @@ def cpu_baseline(args, y, lam, sx, iters, seconds=20.0):
                             "sample": "1 sweep of the centralised MAP ICD over all views"}}
 
 
+def config1_to_tolerance(tol=1e-6):
+    """Both sides timed to the same tolerance, nothing extrapolated: config 1
+    (64^2, 90 views, 95 channels, 4 interleaved agents, quadratic prior,
+    normalised sigma 1, rho 0.8, one ICD pass per Mann iteration, serial
+    voxel order).  The oracle (FP64, one thread per agent) on the host cores
+    and the library (one warp per agent) each run Algorithm 1 from w = 0 to
+    the Mann residual tol; the images are compared at the end."""
+    import torch
+    import synth
+    import oracle
+    import paper_1911_09278_gb300 as mace
+    cfg = synth.CONFIGS["cfg1"]
+    c = synth.make_case(**{k: cfg[k] for k in ("n", "n_views", "n_channels", "I0", "mu_max", "seed", "noise_seed")})
+    y, lam = c["y"][0], c["lam"][0]
+    n, V, D, N = cfg["n"], cfg["n_views"], cfg["n_channels"], cfg["n_agents"]
+    sx = synth.prior_sigma_x(lam, V, frac=cfg["prior_frac"])
+    threads = min(N, os.cpu_count() or 1)
+    P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior="quadratic", sigma_x=sx)
+    sigma = 1.0 / math.sqrt(oracle.mean_theta2(P))
+    t0 = time.perf_counter()
+    res = P.mace(sigma, rho=0.8, sweeps=1, symmetric=False, max_iter=20000, tol=tol, n_threads=threads)
+    t_cpu = time.perf_counter() - t0
+    sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=8)
+    prm = mace.make_params(prior="quadratic", sigma_x=sx, sigma=1.0, sigma_mode=1, rho=0.8, sweeps_per_iter=1,
+                           tol=tol, max_iter=20000, concurrency=1)
+    st = mace.mace_init(sm, y, lam, prm)       # warm-up: kernels loaded, graph captured
+    st.reconstruct()
+    st.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = mace.mace_init(sm, y, lam, prm)
+    x, iters, r, conv = st.reconstruct()
+    t_gpu = time.perf_counter() - t0
+    st.close()
+    sm.close()
+    xo = np.asarray(res["x"], np.float64)
+    return {"tol": tol, "oracle": {"s_per_recon": t_cpu, "iters": int(res["iters"]), "cores": threads},
+            "gpu": {"s_per_recon": t_gpu, "iters": int(iters), "converged": bool(conv),
+                    "includes": "mace_init (inputs from host memory) + mace_reconstruct + image to host"},
+            "gpu_over_oracle": t_cpu / t_gpu,
+            "nrmse_gpu_vs_oracle": float(np.linalg.norm(np.asarray(x, np.float64).ravel() - xo)
+                                         / np.linalg.norm(xo))}
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: each step is a bounded sample of the
     same workload (a few Mann iterations), reported in reconstructions/s."""
@@ -385,7 +435,7 @@ def run_reference(args, rank, world):
     import synth
     import oracle
     y, lam = make_inputs(1, 0)
-    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=args.prior_frac)
     threads = os.cpu_count() or 1
     P = oracle.Problem(WORKLOAD["n"], WORKLOAD["n"], WORKLOAD["n_views"], WORKLOAD["n_channels"], y[0], lam[0],
                        n_agents=WORKLOAD["n_agents"], prior="qggmrf", sigma_x=sx)
@@ -448,8 +498,11 @@ def run_serve(args):
                             noise_seed=3000 + k)
         sx = synth.prior_sigma_x(c["lam"][0], V, frac=1.0)
         reqs.append(serve.Request(k, 0.0, n, n, V, D, N, c["y"][0], c["lam"][0], sx, None))
+    # the work-queue sweep in every mode, so one request's iterates are the
+    # same served grouped and alone (up to the order of float additions)
     params = dict(prior="qggmrf", sigma=args.serve_sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
-                  symmetric=True, recompute_every=10, tol=args.serve_tol, concurrency=args.serve_concurrency)
+                  symmetric=True, recompute_every=10, tol=args.serve_tol, concurrency=args.serve_concurrency,
+                  schedule=1)
     srv = serve.Server(params, dtype=args.serve_dtype, sv_size="auto", max_active=args.max_active,
                        max_iter=args.max_iter)
     for r in reqs:                      # matrices resident before any timing
@@ -611,7 +664,7 @@ def run_autotune(args):
     if args.agents:
         WORKLOAD["n_agents"] = args.agents
     y, lam = make_inputs(args.batch, 0)
-    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=1.0)
+    sx = synth.prior_sigma_x(lam[0], WORKLOAD["n_views"], frac=args.prior_frac)
     params = dict(prior="qggmrf", sigma_x=sx, sigma=args.sigma, sigma_mode=1, rho=args.rho, sweeps_per_iter=2,
                   symmetric=True, recompute_every=args.recompute_every, max_iter=args.max_iter, tol=args.tol,
                   concurrency=args.concurrency, sv_order=0, forward_geometry=forward_param(args))
@@ -657,6 +710,9 @@ def build_parser():
     ap.add_argument("--oracle-iters", dest="oracle_iters", type=int, default=670,
                     help="Mann iterations to tolerance the reference arm scales its sample to (the GPU path's count at the default settings)")
     ap.add_argument("--cpu-seconds", dest="cpu_seconds", type=float, default=20.0)
+    ap.add_argument("--prior-frac", dest="prior_frac", type=float, default=1.0,
+                    help="prior curvature as a fraction of the data curvature (1/sigma_x^2 = frac x the median "
+                         "pixel data curvature)")
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--size", type=int, default=0,
                     help="profiling only: an n x n image with 1.40625 n views and ceil(sqrt(2) n) channels "
