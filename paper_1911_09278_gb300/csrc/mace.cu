@@ -2077,10 +2077,23 @@ static int group_set(mace_group *G, mace_state *const *members, int n)
     }
     SweepArgs *tab = (SweepArgs *)G->h_stage[slot];
     int *off = (int *)(G->h_stage[slot] + tab_bytes);
+    // requests in decreasing order of an item's length (pixels of its share
+    // of super-voxels times the agent's views): the longest items start
+    // first and short ones fill in behind them, so a pass ends soon after
+    // its longest item (a longest-first schedule)
+    std::vector<int> order(n);
+    std::vector<double> cost(n);
+    for (int k = 0; k < n; ++k) {
+        const mace_state *st = members[k];
+        const mace_sysmatrix *M = st->M;
+        order[k] = k;
+        cost[k] = (double)M->nsv / st->concurrency * M->S2 * M->max_views;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     for (int p = 0; p < npass; ++p) {
         int r = 0, t = 0;
-        for (int k = 0; k < n; ++k) {
-            const mace_state *st = members[k];
+        for (int kk = 0; kk < n; ++kk) {
+            const mace_state *st = members[order[kk]];
             if (st->P.sweeps_per_iter <= p) continue;
             tab[(size_t)p * n + r] = sweep_args(st, st->P.symmetric ? (p & 1) : 0, nullptr);
             off[(size_t)p * (n + 1) + r] = t;
