@@ -340,7 +340,10 @@ def run_mace(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, y[0], lam[0], sx, int(np.mean(iters_main)),
                                            seconds=args.cpu_seconds)
-        out["cpu_baseline"]["config1_to_tolerance"] = config1_to_tolerance()
+        try:
+            out["cpu_baseline"]["config1_to_tolerance"] = config1_to_tolerance()
+        except Exception as e:      # a side-measurement: never fails the benchmark line
+            out["cpu_baseline"]["config1_to_tolerance"] = {"error": str(e)}
     if dist:
         dist.destroy_process_group()
     return out
@@ -386,8 +389,10 @@ def cpu_baseline(args, y, lam, sx, iters, seconds=20.0):
 def config1_to_tolerance(tol=1e-6):
     """Both sides timed to the same tolerance, nothing extrapolated: config 1
     (64^2, 90 views, 95 channels, 4 interleaved agents, quadratic prior,
-    normalised sigma 1, rho 0.8, one ICD pass per Mann iteration, serial
-    voxel order).  The oracle (FP64, one thread per agent) on the host cores
+    rho 0.8, serial voxel order) at the parity tests' solver settings:
+    normalised sigma 0.5 and two symmetric ICD passes per Mann iteration (at
+    normalised sigma 1 with one pass the partial-update iteration diverges
+    on both sides: Theorem 2 asks for a small enough sigma).  The oracle (FP64, one thread per agent) on the host cores
     and the library (one warp per agent) each run Algorithm 1 from w = 0 to
     the Mann residual tol; the images are compared at the end."""
     import torch
@@ -401,13 +406,13 @@ def config1_to_tolerance(tol=1e-6):
     sx = synth.prior_sigma_x(lam, V, frac=cfg["prior_frac"])
     threads = min(N, os.cpu_count() or 1)
     P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior="quadratic", sigma_x=sx)
-    sigma = 1.0 / math.sqrt(oracle.mean_theta2(P))
+    sigma = 0.5 / math.sqrt(oracle.mean_theta2(P))
     t0 = time.perf_counter()
-    res = P.mace(sigma, rho=0.8, sweeps=1, symmetric=False, max_iter=20000, tol=tol, n_threads=threads)
+    res = P.mace(sigma, rho=0.8, sweeps=2, symmetric=True, max_iter=20000, tol=tol, n_threads=threads)
     t_cpu = time.perf_counter() - t0
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, sv_size=8)
-    prm = mace.make_params(prior="quadratic", sigma_x=sx, sigma=1.0, sigma_mode=1, rho=0.8, sweeps_per_iter=1,
-                           tol=tol, max_iter=20000, concurrency=1)
+    prm = mace.make_params(prior="quadratic", sigma_x=sx, sigma=0.5, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
+                           symmetric=True, recompute_every=10, tol=tol, max_iter=20000, concurrency=1)
     st = mace.mace_init(sm, y, lam, prm)       # warm-up: kernels loaded, graph captured
     st.reconstruct()
     st.close()
