@@ -221,9 +221,11 @@ CONFIGS = {
     # 512^2, 720 views, 725 channels, 16 agents x 45 views, Q-GGMRF
     "cfg2": dict(n=512, n_views=720, n_channels=725, I0=2e4, mu_max=0.02 * 64 / 512,
                  n_agents=16, prior="qggmrf", seed=2, noise_seed=102, prior_frac=1.0),
-    # the benchmark batch's second scan (phantom and noise seeds + 7)
+    # the benchmark batch's second scan (phantom and noise seeds + 7); the
+    # batch shares one prior scale, set from the first scan's weights
     "cfg2_scan1": dict(n=512, n_views=720, n_channels=725, I0=2e4, mu_max=0.02 * 64 / 512,
-                       n_agents=16, prior="qggmrf", seed=9, noise_seed=109, prior_frac=1.0),
+                       n_agents=16, prior="qggmrf", seed=9, noise_seed=109, prior_frac=1.0,
+                       prior_scale_from="cfg2"),
 }
 
 

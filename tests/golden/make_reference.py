@@ -36,7 +36,11 @@ def main(name, threads=0, target=1e-9, max_iter=20000, chunk=50):
     c = synth.make_case(**cfg)
     y, lam = c["y"][0], c["lam"][0]
     n, V, D, N = cfg["n"], cfg["n_views"], cfg["n_channels"], cfg["n_agents"]
-    sx = synth.prior_sigma_x(lam, V, frac=cfg.get("prior_frac", 1.0))
+    # the prior scale comes from this scan's weights, or from another
+    # configuration's (a batch reconstructed with one shared scale)
+    src = cfg.get("prior_scale_from")
+    lam_s = lam if src is None else synth.make_case(**synth.CONFIGS[src])["lam"][0]
+    sx = synth.prior_sigma_x(lam_s, V, frac=cfg.get("prior_frac", 1.0))
     P = oracle.Problem(n, n, V, D, y, lam, n_agents=N, prior=cfg["prior"], sigma_x=sx)
     t0 = time.time()
     t2 = oracle.mean_theta2(P)
