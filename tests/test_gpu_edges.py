@@ -187,3 +187,34 @@ def test_state_bytes_matches_device_usage(gpu_lib):
     assert used <= persistent + (32 << 20)
     st.close()
     sm.close()
+
+
+@pytest.mark.parametrize("sv", [16, 32])
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_large_super_voxels_one_pass(gpu_lib, sv, schedule):
+    """16 x 16 and 32 x 32 super-voxels (the largest tiles, widest bands):
+    one pass at concurrency 1 equals Algorithm 2 for every agent, on the
+    fixed grid and on the work queue."""
+    mace = gpu_lib
+    c = edge_case("ragged")
+    P, N, n = c["P"], c["N"], c["nx"] * c["ny"]
+    sm = mace.mace_build_sysmatrix(c["nx"], c["ny"], c["V"], c["D"], N, view_agent=c["va"], sv_size=sv)
+    rng = np.random.default_rng(4)
+    xs = c["xs"]
+    X0 = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
+    v = (xs[None, :] + 0.3 * np.abs(xs).mean() * rng.standard_normal((N, n))).astype(np.float32)
+    prm = mace.make_params(prior=c["prior"], sigma_x=c["sx"], sigma=0.5, sigma_mode=1, concurrency=1,
+                           schedule=schedule)
+    st = mace.mace_init(sm, c["y"], c["lam"], prm)
+    st.set_state(X0.copy(), X0)
+    st.prox_pass(v)
+    _, Xg = st.get_state()
+    sigma = st.stats()["sigma_abs"]
+    order = st.visit_order()
+    st.close()
+    sm.close()
+    for g in range(N):
+        x = X0[g].astype(np.float64)
+        e = P.error_sinogram(g, x)
+        P.icd_sweep(g, x, e, v=v[g].astype(np.float64), sigma=sigma, order=order)
+        assert nrmse(Xg.reshape(N, n)[g], x) < 2e-5, g

@@ -82,6 +82,15 @@ def test_full_size_512_parity(gpu_lib):
     err = nrmse(x[0], dref["x"].reshape(512, 512))
     print("512^2: NRMSE vs oracle %.2e (oracle KKT %.1e, %d iterations)" % (err, float(dref["kkt"]), int(dref["iters"])))
     assert err < 1e-4
+    # the second scan, against its own stored oracle image (same shared prior)
+    ref1 = os.path.join(GOLDEN, "cfg2_scan1_reference.npz")
+    if os.path.exists(ref1):
+        d1 = np.load(ref1)
+        assert str(d1["digest"]) == _digest(y[1], lam[1]), "stored oracle image is of other inputs"
+        assert abs(float(d1["sigma_x"]) - sx) <= 1e-6 * sx
+        err1 = nrmse(x[1], d1["x"].reshape(512, 512))
+        print("512^2 scan 1: NRMSE vs oracle %.2e (oracle KKT %.1e)" % (err1, float(d1["kkt"])))
+        assert err1 < 1e-4
 
 
 @pytest.mark.parametrize("batch,chains", [(3, 0), (4, 4), (4, 2)])
