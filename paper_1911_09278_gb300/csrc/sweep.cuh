@@ -1029,6 +1029,15 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_queue_kernel(QueueArgs
         const uint32_t *src = (const uint32_t *)(Q.table + r);
         for (int k = lane; k < (int)(sizeof(SweepArgs) / 4); k += 32) ((uint32_t *)args)[k] = src[k];
         __syncwarp();
+        // the band back to zero: entries an item does not load are read with
+        // matrix value 0, and a value left by another request's item (which
+        // may have diverged) must not turn 0 x e into a NaN
+        {
+            float2 *band = (float2 *)(base + Ly.band);
+            const int nband = Q.wmax * band_width(Q.vpad, W) * K;
+            for (int f = lane; f <= nband; f += 32) band[f] = make_float2(0.f, 0.f);
+            __syncwarp();   // before any lane's loads into the band
+        }
         const SweepArgs &A = *args;
         const int local = (int)item - Q.offsets[r];
         const int Cw = A.nwarps;                 // rows of a pair in flight (the request's concurrency)
