@@ -126,3 +126,46 @@ def test_group_rejects_fixed_schedule_and_duplicates(members):
         assert ei.value.code == mace.MACE_EINVAL
     a.close()
     b.close()
+
+
+def test_group_diverging_member_is_isolated(members):
+    """A member whose iteration diverges (normalised sigma 3 with one
+    forward pass: outside Theorem 2's range) fills its error sinogram with
+    non-finite values while it shares launches with a well-posed member; it
+    is reported (MACE_ENUMERIC), dropped from the group, and the other
+    member still converges to its oracle MAP image."""
+    import torch
+    mace, cs, sms = members
+    c = cs[0]
+    bad = mace.mace_init(sms[0], c["y"], c["lam"], _params(mace, c, sigma=10.0, sweeps_per_iter=1, symmetric=False,
+                                                             concurrency=-1), batch=c["B"])
+    good = mace.mace_init(sms[0], c["y"], c["lam"], _params(mace, c), batch=c["B"])
+    grp = mace.mace_group_create([bad, good], stream=torch.cuda.Stream())
+    failed_at = None
+    for chunk in range(100):
+        grp.launch(10)
+        try:
+            bad.poll()
+        except mace.MaceError as e:
+            assert e.code == mace.MACE_ENUMERIC
+            failed_at = 10 * (chunk + 1)
+            break
+    assert failed_at is not None
+    grp.update([good])
+    bad.close()
+    conv = False
+    for _ in range(600):
+        grp.launch(10)
+        r, conv = good.poll()
+        if conv:
+            break
+    grp.close()
+    assert conv
+    x = np.asarray(good.consensus(), np.float64).ravel()
+    good.close()
+    P = oracle.Problem(c["nx"], c["ny"], c["V"], c["D"], c["y"][0], c["lam"][0], n_agents=c["N"],
+                       view_agent=c["va"], prior="qggmrf", sigma_x=c["sx"])
+    xs, _, _ = P.central_icd(max_sweeps=40000, tol=1e-13)
+    err = nrmse(x, xs)
+    print("diverged member reported after %d iterations; the other: NRMSE vs oracle %.2e" % (failed_at, err))
+    assert np.all(np.isfinite(x)) and err < 1e-4
