@@ -129,7 +129,7 @@ def test_group_rejects_fixed_schedule_and_duplicates(members):
 
 
 def test_group_diverging_member_is_isolated(members):
-    """A member whose iteration diverges (normalised sigma 3 with one
+    """A member whose iteration diverges (normalised sigma 10 with one
     forward pass: outside Theorem 2's range) fills its error sinogram with
     non-finite values while it shares launches with a well-posed member; it
     is reported (MACE_ENUMERIC), dropped from the group, and the other
