@@ -587,8 +587,9 @@ def run_volume(args):
     (16-40 views each, spread over the half circle), 26-neighbourhood
     Q-GGMRF coupling the slices.  Schedule 1 (default): a persistent grid fed
     from a work queue of (slice, agent, row of super-voxels) items, even
-    slices first, then odd ones; schedule 0: one fixed warp per (slice,
-    agent) pair.  Times args.steps Mann iterations (value = Mann iterations
+    slices first, then odd ones, two slices of one parity per warp with
+    --chains 2 (the default); schedule 0: fixed warps per (slice pair,
+    agent).  Times args.steps Mann iterations (value = Mann iterations
     per second of the whole volume); with --volume-tol > 0 it then runs on
     to that residual (at most args.max_iter iterations) and reports the
     iterations and the time to get there."""
@@ -611,7 +612,7 @@ def run_volume(args):
     prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.volume_sigma, sigma_mode=1, rho=args.rho,
                            sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
                            tol=args.volume_tol, concurrency=args.concurrency, neighbourhood=26,
-                           schedule=args.volume_schedule)
+                           schedule=args.volume_schedule, chains=args.chains)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, stream=stream, batch=nz)
     st.iterate(args.warmup)
     st.set_timing(True, max_launches=4 * args.steps + 8)
@@ -634,6 +635,7 @@ def run_volume(args):
         "sweep_ms": ms / max(1, nl), "voxel_updates_per_s": nz * n * n * N / (ms / max(1, nl) / 1000.0),
         "residual_after_timed": r_now,
         "schedule": stats["schedule"], "concurrency_per_agent": stats["concurrency"], "warps": stats["warps"],
+        "chains": stats["chains"],
         "config": {"workload": "3D %dx%dx%d, 960 views, 725 channels, 32 agents with 16-40 views, "
                                "26-neighbour Q-GGMRF" % (n, n, nz),
                    "matrix_gb": info["bytes_columns"] / 1e9, "sv_size": args.volume_sv,

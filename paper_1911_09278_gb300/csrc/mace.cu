@@ -592,6 +592,7 @@ static __device__ __align__(256) float g_noalloc_images[kNoAllocFloats];
 struct QueueLaunch {
     sweep_queue_fn fn = nullptr;
     int W = 1;                           // warps per super-voxel (a team)
+    int K = 1;                           // chains per warp (two slices of a volume)
     int vpad = 0, wmax = 0, col_stride = 16, S = 4;
     int wpb = 1, blocks = 0;
     size_t smem = 0;
@@ -1237,12 +1238,12 @@ static int launch_sweep(mace_state *st, int backward, const float *vexp)
 }
 
 // --- work-queue launches ------------------------------------------------------
-static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26, int W)
+static sweep_queue_fn queue_kernel_ptr(mace_dtype dt, int max_views, bool nb26, int W, int K)
 {
     switch (dt) {
-    case MACE_F32: return mace_sweep_queue_kernel_f32(max_views, nb26, W);
-    case MACE_BF16: return mace_sweep_queue_kernel_bf16(max_views, nb26, W);
-    default: return mace_sweep_queue_kernel_f16(max_views, nb26, W);
+    case MACE_F32: return mace_sweep_queue_kernel_f32(max_views, nb26, W, K);
+    case MACE_BF16: return mace_sweep_queue_kernel_bf16(max_views, nb26, W, K);
+    default: return mace_sweep_queue_kernel_f16(max_views, nb26, W, K);
     }
 }
 
@@ -1256,9 +1257,10 @@ static int resolve_wpv(const mace_params &P)
     return P.warps_per_voxel > 0 ? P.warps_per_voxel : 1;
 }
 
-static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L)
+static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, int W, QueueLaunch *L, int K = 1)
 {
     L->W = W;
+    L->K = K;
     int max_views = 1;
     for (int k = 0; k < n; ++k) {
         const mace_sysmatrix *M = Ms[k];
@@ -1274,18 +1276,18 @@ static int queue_configure(const mace_sysmatrix *const *Ms, int n, bool nb26, in
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t per_warp = warp_smem_layout(L->vpad, L->wmax, L->col_stride, L->S, 1, nb26, W).total +
+    const size_t per_warp = warp_smem_layout(L->vpad, L->wmax, L->col_stride, L->S, K, nb26, W).total +
                             ((sizeof(SweepArgs) + 15) & ~(size_t)15);
     if (per_warp > (size_t)max_smem)
         return fail(MACE_EINVAL, "super-voxel working set does not fit in shared memory; use a smaller sv_size");
     // the kernel with enough rounds of views per lane for every matrix; the
     // generic one (decoding each column as it is used) when a column's
     // three-channel list is longer than that kernel's rounds hold
-    const int R = sweep_rounds(max_views, 1);
+    const int R = sweep_rounds(max_views, K);
     if (R <= 4)
         for (int k = 0; k < n; ++k)
-            if (Ms[k]->max_n3 > sweep_ovf_rounds(R, 1) * 32) max_views = 5 * 32 + 1;
-    L->fn = queue_kernel_ptr(Ms[0]->dtype, max_views, nb26, W);
+            if (Ms[k]->max_n3 > sweep_ovf_rounds(R, K) * (32 / K)) max_views = 5 * 32 + 1;
+    L->fn = queue_kernel_ptr(Ms[0]->dtype, max_views, nb26, W, K);
     if (!L->fn) return fail(MACE_EINVAL, "no queue-fed sweep kernel for this matrix and warps per voxel");
     CUDA_TRY(cudaFuncSetAttribute(L->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     // blocks of whole teams (at most 8 warps: team barriers 1..8)
@@ -1327,7 +1329,7 @@ static int queue_run(const QueueLaunch &L, const SweepArgs *d_table, const int *
 // items of one state for z parity p (volumes) or all groups (p < 0)
 static int queue_items(const mace_state *st, int p)
 {
-    const int groups = p < 0 ? st->B : (st->B - p + 1) / 2;
+    const int groups = (p < 0 ? st->B : (st->B - p + 1) / 2) / st->chains;
     return groups * st->M->N * st->concurrency;
 }
 
@@ -1374,11 +1376,19 @@ static int configure_queue(mace_state *st)
     C = std::max<int64_t>(1, std::min<int64_t>(C, M->nsv));
     st->concurrency = (int)C;
     st->wpv = resolve_wpv(st->P);
-    int rc = queue_configure(Ms, 1, st->P.neighbourhood == 26, st->wpv, &st->q);
+    // volumes: two slices of one z parity per warp when asked and every
+    // parity class pairs up (a multiple of 4 slices)
+    const bool nb26 = st->P.neighbourhood == 26;
+    int K = (nb26 && st->P.chains >= 2 && st->B % 4 == 0) ? 2 : 1;
+    int rc = queue_configure(Ms, 1, nb26, st->wpv, &st->q, K);
+    if (rc && K == 2) {
+        K = 1;
+        rc = queue_configure(Ms, 1, nb26, st->wpv, &st->q, K);
+    }
     if (rc) return rc;
-    st->chains = 1;
+    st->chains = K;
     st->sweep_warps = (int)std::min<int64_t>((int64_t)st->q.blocks * st->q.wpb,
-                                             (int64_t)st->B * M->N * C * st->wpv);
+                                             (int64_t)(st->B / K) * M->N * C * st->wpv);
     st->sweep_wpb = st->q.wpb;
     st->sweep_smem = st->q.smem;
     return MACE_OK;
@@ -1413,10 +1423,10 @@ static int configure_fixed(mace_state *st)
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int col_stride = (M->max_col_bytes + 15) & ~15;
-    // chains per warp: reconstructions of the batch that share each column
-    // load (two when asked and the batch is even; volumes run one)
+    // chains per warp: reconstructions of the batch (slices of a volume)
+    // that share each column load (two when asked and the batch is even)
     const bool nb26 = st->P.neighbourhood == 26;
-    int K = (st->P.chains >= 2 && st->B % 2 == 0 && !nb26) ? 2 : 1;
+    int K = (st->P.chains >= 2 && st->B % 2 == 0) ? 2 : 1;
     sweep_fn fn = nullptr;
     for (;;) {
         st->warp_smem = warp_smem_layout(M->vpad, M->wmax, col_stride, M->S, K, nb26).total;
@@ -1789,8 +1799,8 @@ extern "C" int mace_state_bytes(const mace_sysmatrix *M, int32_t batch, const ma
     const int64_t m = B * (int64_t)M->V * M->geo.D, NN = B * M->N * n;
     const int64_t per = (int64_t)M->N * n;
     const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(std::max(1, nsm * 4 / batch), (per + 255) / 256));
-    const int K = (params->chains >= 2 && batch % 2 == 0 && params->neighbourhood != 26 && params->schedule == 0)
-                      ? 2 : 1;
+    const int K = params->schedule == 0 ? ((params->chains >= 2 && batch % 2 == 0) ? 2 : 1)
+                                        : ((params->neighbourhood == 26 && params->chains >= 2 && batch % 4 == 0) ? 2 : 1);
     int64_t p = m * (8 + 8 + 4)                 // (e, Lambda), changes of e, y
                 + NN * 4 * 3                    // w, X, theta2
                 + B * n * 8 + B * 3 * 8 + 4     // consensus, residuals, status

@@ -84,7 +84,7 @@ typedef void (*sweep_fn)(SweepArgs);
 //   pl:     2 * S^2 * 4                 per visited pixel: tile index | neighbour mask << 11
 //                                       | pixel offset in the super-voxel << 20
 //   cl:     2 * S^2 * 8                 per visited pixel: (column offset in 16-byte units, bytes)
-//   halo:   2 * (S+2)^2 * 4             X tiles of the slices below and above (volumes only)
+//   halo:   2 K (S+2)^2 * 4             per chain, X tiles of the slices below and above (volumes only)
 //   band:   (wmax bw K + 1) * 8         (e, Lambda), chains interleaved; the last entry is a
 //                                       sink that idle lanes read and write with value 0
 //   snap:   K wmax bw * 4               e of the band when the super-voxel began
@@ -117,7 +117,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int vpad, int wmax, int col
     L.coff = o;  o += r16((S2 + 1) * 4);
     L.pl = o;    o += r16(2 * S2 * 4);
     L.cl = o;    o += r16(2 * S2 * 8);
-    L.halo = o;  o += halo ? r16(2 * TA * 4) : 0;
+    L.halo = o;  o += halo ? r16((size_t)2 * K * TA * 4) : 0;
     L.band = o;  o += r16(((size_t)wmax * bw * K + 1) * 8);
     L.snap = o;  o += r16((size_t)K * wmax * bw * 4);
     L.xt = o;    o += r16((size_t)K * TA * 4);
@@ -243,13 +243,15 @@ __device__ __forceinline__ void sweep_warp_init(uint8_t *base, const WarpSmem &L
     __syncwarp();
 }
 
+// grp: the warp's (group, agent) pair is grp N + g; chain k updates
+// reconstruction (slice) rbase + k rstride (rstride 2: two slices of one
+// z parity).
 template <typename T, int K, int R, int RO, bool NB26, bool DET, int W, class ARGS>
 __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem &Ly, const int grp, const int g,
                                            const int cidx, const int Cw, uint32_t &dec, uint32_t &issued,
-                                           const TeamCtx &tm)
+                                           const TeamCtx &tm, const int rbase, const int rstride)
 {
     static_assert(K == 1 || K == 2, "one or two chains per warp");
-    static_assert(!NB26 || K == 1, "volumes run one chain per warp");
     static_assert(W == 1 || (W == 2 || W == 4) && K == 1 && R == 0 && !DET && !NB26,
                   "teams of 2 or 4 warps run the 2D decode-at-use sweep, one chain, free mode");
     static_assert((kRing & (kRing - 1)) == 0 && kRing >= 3, "ring size is a power of two >= 4");
@@ -268,8 +270,7 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     uint32_t *scoff = (uint32_t *)(base + Ly.coff);
     uint32_t *pl2 = (uint32_t *)(base + Ly.pl);
     uint2 *cl2 = (uint2 *)(base + Ly.cl);
-    float *halo_lo = (float *)(base + Ly.halo);
-    float *halo_hi = halo_lo + TA;
+    float *const halo0 = (float *)(base + Ly.halo);   // chain k: below at 2k TA, above at (2k + 1) TA
     float2 *band = (float2 *)(base + Ly.band);
     float *snap = (float *)(base + Ly.snap);
     float *xt0 = (float *)(base + Ly.xt);
@@ -309,38 +310,64 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
     const int lP = TS <= 8 ? 3 : TS <= 16 ? 4 : 5;
     const int tr0 = lane >> lP, tc0 = lane & ((1 << lP) - 1), trs = 32 >> lP;
 
-    // this lane's prior neighbour: lanes 0..7 of each chain the in-plane
-    // 8-neighbourhood, or (volumes) lanes 0..25 the 26-neighbourhood; other
-    // lanes read the pixel itself with weight 0.  mbit: the neighbour's bit in
-    // a pixel's 3x3 in-image mask.
-    int pdz = 0, pdi = 0, pdj = 0;
-    float pb = 0.f;
-    if (NB26) {
-        if (lane < 26) {
-            const int kk = lane < 13 ? lane : lane + 1;   // skip the centre of the 3x3x3
-            pdz = kk / 9 - 1;
-            pdi = (kk / 3) % 3 - 1;
-            pdj = kk % 3 - 1;
-            const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
-            const int zz = grp + pdz;
-            pb = (zz >= 0 && zz < A.B) ? A.pscale * A.b26[d2 - 1] : 0.f;
-        }
-    } else if (hl < 8) {
-        const int kk = hl < 4 ? hl : hl + 1;
-        pdi = kk / 3 - 1;
-        pdj = kk % 3 - 1;
-        pb = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
-    }
-    const int mbit = (pdi + 1) * 3 + (pdj + 1);
-    const int noff = pdi * TS + pdj;
+    // chain k: reconstruction (slice) rbase + k rstride
+    auto rb_of = [&](int k) { return (int64_t)(rbase + k * rstride); };
+    // this lane's prior neighbours: lanes 0..7 of each chain the in-plane
+    // 8-neighbourhood; volumes: the 26-neighbourhood, lane l neighbour l with
+    // one chain, lane l of a chain's 16 neighbours l and l + 16 with two
+    // (NBL per lane); other lanes read the pixel itself with weight 0.
+    // mbit: the neighbour's bit in a pixel's 3x3 in-image mask.
+    constexpr int NBL = (NB26 && K == 2) ? 2 : 1;
     float *xth = xt0 + h * TA;                   // this lane's chain's X tile
     const float2 *vt2h = vt20 + h * S2;
-    const float *nb_tile = (pdz == 0 ? xth : (pdz < 0 ? halo_lo : halo_hi)) + noff;
-    const uint32_t xth_s = smem_u32(xth), nbt_s = smem_u32(nb_tile), vt2h_s = smem_u32(vt2h);
+    int mbit[NBL];
+    float pb[NBL];
+    const float *nb_tile[NBL];
+    uint32_t nbt_s[NBL];
+#pragma unroll
+    for (int t = 0; t < NBL; ++t) {
+        int pdz = 0, pdi = 0, pdj = 0;
+        pb[t] = 0.f;
+        if (NB26) {
+            const int l = K == 2 ? hl + 16 * t : lane;
+            if (l < 26) {
+                const int kk = l < 13 ? l : l + 1;   // skip the centre of the 3x3x3
+                pdz = kk / 9 - 1;
+                pdi = (kk / 3) % 3 - 1;
+                pdj = kk % 3 - 1;
+                const int d2 = pdz * pdz + pdi * pdi + pdj * pdj;
+                const int64_t zz = rb_of(h) + pdz;
+                pb[t] = (zz >= 0 && zz < A.B) ? A.pscale * A.b26[d2 - 1] : 0.f;
+            }
+        } else if (hl < 8) {
+            const int kk = hl < 4 ? hl : hl + 1;
+            pdi = kk / 3 - 1;
+            pdj = kk % 3 - 1;
+            pb[t] = A.pscale * ((pdi != 0 && pdj != 0) ? A.b_diag : A.b_edge);
+        }
+        mbit[t] = (pdi + 1) * 3 + (pdj + 1);
+        const float *tile = pdz == 0 ? xth : halo0 + (2 * h + (pdz < 0 ? 0 : 1)) * TA;
+        nb_tile[t] = tile + pdi * TS + pdj;
+        nbt_s[t] = smem_u32(nb_tile[t]);
+    }
+    const uint32_t xth_s = smem_u32(xth), vt2h_s = smem_u32(vt2h);
     const uint32_t ring_s = smem_u32(ring);
-
-    // chain k: reconstruction grp*K + k
-    auto rb_of = [&](int k) { return (int64_t)(grp * K + k); };
+    // the prior's curvature and gradient at the pixel of tile index tc and
+    // value xs, this lane's share (summed over the chain's lanes below); the
+    // neighbours' values by tile pointer (nbv(t)) or shared address
+    auto prior_terms = [&](uint32_t pq, float xs, auto nbv, float &pr2, float &pr1) {
+        const float d0 = xs - nbv(0);
+        const float w0 = (((pq >> (11 + mbit[0])) & 1u) ? pb[0] : 0.f) * prior_weight(A, d0);
+        pr2 = w0;
+        pr1 = w0 * d0;
+#pragma unroll
+        for (int t = 1; t < NBL; ++t) {
+            const float d = xs - nbv(t);
+            const float wgt = (((pq >> (11 + mbit[t])) & 1u) ? pb[t] : 0.f) * prior_weight(A, d);
+            pr2 += wgt;
+            pr1 = fmaf(wgt, d, pr1);
+        }
+    };
     float2 *const eLh = A.eL + rb_of(h) * A.ne + (int64_t)v0 * A.D;   // this lane's chain, agent g
     unsigned long long *const dacch = DET ? A.dacc + rb_of(h) * A.ne + (int64_t)v0 * A.D : nullptr;
     unsigned *const phase_c = DET ? A.phase + pair : nullptr;
@@ -590,10 +617,10 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             }
         }
         if (NB26) {
-            // X tiles of the neighbouring slices
-            for (int hh = 0; hh < 2; ++hh) {
-                const int zz = grp + (hh ? 1 : -1);
-                float *ht = hh ? halo_hi : halo_lo;
+            // X tiles of each chain's neighbouring slices
+            for (int hh = 0; hh < 2 * K; ++hh) {
+                const int64_t zz = rb_of(hh >> 1) + ((hh & 1) ? 1 : -1);
+                float *ht = halo0 + hh * TA;
                 const float *Xz = (zz >= 0 && zz < A.B) ? A.X + ((int64_t)zz * A.N + g) * n : nullptr;
                 for (int ti = tr0; ti < TS; ti += trs)
                     for (int tj = tc0; tj < TS; tj += 32) {
@@ -699,21 +726,19 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             }
 #pragma unroll
             for (int o = 0; o < RRO; ++o) g2[o] = lds_f2(c.oaddr[o]);
-            // prior through the surrogate weights (lane l of a chain:
-            // neighbour l), from the X tiles only.  No branch: out-of-image
+            // prior through the surrogate weights (a lane's neighbours, see
+            // above), from the X tiles only.  No branch: out-of-image
             // neighbours and idle lanes get weight 0.
             const uint32_t pq = pl[q];
             const int tc = (int)(pq & 0x7FFu);
             const float2 vq = vt2h[q];
             const float xs = xth[tc];
-            const float d = xs - nb_tile[tc];
-            const float pbv = ((pq >> (11 + mbit)) & 1u) ? pb : 0.f;
-            float pr2 = pbv * prior_weight(A, d);
-            const float pr1 = pr2 * d;
+            float pr2, pr1;
+            prior_terms(pq, xs, [&](int t) { return nb_tile[t][tc]; }, pr2, pr1);
             const float prox = fmaf(xs, A.inv_s2, -vq.x);   // (x - v) / sigma^2
             if (NB26) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+                for (int o = 1; o < LPC; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
             } else {
 #pragma unroll
                 for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
@@ -798,14 +823,12 @@ __device__ __forceinline__ bool sweep_work(ARGS A, uint8_t *base, const WarpSmem
             const uint32_t tc4 = (pq & 0x7FFu) * 4u;
             const float2 vq = lds_f2(vt2h_s + 8u * q);
             const float xs = lds_f32(xth_s + tc4);
-            const float d = xs - lds_f32(nbt_s + tc4);
-            const float pbv = ((pq >> (11 + mbit)) & 1u) ? pb : 0.f;
-            float pr2 = pbv * prior_weight(A, d);
-            const float pr1 = pr2 * d;
+            float pr2, pr1;
+            prior_terms(pq, xs, [&](int t) { return lds_f32(nbt_s[t] + tc4); }, pr2, pr1);
             const float prox = fmaf(xs, A.inv_s2, -vq.x);
             if (NB26) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
+                for (int o = 1; o < LPC; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
             } else {
 #pragma unroll
                 for (int o = 1; o < 8; o <<= 1) pr2 += __shfl_xor_sync(FULL, pr2, o);
@@ -973,7 +996,7 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_kernel(SweepArgs A)
     uint32_t dec = 0, issued = 0;
     const TeamCtx solo = {0, 0, 0u, 0u};
     sweep_work<T, K, R, RO, NB26, DET, 1, SweepArgs>(A, base, Ly, pair / A.N, pair % A.N, gw / (G * A.N),
-                                                     A.nwarps / (G * A.N), dec, issued, solo);
+                                                     A.nwarps / (G * A.N), dec, issued, solo, (pair / A.N) * K, 1);
 }
 
 // Work queue over (request, group, agent, row of super-voxels): every resident
@@ -1042,11 +1065,13 @@ __global__ void __maxnreg__(MACE_SWEEP_MAXNREG) icd_sweep_queue_kernel(QueueArgs
         const int local = (int)item - Q.offsets[r];
         const int Cw = A.nwarps;                 // rows of a pair in flight (the request's concurrency)
         const int pl = local / Cw, cidx = local - pl * Cw;
-        int grp = pl / A.N;
+        const int grp = pl / A.N;
         const int g = pl - grp * A.N;
-        if (Q.zpar >= 0) grp = 2 * grp + Q.zpar;
+        // zpar >= 0: group grp holds the K slices zpar + 2 (K grp + k)
+        const int rbase = Q.zpar >= 0 ? Q.zpar + 2 * K * grp : K * grp;
+        const int rstride = Q.zpar >= 0 ? 2 : 1;
         if (!sweep_work<T, K, R, RO, NB26, false, W, const SweepArgs &>(A, base, Ly, grp, g, cidx, Cw, dec, issued,
-                                                                          tm))
+                                                                          tm, rbase, rstride))
             return;
         __syncwarp();
     }
@@ -1078,8 +1103,9 @@ static sweep_fn sweep_lookup(int max_views, int K, bool nb26, bool det)
 {
     const int R = sweep_rounds(max_views, K);
     if (nb26) {
-        if (K != 1) return nullptr;
-        return det ? sweep_lookup_k<T, 1, true, true>(R) : sweep_lookup_k<T, 1, true, false>(R);
+        if (K == 1) return det ? sweep_lookup_k<T, 1, true, true>(R) : sweep_lookup_k<T, 1, true, false>(R);
+        if (K == 2) return det ? sweep_lookup_k<T, 2, true, true>(R) : sweep_lookup_k<T, 2, true, false>(R);
+        return nullptr;
     }
     if (K == 1) return det ? sweep_lookup_k<T, 1, false, true>(R) : sweep_lookup_k<T, 1, false, false>(R);
     if (K == 2) return det ? sweep_lookup_k<T, 2, false, true>(R) : sweep_lookup_k<T, 2, false, false>(R);
@@ -1088,34 +1114,36 @@ static sweep_fn sweep_lookup(int max_views, int K, bool nb26, bool det)
 
 typedef void (*sweep_queue_fn)(QueueArgs);
 
-template <typename T, bool NB26>
+template <typename T, int K, bool NB26>
 static sweep_queue_fn sweep_queue_lookup_r(int R)
 {
     switch (R) {
-    case 1: return icd_sweep_queue_kernel<T, 1, 1, 1, NB26, 1>;
-    case 2: return icd_sweep_queue_kernel<T, 1, 2, 1, NB26, 1>;
-    case 3: return icd_sweep_queue_kernel<T, 1, 3, 2, NB26, 1>;
-    case 4: return icd_sweep_queue_kernel<T, 1, 4, 2, NB26, 1>;
-    default: return icd_sweep_queue_kernel<T, 1, 0, 1, NB26, 1>;
+    case 1: return icd_sweep_queue_kernel<T, K, 1, (K == 2 ? 2 : 1), NB26, 1>;
+    case 2: return icd_sweep_queue_kernel<T, K, 2, (K == 2 ? 2 : 1), NB26, 1>;
+    case 3: return icd_sweep_queue_kernel<T, K, 3, 2, NB26, 1>;
+    case 4: return icd_sweep_queue_kernel<T, K, 4, 2, NB26, 1>;
+    default: return icd_sweep_queue_kernel<T, K, 0, 1, NB26, 1>;
     }
 }
 
-// The queue-fed sweep (one chain per warp) for agents of at most max_views
-// views and the 8- or 26-neighbourhood; W = 2 or 4: teams of W warps per
-// super-voxel (2D, decoding each column as it is used).
+// The queue-fed sweep for agents of at most max_views views and the 8- or
+// 26-neighbourhood: one chain per warp, or (volumes) two slices of one z
+// parity per warp; W = 2 or 4: teams of W warps per super-voxel (2D, one
+// chain, decoding each column as it is used).
 template <typename T>
-static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26, int W)
+static sweep_queue_fn sweep_queue_lookup(int max_views, bool nb26, int W, int K)
 {
+    if (K == 2) return (nb26 && W == 1) ? sweep_queue_lookup_r<T, 2, true>(sweep_rounds(max_views, 2)) : nullptr;
     if (W == 2 && !nb26) return icd_sweep_queue_kernel<T, 1, 0, 1, false, 2>;
     if (W == 4 && !nb26) return icd_sweep_queue_kernel<T, 1, 0, 1, false, 4>;
     if (W != 1) return nullptr;
     const int R = sweep_rounds(max_views, 1);
-    return nb26 ? sweep_queue_lookup_r<T, true>(R) : sweep_queue_lookup_r<T, false>(R);
+    return nb26 ? sweep_queue_lookup_r<T, 1, true>(R) : sweep_queue_lookup_r<T, 1, false>(R);
 }
 
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f32(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_bf16(int max_views, int K, bool nb26, bool det);
 __attribute__((visibility("hidden"))) sweep_fn mace_sweep_kernel_f16(int max_views, int K, bool nb26, bool det);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f32(int max_views, bool nb26, int W);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_bf16(int max_views, bool nb26, int W);
-__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f16(int max_views, bool nb26, int W);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f32(int max_views, bool nb26, int W, int K);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_bf16(int max_views, bool nb26, int W, int K);
+__attribute__((visibility("hidden"))) sweep_queue_fn mace_sweep_queue_kernel_f16(int max_views, bool nb26, int W, int K);

@@ -119,20 +119,22 @@ def _volume(nz):
     return n, V, D, N, va, sx, c, P
 
 
-def test_queue_volume_one_pass_is_zparity_algorithm2(gpu_lib):
-    """A volume of 5 slices at concurrency 1: the even slices are swept side
-    by side, then the odd ones, each reading neighbour slices that no warp
-    is updating, so the pass equals Algorithm 2 over the whole volume in the
+@pytest.mark.parametrize("nz,chains", [(5, 1), (8, 2)])
+def test_queue_volume_one_pass_is_zparity_algorithm2(gpu_lib, nz, chains):
+    """A volume at concurrency 1: the even slices are swept side by side,
+    then the odd ones, each reading neighbour slices that no warp is
+    updating, so the pass equals Algorithm 2 over the whole volume in the
     order (even slices, then odd slices, each in the library's in-slice
-    order)."""
+    order).  With two chains a warp sweeps two slices of one parity (z and
+    z + 2) over each column load."""
     mace = gpu_lib
-    nz = 5
     n, V, D, N, va, sx, c, P = _volume(nz)
     npx = n * n
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=8)
     prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=0.5, sigma_mode=1, concurrency=1, neighbourhood=26,
-                           schedule=1)
+                           schedule=1, chains=chains)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, batch=nz)
+    assert st.stats()["chains"] == chains
     rng = np.random.default_rng(9)
     xs = _map(P)
     sc = 0.3 * np.abs(xs).mean()
@@ -156,18 +158,18 @@ def test_queue_volume_one_pass_is_zparity_algorithm2(gpu_lib):
         assert nrmse(Xg[:, g, :].ravel(), x) < 2e-5, g
 
 
-@pytest.mark.parametrize("concurrency", [1, -1])
-def test_queue_volume_matches_3d_map(gpu_lib, concurrency):
+@pytest.mark.parametrize("concurrency,nz,chains", [(1, 6, 1), (-1, 6, 1), (-1, 8, 2)])
+def test_queue_volume_matches_3d_map(gpu_lib, concurrency, nz, chains):
     mace = gpu_lib
-    nz = 6
     n, V, D, N, va, sx, c, P = _volume(nz)
     xs = _map(P)
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=8)
     prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=0.5 if concurrency == 1 else 0.2, sigma_mode=1,
                            rho=0.8, sweeps_per_iter=2, symmetric=True, recompute_every=10,
                            tol=1e-7, max_iter=8000,
-                           concurrency=concurrency, neighbourhood=26, schedule=1)
+                           concurrency=concurrency, neighbourhood=26, schedule=1, chains=chains)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, batch=nz)
+    assert st.stats()["chains"] == chains
     x, iters, res, conv = st.reconstruct()
     st.close()
     sm.close()
