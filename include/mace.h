@@ -86,9 +86,10 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   over the neighbourhood, normalised to sum 1.  neighbourhood 8: in-plane;
  *   neighbourhood 26: the batch of mace_init is the z-stack of ONE volume
  *   (batch element b is slice z = b, all slices share the 2D matrix) and the
- *   prior couples neighbouring slices; slices are then updated one per warp,
- *   each reading its neighbour slices as they were when its super-voxel
- *   began.
+ *   prior couples neighbouring slices; with schedule 0 all slices are
+ *   updated at once, each reading its neighbour slices as they were when its
+ *   super-voxel began; with schedule 1 even slices are swept first, then odd
+ *   ones (see schedule).
  *   sigma: the proximal parameter of Eq. "prox_F"; sigma_mode 0 takes it in
  *   image units, 1 scales it by 1/sqrt(mean_{i,s} sum_{k in J_i} A^2 Lambda).
  *   rho in (0, 1): Mann parameter (Eq. "Mann").
@@ -108,10 +109,12 @@ typedef enum { MACE_F32 = 0, MACE_BF16 = 1, MACE_F16 = 2 } mace_dtype;
  *   bands that run side by side (plain raster when concurrency is 1);
  *   1 a stride permutation spreading consecutive super-voxels apart.
  *   Pixels inside a super-voxel are visited in raster order.
- *   chains: reconstructions of a batch one warp updates together, sharing
- *   every column load (0 or 1: one; 2 or 4: two when the batch is even, the
- *   warp then working as two 16-lane halves, one per reconstruction).
- *   Results do not depend on it.
+ *   chains: reconstructions of a batch (slices of a volume) one warp updates
+ *   together, sharing every column load (0 or 1: one; 2 or 4: two, the warp
+ *   then working as two 16-lane halves, one per reconstruction; schedule 0:
+ *   when the batch is even, slices 2k and 2k + 1; schedule 1: volumes only,
+ *   when the slice count is a multiple of 4, two slices of one z parity,
+ *   z and z + 2).  Results do not depend on it.
  *   pnp: 0 = Algorithm 1 (the prior inside every agent, weight beta/N);
  *   1 = Algorithm 3 (Sec. III, MACE with a plug-and-play prior): the agents
  *   hold the data terms only and use proximal parameter sqrt(N) sigma; the
