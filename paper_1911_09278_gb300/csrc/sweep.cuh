@@ -203,10 +203,6 @@ struct ColRaw {
 #define MACE_SWEEP_MAXNREG 128
 #endif
 
-// R: rounds of views per lane (R * 32/K >= the agent's views); RO: rounds of
-// the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
-// z-stack of one volume, 26-neighbourhood prior (K = 1).  DET: deterministic
-// mode (lock-step phases, fixed-point changes of e).
 // A team of W warps of one block sweeping the same super-voxels, the
 // agent's views split between them (warp wi owns views 32 (wi + W j) + lane):
 // each warp keeps its own views' band, the partial sums of a pixel's theta1
@@ -243,6 +239,11 @@ __device__ __forceinline__ void sweep_warp_init(uint8_t *base, const WarpSmem &L
     __syncwarp();
 }
 
+// R: rounds of views per lane (R * 32/K >= the agent's views); RO: rounds of
+// the three-channel list (RO * 32/K >= its longest).  NB26: the batch is the
+// z-stack of one volume, 26-neighbourhood prior (with K = 2 each lane of a
+// chain takes two of the 26 neighbours).  DET: deterministic mode (lock-step
+// phases, fixed-point changes of e).  W: warps per super-voxel (a team).
 // grp: the warp's (group, agent) pair is grp N + g; chain k updates
 // reconstruction (slice) rbase + k rstride (rstride 2: two slices of one
 // z parity).
