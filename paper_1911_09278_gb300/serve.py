@@ -21,7 +21,7 @@ Membership follows admission and retirement (mace_group_update, stream
 ordered); one chunk stays queued behind the one whose status is read.  Every
 member advances one pass per launch and a pass lasts as long as its longest
 item, so on mixes dominated by large requests the per-request mode (the
-default) serves faster; measured on this GPU it does on small requests too.
+default) serves faster; measured on a GB300 it does on small requests too.
 
 Admission is by device-memory footprint: the request's state (the library's
 own count, mace_state_bytes, once its geometry's matrix is resident) plus,
