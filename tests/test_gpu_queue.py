@@ -301,8 +301,9 @@ def test_queue_volume_64x64x8_matches_3d_map(gpu_lib):
                        neighbourhood=26, sigma_x=sx)
     xs = _map(P)
     sm = mace.mace_build_sysmatrix(n, n, V, D, N, view_agent=va, sv_size=8)
+    # FP32 iterates: the Mann residual settles near 1.4e-7 on this scan
     prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=0.5, sigma_mode=1, rho=0.8, sweeps_per_iter=2,
-                           symmetric=True, recompute_every=10, tol=1e-7, max_iter=8000, concurrency=1,
+                           symmetric=True, recompute_every=10, tol=3e-7, max_iter=8000, concurrency=1,
                            neighbourhood=26, schedule=1, chains=2)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, batch=nz)
     assert st.stats()["chains"] == 2
