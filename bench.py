@@ -585,11 +585,11 @@ def run_volume(args):
     """A 3D stack: args.slices slices of 512^2 sharing one 2D matrix (960
     views over 180 deg, 725 channels), 32 agents with uneven view subsets
     (16-40 views each, spread over the half circle), 26-neighbourhood
-    Q-GGMRF coupling the slices.  Schedule 1 (default): a persistent grid fed
-    from a work queue of (slice, agent, row of super-voxels) items, even
+    Q-GGMRF coupling the slices.  Schedule 0 (default): fixed warps per
+    (slice pair, agent), all slices at once; schedule 1: a persistent grid
+    fed from a work queue of (slice, agent, row of super-voxels) items, even
     slices first, then odd ones, two slices of one parity per warp with
-    --chains 2 (the default); schedule 0: fixed warps per (slice pair,
-    agent).  Times args.steps Mann iterations (value = Mann iterations
+    --chains 2 (the default).  Times args.steps Mann iterations (value = Mann iterations
     per second of the whole volume); with --volume-tol > 0 it then runs on
     to that residual (at most args.max_iter iterations) and reports the
     iterations and the time to get there."""
@@ -747,9 +747,12 @@ def build_parser():
     ap.add_argument("--volume", action="store_true",
                     help="time Mann iterations of a 3D stack with uneven agents (its own JSON line)")
     ap.add_argument("--slices", type=int, default=64)
-    ap.add_argument("--volume-schedule", dest="volume_schedule", type=int, default=1, choices=[0, 1])
+    # the fixed grid (one warp per slice pair and agent: serial order per
+    # pair) converges at sigma 0.3; the work queue with a row of super-voxels
+    # per item runs as fast per iteration but diverged at 0.13 on this stack
+    ap.add_argument("--volume-schedule", dest="volume_schedule", type=int, default=0, choices=[0, 1])
     ap.add_argument("--volume-sv", dest="volume_sv", type=int, default=8)
-    ap.add_argument("--volume-sigma", dest="volume_sigma", type=float, default=0.13)
+    ap.add_argument("--volume-sigma", dest="volume_sigma", type=float, default=0.3)
     ap.add_argument("--volume-tol", dest="volume_tol", type=float, default=0.0,
                     help="volume: after the timed iterations, run on to this Mann residual")
     ap.add_argument("--autotune", action="store_true",
