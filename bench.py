@@ -588,8 +588,7 @@ def run_volume(args):
     Q-GGMRF coupling the slices.  Schedule 0 (default): fixed warps per
     (slice pair, agent), all slices at once; schedule 1: a persistent grid
     fed from a work queue of (slice, agent, row of super-voxels) items, even
-    slices first, then odd ones, two slices of one parity per warp with
-    --chains 2 (the default).  Times args.steps Mann iterations (value = Mann iterations
+    slices first, then odd ones; --volume-chains 2: two slices per warp.  Times args.steps Mann iterations (value = Mann iterations
     per second of the whole volume); with --volume-tol > 0 it then runs on
     to that residual (at most args.max_iter iterations) and reports the
     iterations and the time to get there."""
@@ -612,7 +611,7 @@ def run_volume(args):
     prm = mace.make_params(prior="qggmrf", sigma_x=sx, sigma=args.volume_sigma, sigma_mode=1, rho=args.rho,
                            sweeps_per_iter=2, symmetric=True, recompute_every=10, max_iter=args.max_iter,
                            tol=args.volume_tol, concurrency=args.concurrency, neighbourhood=26,
-                           schedule=args.volume_schedule, chains=args.chains)
+                           schedule=args.volume_schedule, chains=args.volume_chains)
     st = mace.mace_init(sm, c["y"], c["lam"], prm, stream=stream, batch=nz)
     st.iterate(args.warmup)
     st.set_timing(True, max_launches=4 * args.steps + 8)
@@ -752,6 +751,8 @@ def build_parser():
     # per item runs as fast per iteration but diverged at 0.13 on this stack
     ap.add_argument("--volume-schedule", dest="volume_schedule", type=int, default=0, choices=[0, 1])
     ap.add_argument("--volume-sv", dest="volume_sv", type=int, default=8)
+    ap.add_argument("--volume-chains", dest="volume_chains", type=int, default=1,
+                    help="volume: slices one warp sweeps over each column load (1 or 2)")
     ap.add_argument("--volume-sigma", dest="volume_sigma", type=float, default=0.3)
     ap.add_argument("--volume-tol", dest="volume_tol", type=float, default=0.0,
                     help="volume: after the timed iterations, run on to this Mann residual")
